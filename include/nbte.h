@@ -1,0 +1,216 @@
+/*
+ * nbte.h -- C ABI of libnanobte: steady non-gray phonon BTE (relaxation-time
+ * approximation) on one B300 GPU.
+ *
+ * What the library computes (paper: "NanoBTE", Sec. II and III):
+ *   for every band l and discrete direction i the steady per-mode equation
+ *   (Sec. II, Eq. (4))   v_l s_i . grad e + (e - e0_l)/tau_l = S_l,
+ *   e0_l = C_l T / W (Eq. (11)), discretised with first-order upwind finite
+ *   volumes; walls are thermalizing, diffuse, specular or partially specular
+ *   (Sec. II, Sec. III A/B); the volumetric heat source is an equilibrium
+ *   source, uniform over directions and split over bands by heat capacity
+ *   (Sec. III B); the lattice temperature follows from the collision moment
+ *   (Eq. (5)) -- the sequential scheme (Eq. (6)) -- or additionally from the
+ *   diffusion-type correction of Eqs. (8)-(10) -- the synthetic scheme
+ *   (Eq. (12)); the heat flux is the moment of Eq. (7).
+ *
+ * Conventions for every call:
+ *   - SI units: metres, kelvin, J/(m^3 K), m/s, s, W/m^3.
+ *   - Host arrays only.  The caller owns every array it passes; the library
+ *     copies what it needs before returning and never keeps a caller pointer.
+ *     Output arrays are caller-allocated and written in full on success.
+ *   - Every call returns an int status: NBTE_OK (0) or a negative NBTE_ERR_*
+ *     code; on error nothing observable has changed (for solves: the solver
+ *     state is as after the last completed iteration) and nbte_last_error()
+ *     describes the failure.  Argument checks (sizes, NaN, signs, mesh
+ *     validity) happen before any device work.
+ *   - Handles are not thread-safe: one handle must not be used by two host
+ *     threads at once.  Different handles are independent.
+ *   - Each solver runs on its own CUDA stream (or the one given with
+ *     nbte_solver_set_stream) of the device current when it was created.
+ */
+#ifndef NBTE_H
+#define NBTE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nbte_mesh nbte_mesh;
+typedef struct nbte_solver nbte_solver;
+
+enum {
+  NBTE_OK = 0,
+  NBTE_ERR_ARG = -1,            /* invalid argument (size, NaN, sign, range)        */
+  NBTE_ERR_MESH = -2,           /* invalid mesh (degenerate cell, untagged face...) */
+  NBTE_ERR_OOM = -3,            /* host or device allocation failed                 */
+  NBTE_ERR_CUDA = -4,           /* a CUDA call failed                               */
+  NBTE_ERR_NOT_CONVERGED = -5,  /* max_iter reached before tol (results are kept)  */
+  NBTE_ERR_DIVERGED = -6,       /* residual grew without bound / non-finite values  */
+  NBTE_ERR_DEVICE_TIMEOUT = -7, /* a bounded device-side wait gave up               */
+  NBTE_ERR_STATE = -8           /* call out of order (e.g. solve before set_bands)  */
+};
+
+/* cell types: node counts and local orderings
+ *   NBTE_TRI  (2D) 3 nodes;  NBTE_QUAD (2D) 4 nodes in cyclic order;
+ *   NBTE_TET  (3D) 4 nodes;  NBTE_HEX  (3D) 8 nodes, bottom cycle 0-1-2-3 then
+ *   top cycle 4-5-6-7 with node 4 above node 0 (faces planar).            */
+enum { NBTE_TRI = 3, NBTE_QUAD = 4, NBTE_TET = 10, NBTE_HEX = 12 };
+
+/* wall types (Sec. II; Sec. III A/B) */
+enum { NBTE_THERMALIZING = 0, NBTE_DIFFUSE = 1, NBTE_SPECULAR = 2, NBTE_PARTIAL = 3 };
+
+/* ------------------------------------------------------------------ mesh --
+ * nbte_mesh_create: build the finite-volume mesh (faces, outward face
+ * vectors, volumes, centroids) from nodes and cells.
+ *   dim          2 or 3; must match cell_type.
+ *   xyz          n_nodes*dim coordinates, node-major.
+ *   cell_nodes   n_cells*nodes_per_cell node indices (0-based).
+ *   bface_nodes  n_bfaces*nodes_per_face node indices of the exterior faces
+ *                (2 per face in 2D, 3 for tet meshes, 4 for hex meshes), any
+ *                order within a face; bface_tag[n_bfaces] their integer tags.
+ * Every exterior face must appear exactly once in bface_nodes, and every
+ * listed face must be exterior: otherwise NBTE_ERR_MESH.  Degenerate cells
+ * (volume or face area ~0, non-convex) give NBTE_ERR_MESH.  Geometry:
+ * centroids are vertex averages; a 3D quadrilateral face vector is half the
+ * cross product of its diagonals; volumes come from the divergence theorem.
+ * The library renumbers cells internally (space-filling-curve order); every
+ * per-cell array of this API is in the caller's cell order.
+ */
+int nbte_mesh_create(int dim, int64_t n_nodes, const double* xyz, int cell_type,
+                     int64_t n_cells, const int64_t* cell_nodes, int64_t n_bfaces,
+                     const int64_t* bface_nodes, const int32_t* bface_tag, nbte_mesh** out);
+int nbte_mesh_destroy(nbte_mesh* mesh);
+/* n_cells of the mesh; total volume (m^3, or m^2 in 2D) */
+int nbte_mesh_info(const nbte_mesh* mesh, int64_t* n_cells, double* volume);
+
+/* ---------------------------------------------------------------- solver --
+ * nbte_solver_create: a solver bound to `mesh` (the mesh must outlive it) and
+ * the CUDA device current at this call.  T_ref: reference temperature (K)
+ * around which deviations are carried (Sec. III A uses 300 K).            */
+int nbte_solver_create(const nbte_mesh* mesh, double T_ref, nbte_solver** out);
+int nbte_solver_destroy(nbte_solver* solver);
+/* Use the caller's stream (a cudaStream_t passed as void*) for all device work
+ * of this solver; NULL restores the solver's own stream.                 */
+int nbte_solver_set_stream(nbte_solver* solver, void* cuda_stream);
+
+/* Band table (Sec. II; Sec. III A/B): heat capacity C[l] > 0 (J/m^3K),
+ * group velocity v[l] > 0 (m/s), relaxation time tau[l] > 0 (s).          */
+int nbte_set_bands(nbte_solver* solver, int n_bands, const double* C, const double* v,
+                   const double* tau);
+
+/* Discrete-ordinates set (Sec. II, Eq. (11)): s[n_dirs*3] unit vectors
+ * (|s| = 1 within 1e-9), w[n_dirs] > 0.  On a 2D mesh only (s_x, s_y) enter
+ * the transport; s_z distinguishes out-of-plane directions of a 3D material
+ * (Sec. III A, the cross-plane case).  W = sum w.                         */
+int nbte_set_quadrature(nbte_solver* solver, int n_dirs, const double* s, const double* w);
+
+/* One condition per boundary tag.  T_wall (K) is used by THERMALIZING walls;
+ * specularity p in [0,1] by PARTIAL walls (incoming = p*specular +
+ * (1-p)*diffuse).  Every tag present in the mesh must be covered and at least
+ * one wall must be THERMALIZING (otherwise the steady problem has no unique
+ * solution): NBTE_ERR_ARG.                                                */
+typedef struct {
+  int32_t tag;
+  int32_t type;
+  double T_wall;
+  double specularity;
+} nbte_boundary;
+int nbte_set_boundaries(nbte_solver* solver, int n, const nbte_boundary* bcs);
+
+/* Volumetric heat generation Qdot[n_cells] (W/m^3, finite; NULL = none).  */
+int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
+
+/* ------------------------------------------------------------------ solve --
+ * scheme:    0 sequential (Eq. (6)); 1 synthetic, diffusion-synthetic form of
+ *            Eqs. (8)-(10) (correction added to the kinetic temperature of
+ *            the new distribution); 2 synthetic, literal form (correction
+ *            added to the previous iterate).
+ * precision: 0 FP64 throughout; 1 FP32 sweep (distributions and transport
+ *            coefficients FP32; moments, temperature, residual, correction
+ *            and energy balance FP64).
+ * tol:       stop when |T^{n+1}-T^n|_inf / |T^{n+1}-T_ref|_inf < tol.
+ * max_iter:  iteration cap (> 0).  n_iter > 0 instead runs exactly n_iter
+ *            iterations with no convergence test.
+ * T_init:    initial temperature field [n_cells] (K) or NULL (= T_ref).
+ * warm:      1 = continue from the solver's current state (T and wall
+ *            values) instead of T_init.
+ * band_group: bands per work item (0 = planner's choice); threads_per_cell:
+ *            threads sharing one cell's bands (0 = planner's choice, power
+ *            of two <= 32); both tune the sweep kernel.
+ * cg_tol, cg_max_iter: relative residual and cap of the conjugate-gradient
+ *            solve of the synthetic correction (0 = defaults 1e-10, 5000); the
+ *            correction only changes the rate of convergence, not the limit.
+ * use_graph: 1 = replay each iteration from a captured CUDA graph.
+ */
+typedef struct {
+  int32_t scheme;
+  int32_t precision;
+  double tol;
+  int32_t max_iter;
+  int32_t n_iter;
+  const double* T_init;
+  int32_t warm;
+  int32_t band_group;
+  int32_t threads_per_cell;
+  double cg_tol;
+  int32_t cg_max_iter;
+  int32_t use_graph;
+} nbte_solve_opts;
+
+/* Filled on return from nbte_solve_steady (also on NOT_CONVERGED):
+ *   iterations        sweeps performed;
+ *   residual          last relative increment (see tol);
+ *   energy_imbalance  |net heat through thermalizing walls - integral of
+ *                     Qdot| / max(integral |Qdot|, sum |wall heat|), FP64;
+ *   lagged_faces      inflow faces whose upwind value is taken from the
+ *                     previous iteration to break upwind-graph cycles;
+ *   seconds           wall time of the iteration loop;
+ *   cg_iterations     total CG iterations (synthetic schemes).            */
+typedef struct {
+  int32_t iterations;
+  double residual;
+  double energy_imbalance;
+  int64_t lagged_faces;
+  double seconds;
+  int64_t cg_iterations;
+} nbte_solve_info;
+
+/* Default options: sequential, FP64, tol 1e-10, max_iter 10000.           */
+int nbte_default_opts(nbte_solve_opts* opts);
+
+/* Run the iteration (Eq. (6) or Eq. (12)) until tol or for n_iter sweeps.
+ * Returns NBTE_OK, NBTE_ERR_NOT_CONVERGED (results of the last iteration are
+ * kept and readable), NBTE_ERR_DIVERGED or NBTE_ERR_DEVICE_TIMEOUT.       */
+int nbte_solve_steady(nbte_solver* solver, const nbte_solve_opts* opts, nbte_solve_info* info);
+
+/* Results of the last solve, in the caller's cell order.
+ *   kind 0: lattice temperature T_L after the last update (K);
+ *   kind 1: energy temperature sum_l sum_i w_i e / C_tot of the last sweep (K);
+ *   kind 2: kinetic pseudo-temperature of the last sweep, Eq. (5), before any
+ *           synthetic correction (K).                                      */
+int nbte_get_temperature(const nbte_solver* solver, int kind, double* out);
+/* Heat flux of the last sweep, Eq. (7): out[n_cells*dim] (W/m^2).          */
+int nbte_get_heat_flux(const nbte_solver* solver, double* out);
+/* Net outward heat flow through the walls of one tag after the last sweep
+ * (W, or W/m in 2D): sum over its faces of sum_l sum_i w_i v_l (s_i.An) e~. */
+int nbte_get_wall_heat(const nbte_solver* solver, int32_t tag, double* out);
+
+/* Planner statistics of the current quadrature/mesh (for tuning and tests):
+ * stats[0] total levels over all directions, [1] max levels of one
+ * direction, [2] max ring slots of one direction, [3] lagged faces,
+ * [4] work items, [5] bands per item, [6] threads per cell, [7] device bytes
+ * held by the solver.                                                      */
+int nbte_plan_stats(nbte_solver* solver, const nbte_solve_opts* opts, int64_t stats[8]);
+
+/* Message of the last failing call on this thread (library-owned string). */
+const char* nbte_last_error(void);
+/* Library version string. */
+const char* nbte_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBTE_H */

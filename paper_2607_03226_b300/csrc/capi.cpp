@@ -1,0 +1,1000 @@
+// extern "C" entry points of libnanobte (see include/nbte.h) and the solve
+// driver.  One outer iteration (Sec. II, Eq. (6) / Eq. (12)) is
+//   walls -> sweep -> moment reduction + update [-> CG correction -> update]
+// on the solver's stream; the host reads two residual words per iteration
+// and stops at tol.  With use_graph the iteration is captured once as a CUDA
+// graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels.h"
+#include "nbte_internal.h"
+
+using namespace nbte;
+
+namespace nbte {
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace nbte
+
+#define NBTE_CK(call)                                                                               \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      set_error(std::string("CUDA error in ") + #call + ": " + cudaGetErrorString(e_));             \
+      return e_ == cudaErrorMemoryAllocation ? NBTE_ERR_OOM : NBTE_ERR_CUDA;                        \
+    }                                                                                               \
+  } while (0)
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+// RAII device allocation
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t alloc(size_t n) {
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    else p = nullptr;
+    return e;
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+template <typename T>
+cudaError_t upload(DBuf& b, const std::vector<T>& v) {
+  cudaError_t e = b.alloc(v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+template <typename T>
+std::vector<float> to_float(const std::vector<T>& v) {
+  std::vector<float> f(v.size());
+  for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
+  return f;
+}
+
+}  // namespace
+
+struct nbte_mesh {
+  Mesh m;
+};
+
+struct nbte_solver {
+  const nbte_mesh* mesh = nullptr;
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  double T_ref = 300.0;
+  // inputs (caller order for Q converted to internal)
+  int B = 0;
+  std::vector<double> C, v, tau;
+  int D = 0;
+  std::vector<double> s, w;
+  std::vector<BC> bcs;
+  bool bcs_set = false;
+  std::vector<double> Q;   // internal order
+  int64_t version_plan = 0, version_bands = 0, version_q = 0;
+
+  // ---- plan (depends on quadrature and walls)
+  int64_t plan_built = -1;
+  int K = 0, D_plan = 0;
+  int64_t n_exp = 0, n_imp = 0, n_dbf = 0, n_wf = 0, lagged = 0, total_levels = 0;
+  int max_levels = 0, max_slots = 0, max_width = 0;
+  std::vector<int32_t> wf_tag_h;
+  std::vector<double> pos_G_h, pos_coef_h;   // kept for the FP32 copies
+  DBuf lvl_off, level_ptr, pos_cell, pos_slot, pos_exp, pos_ref, pos_G64, pos_coef64, pos_G32, pos_coef32;
+  DBuf exp_off, imp_off, exp_cell, imp_kind, imp_dbf, imp_src, imp_par, dif_ptr, dif_src, dif_wt;
+  DBuf wf_ptr, wf_val, wf_coef, dir_w, dir_s;
+  // ---- band layout (depends on bands, precision and tuning)
+  std::string layout_key;
+  int prec = 0, G = 1, bpt = 1, lanes = 1, n_groups = 1, Bp = 1, n_items = 0, threads = 64;
+  size_t smem = 0;
+  double W = 0, beta = 0, Ctot = 0;
+  DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
+  DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
+  DBuf cg_r, cg_z, cg_p, cg_Ap, cg_partial, cg_bar, cg_err, cg_it, cg_res;
+  int cg_grid = 0;
+  // ---- laplacian (synthetic)
+  int64_t lap_built = -1;
+  DBuf L_rp, L_col, L_val, L_dinv;
+  // ---- state
+  bool have_state = false;
+  bool have_results = false;
+  unsigned long long* h_res = nullptr;   // pinned: [2] residual words
+  int32_t* h_misc = nullptr;             // pinned: [2] device error, cg iterations
+  cudaGraphExec_t graph = nullptr;
+  std::string graph_key;
+  double last_energy_imbalance = 0;
+  std::vector<double> wall_heat_by_face;
+
+  ~nbte_solver() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (h_res) cudaFreeHost(h_res);
+    if (h_misc) cudaFreeHost(h_misc);
+    if (own_stream) cudaStreamDestroy(own_stream);
+  }
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t device_bytes(const nbte_solver* S) {
+  const DBuf* all[] = {&S->lvl_off, &S->level_ptr, &S->pos_cell, &S->pos_slot, &S->pos_exp, &S->pos_ref,
+                       &S->pos_G64, &S->pos_coef64, &S->pos_G32, &S->pos_coef32, &S->exp_off, &S->imp_off,
+                       &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
+                       &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
+                       &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
+                       &S->band_CoW, &S->band_v64, &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part,
+                       &S->T, &S->Tprev, &S->Tkin, &S->Delta, &S->rhs, &S->delta, &S->Qd, &S->Vd, &S->dsum,
+                       &S->accE, &S->accQ, &S->res, &S->heat, &S->cg_r, &S->cg_z, &S->cg_p, &S->cg_Ap,
+                       &S->cg_partial, &S->cg_bar, &S->cg_err, &S->cg_it, &S->cg_res, &S->L_rp, &S->L_col,
+                       &S->L_val, &S->L_dinv};
+  size_t t = 0;
+  for (auto* b : all) t += b->bytes;
+  return t;
+}
+
+void drop_graph(nbte_solver* S) {
+  if (S->graph) cudaGraphExecDestroy(S->graph);
+  S->graph = nullptr;
+  S->graph_key.clear();
+}
+
+// ------------------------------------------------------------------ plan
+int ensure_plan(nbte_solver* S) {
+  if (S->plan_built == S->version_plan) return NBTE_OK;
+  if (S->D <= 0) return fail(NBTE_ERR_STATE, "nbte_set_quadrature must be called before solving");
+  if (!S->bcs_set) return fail(NBTE_ERR_STATE, "nbte_set_boundaries must be called before solving");
+  const Mesh& m = S->mesh->m;
+  Plan P;
+  const int nt = (int)std::max(1u, std::thread::hardware_concurrency());
+  Status st = build_plan(m, S->D, S->s.data(), S->w.data(), S->bcs, S->T_ref, P, nt);
+  if (!st.good()) return fail(st.code, st.msg);
+  // compact the inflow entries to the largest count actually used
+  const int64_t N = P.N;
+  int K = 1;
+  for (int i = 0; i < P.D; ++i)
+    for (int k = P.K - 1; k >= K; --k) {
+      bool any = false;
+      const size_t off = ((size_t)i * P.K + k) * N;
+      for (int64_t p = 0; p < N && !any; ++p) any = P.pos_coef[off + p] != 0.0 || P.pos_ref[off + p] != 0;
+      if (any) { K = k + 1; break; }
+    }
+  std::vector<int32_t> ref((size_t)P.D * K * N);
+  std::vector<double> coef((size_t)P.D * K * N);
+  for (int i = 0; i < P.D; ++i)
+    for (int k = 0; k < K; ++k) {
+      std::copy_n(P.pos_ref.begin() + ((size_t)i * P.K + k) * N, N, ref.begin() + ((size_t)i * K + k) * N);
+      std::copy_n(P.pos_coef.begin() + ((size_t)i * P.K + k) * N, N, coef.begin() + ((size_t)i * K + k) * N);
+    }
+  P.pos_ref.clear(); P.pos_ref.shrink_to_fit();
+  P.pos_coef.clear(); P.pos_coef.shrink_to_fit();
+  DeviceGuard g(S->device);
+  drop_graph(S);
+  S->pos_G32.release();
+  S->pos_coef32.release();
+  NBTE_CK(upload(S->lvl_off, P.lvl_off));
+  NBTE_CK(upload(S->level_ptr, P.level_ptr));
+  NBTE_CK(upload(S->pos_cell, P.pos_cell));
+  NBTE_CK(upload(S->pos_slot, P.pos_slot));
+  NBTE_CK(upload(S->pos_exp, P.pos_exp));
+  NBTE_CK(upload(S->pos_ref, ref));
+  NBTE_CK(upload(S->pos_G64, P.pos_G));
+  NBTE_CK(upload(S->pos_coef64, coef));
+  NBTE_CK(upload(S->exp_off, P.exp_off));
+  NBTE_CK(upload(S->imp_off, P.imp_off));
+  NBTE_CK(upload(S->exp_cell, P.exp_cell));
+  NBTE_CK(upload(S->imp_kind, P.imp_kind));
+  NBTE_CK(upload(S->imp_dbf, P.imp_dbf));
+  NBTE_CK(upload(S->imp_src, P.imp_src));
+  NBTE_CK(upload(S->imp_par, P.imp_par));
+  NBTE_CK(upload(S->dif_ptr, P.dif_ptr));
+  NBTE_CK(upload(S->dif_src, P.dif_src));
+  NBTE_CK(upload(S->dif_wt, P.dif_wt));
+  NBTE_CK(upload(S->wf_ptr, P.wf_ptr));
+  NBTE_CK(upload(S->wf_val, P.wf_val));
+  NBTE_CK(upload(S->wf_coef, P.wf_coef));
+  NBTE_CK(upload(S->dir_w, S->w));
+  NBTE_CK(upload(S->dir_s, S->s));
+  S->pos_G_h = std::move(P.pos_G);
+  S->pos_coef_h = std::move(coef);
+  S->K = K;
+  S->D_plan = P.D;
+  S->n_exp = P.exp_off.back();
+  S->n_imp = P.imp_off.back();
+  S->n_dbf = (int64_t)P.dif_ptr.size() - 1;
+  S->n_wf = (int64_t)P.wf_tag.size();
+  S->wf_tag_h = P.wf_tag;
+  S->lagged = P.lagged_faces;
+  S->total_levels = P.total_levels;
+  S->max_levels = P.max_levels;
+  S->max_slots = P.max_slots;
+  S->max_width = P.max_width_all;
+  S->plan_built = S->version_plan;
+  S->layout_key.clear();
+  S->have_state = false;
+  return NBTE_OK;
+}
+
+int ensure_fp32_coefs(nbte_solver* S) {
+  if (S->pos_G32.p) return NBTE_OK;
+  NBTE_CK(upload(S->pos_G32, to_float(S->pos_G_h)));
+  NBTE_CK(upload(S->pos_coef32, to_float(S->pos_coef_h)));
+  return NBTE_OK;
+}
+
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// ------------------------------------------------------------------ layout
+int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
+  if (S->B <= 0) return fail(NBTE_ERR_STATE, "nbte_set_bands must be called before solving");
+  const int prec = o.precision;
+  const size_t sz = prec ? 4 : 8;
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device);
+  if (smem_optin <= 0) smem_optin = 48 * 1024;
+  const int Gmax = (int)((size_t)smem_optin / ((size_t)(S->max_slots + 1) * sz));
+  if (Gmax < 1)
+    return fail(NBTE_ERR_ARG, "one direction's live cells exceed shared memory (" + std::to_string(S->max_slots) +
+                                  " ring slots); use FP32 or a smaller mesh");
+  const int maxbpt = prec ? 8 : 4;
+  int G = o.band_group;
+  if (G > 0) {
+    if (!pow2(G) || G > 32) return fail(NBTE_ERR_ARG, "band_group must be a power of two <= 32");
+    if (G > Gmax) return fail(NBTE_ERR_ARG, "band_group too large for shared memory on this mesh");
+  } else {
+    G = 1;
+    double best = 1e300;
+    for (int c : {32, 16, 8, 4, 2, 1}) {
+      if (c > Gmax || c > 2 * maxbpt) continue;
+      const int ng = (S->B + c - 1) / c;
+      const double waste = (double)(ng * c - S->B) / S->B;
+      // prefer wide groups unless they pad more than 12.5%
+      const double score = waste <= 0.125 ? -c : 1000.0 * waste - c;
+      if (score < best) { best = score; G = c; }
+    }
+  }
+  int lanes = o.threads_per_cell > 0 ? o.threads_per_cell : 1;
+  if (!pow2(lanes) || lanes > 8) return fail(NBTE_ERR_ARG, "threads_per_cell must be 1, 2, 4 or 8");
+  if (lanes > G) lanes = G;
+  while (G / lanes > maxbpt) lanes *= 2;
+  if (lanes > 8) return fail(NBTE_ERR_ARG, "band_group too large for the thread layout");
+  const int bpt = G / lanes;
+  const int ng = (S->B + G - 1) / G;
+  const int Bp = ng * G;
+  const int threads = std::min(512, std::max(32, ((S->max_width * lanes + 31) / 32) * 32));
+  const std::string key = std::to_string(prec) + "/" + std::to_string(G) + "/" + std::to_string(lanes) + "/" +
+                          std::to_string(S->version_bands) + "/" + std::to_string(S->plan_built);
+  if (key == S->layout_key) return NBTE_OK;
+  DeviceGuard dg(S->device);
+  drop_graph(S);
+  if (prec) {
+    int rc = ensure_fp32_coefs(S);
+    if (rc) return rc;
+  }
+  S->prec = prec; S->G = G; S->lanes = lanes; S->bpt = bpt; S->n_groups = ng; S->Bp = Bp;
+  S->n_items = S->D * ng;
+  S->threads = threads;
+  S->smem = (size_t)(S->max_slots + 1) * G * sz;
+  const int64_t N = S->mesh->m.n_cells;
+  // band constants, padded bands are inert (C = 0, v = 0, 1/tau = 1)
+  S->W = 0;
+  for (double x : S->w) S->W += x;
+  S->beta = 0;
+  S->Ctot = 0;
+  for (int l = 0; l < S->B; ++l) { S->beta += S->C[l] / S->tau[l]; S->Ctot += S->C[l]; }
+  std::vector<double> bv(Bp, 0.0), bit(Bp, 1.0), baT(Bp, 0.0), baQ(Bp, 0.0), bCoW(Bp, 0.0);
+  for (int l = 0; l < S->B; ++l) {
+    bv[l] = S->v[l];
+    bit[l] = 1.0 / S->tau[l];
+    baT[l] = S->C[l] / (S->W * S->tau[l]);
+    baQ[l] = S->C[l] / (S->Ctot * S->W);
+    bCoW[l] = S->C[l] / S->W;
+  }
+  if (prec) {
+    NBTE_CK(upload(S->band_v, to_float(bv)));
+    NBTE_CK(upload(S->band_itau, to_float(bit)));
+    NBTE_CK(upload(S->band_aT, to_float(baT)));
+    NBTE_CK(upload(S->band_aQ, to_float(baQ)));
+  } else {
+    NBTE_CK(upload(S->band_v, bv));
+    NBTE_CK(upload(S->band_itau, bit));
+    NBTE_CK(upload(S->band_aT, baT));
+    NBTE_CK(upload(S->band_aQ, baQ));
+  }
+  NBTE_CK(upload(S->band_CoW, bCoW));
+  NBTE_CK(upload(S->band_v64, bv));
+  std::vector<int32_t> idir(S->n_items), igrp(S->n_items);
+  for (int i = 0; i < S->D; ++i)
+    for (int g = 0; g < ng; ++g) { idir[i * ng + g] = i; igrp[i * ng + g] = g; }
+  NBTE_CK(upload(S->item_dir, idir));
+  NBTE_CK(upload(S->item_grp, igrp));
+  NBTE_CK(S->expt.alloc((size_t)S->n_exp * Bp * sz));
+  NBTE_CK(S->impt.alloc((size_t)S->n_imp * Bp * sz));
+  NBTE_CK(S->srcTQ.alloc((size_t)2 * N * sz));
+  NBTE_CK(S->srcTQ_fin.alloc((size_t)2 * N * sz));
+  NBTE_CK(S->part.alloc((size_t)S->n_items * N * 8));
+  NBTE_CK(S->T.alloc(N * 8));
+  NBTE_CK(S->Tprev.alloc(N * 8));
+  NBTE_CK(S->Tkin.alloc(N * 8));
+  NBTE_CK(S->Delta.alloc(N * 8));
+  NBTE_CK(S->rhs.alloc(N * 8));
+  NBTE_CK(S->delta.alloc(N * 8));
+  NBTE_CK(S->Qd.alloc(N * 8));
+  NBTE_CK(S->Vd.alloc(N * 8));
+  NBTE_CK(S->dsum.alloc((size_t)S->n_dbf * Bp * 8));
+  NBTE_CK(S->accE.alloc(N * 8));
+  NBTE_CK(S->accQ.alloc((size_t)N * S->mesh->m.dim * 8));
+  NBTE_CK(S->res.alloc(16));
+  NBTE_CK(S->heat.alloc((size_t)S->n_wf * 8));
+  NBTE_CK(cudaMemcpy(S->Vd.p, S->mesh->m.V.data(), N * 8, cudaMemcpyHostToDevice));
+  S->version_q = -1;   // force heat-source upload
+  S->layout_key = key;
+  S->have_state = false;
+  return NBTE_OK;
+}
+
+int ensure_q(nbte_solver* S) {
+  static_cast<void>(S);
+  const int64_t N = S->mesh->m.n_cells;
+  if (S->Q.empty()) S->Q.assign(N, 0.0);
+  NBTE_CK(cudaMemcpyAsync(S->Qd.p, S->Q.data(), N * 8, cudaMemcpyHostToDevice, S->stream));
+  return NBTE_OK;
+}
+
+int ensure_laplacian(nbte_solver* S) {
+  const int64_t want = S->version_bands * 1000003 + S->version_plan;
+  if (S->lap_built == want && S->L_rp.p) return NBTE_OK;
+  const Mesh& m = S->mesh->m;
+  // kappa_bulk = sum C v^2 tau * (1/dim) sum_i w_i |s_i|^2 / W  (in-domain s)
+  double ang = 0, mean_abs = 0, W = 0;
+  for (int i = 0; i < S->D; ++i) {
+    double s2 = 0, sa = 0;
+    for (int d = 0; d < m.dim; ++d) { s2 += S->s[i * 3 + d] * S->s[i * 3 + d]; sa += std::fabs(S->s[i * 3 + d]); }
+    ang += S->w[i] * s2;
+    mean_abs += S->w[i] * sa;
+    W += S->w[i];
+  }
+  ang /= (m.dim * W);
+  mean_abs /= (m.dim * W);
+  double kb = 0, cv = 0;
+  for (int l = 0; l < S->B; ++l) { kb += S->C[l] * S->v[l] * S->v[l] * S->tau[l]; cv += S->C[l] * S->v[l]; }
+  kb *= ang;
+  const double k1 = 0.25 * mean_abs * cv;
+  Laplacian L;
+  build_laplacian(m, S->bcs, kb, k1, L);
+  std::vector<double> dinv(L.diag.size());
+  for (size_t c = 0; c < dinv.size(); ++c) dinv[c] = 1.0 / L.diag[c];
+  DeviceGuard g(S->device);
+  NBTE_CK(upload(S->L_rp, L.row_ptr));
+  NBTE_CK(upload(S->L_col, L.col));
+  NBTE_CK(upload(S->L_val, L.val));
+  NBTE_CK(upload(S->L_dinv, dinv));
+  const int64_t N = m.n_cells;
+  NBTE_CK(S->cg_r.alloc(N * 8));
+  NBTE_CK(S->cg_z.alloc(N * 8));
+  NBTE_CK(S->cg_p.alloc(N * 8));
+  NBTE_CK(S->cg_Ap.alloc(N * 8));
+  S->cg_grid = std::max(1, std::min(cg_max_grid(S->device), (int)((N + 255) / 256)));
+  NBTE_CK(S->cg_partial.alloc((size_t)3 * S->cg_grid * 8));
+  NBTE_CK(S->cg_bar.alloc(16));
+  NBTE_CK(S->cg_err.alloc(16));
+  NBTE_CK(S->cg_it.alloc(16));
+  NBTE_CK(S->cg_res.alloc(16));
+  NBTE_CK(cudaMemset(S->cg_bar.p, 0, 16));
+  NBTE_CK(cudaMemset(S->cg_err.p, 0, 16));
+  S->lap_built = want;
+  drop_graph(S);
+  return NBTE_OK;
+}
+
+// ------------------------------------------------------------------ iteration body
+template <typename R>
+SweepArgs<R> sweep_args(nbte_solver* S, const void* srcTQ, int full) {
+  SweepArgs<R> a{};
+  a.N = (int)S->mesh->m.n_cells;
+  a.Bp = S->Bp; a.G = S->G; a.n_groups = S->n_groups; a.dim = S->mesh->m.dim;
+  a.full = full;
+  a.item_dir = S->item_dir.as<int32_t>();
+  a.item_grp = S->item_grp.as<int32_t>();
+  a.lvl_off = S->lvl_off.as<int64_t>();
+  a.level_ptr = S->level_ptr.as<int32_t>();
+  a.pos_cell = S->pos_cell.as<int32_t>();
+  a.pos_slot = S->pos_slot.as<int32_t>();
+  a.pos_exp = S->pos_exp.as<int32_t>();
+  a.pos_ref = S->pos_ref.as<int32_t>();
+  if constexpr (sizeof(R) == 4) {
+    a.pos_G = S->pos_G32.as<R>();
+    a.pos_coef = S->pos_coef32.as<R>();
+  } else {
+    a.pos_G = S->pos_G64.as<R>();
+    a.pos_coef = S->pos_coef64.as<R>();
+  }
+  a.exp_off = S->exp_off.as<int64_t>();
+  a.imp_off = S->imp_off.as<int64_t>();
+  a.imp = S->impt.as<R>();
+  a.exp = S->expt.as<R>();
+  a.srcTQ = static_cast<const R*>(srcTQ);
+  a.band_v = S->band_v.as<R>();
+  a.band_inv_tau = S->band_itau.as<R>();
+  a.band_aT = S->band_aT.as<R>();
+  a.band_aQ = S->band_aQ.as<R>();
+  a.dir_w = S->dir_w.as<double>();
+  a.dir_s = S->dir_s.as<double>();
+  a.part = S->part.as<double>();
+  a.accE = S->accE.as<double>();
+  a.accQ = S->accQ.as<double>();
+  return a;
+}
+
+template <typename R>
+WallArgs<R> wall_args(nbte_solver* S) {
+  WallArgs<R> a{};
+  a.Bp = S->Bp;
+  a.n_imp = S->n_imp;
+  a.n_dbf = S->n_dbf;
+  a.exp = S->expt.as<R>();
+  a.imp = S->impt.as<R>();
+  a.exp_cell = S->exp_cell.as<int32_t>();
+  a.Delta = S->Delta.as<double>();
+  a.CoW = S->band_CoW.as<double>();
+  a.imp_kind = S->imp_kind.as<int32_t>();
+  a.imp_dbf = S->imp_dbf.as<int32_t>();
+  a.imp_src = S->imp_src.as<int64_t>();
+  a.imp_par = S->imp_par.as<double>();
+  a.dif_ptr = S->dif_ptr.as<int64_t>();
+  a.dif_src = S->dif_src.as<int64_t>();
+  a.dif_wt = S->dif_wt.as<double>();
+  a.dsum = S->dsum.as<double>();
+  return a;
+}
+
+template <typename R>
+UpdateArgs<R> update_args(nbte_solver* S, int mode) {
+  UpdateArgs<R> a{};
+  a.N = (int)S->mesh->m.n_cells;
+  a.n_items = S->n_items;
+  a.mode = mode;
+  a.beta = S->beta;
+  a.inv_beta = 1.0 / S->beta;
+  a.part = S->part.as<double>();
+  a.Q = S->Qd.as<double>();
+  a.V = S->Vd.as<double>();
+  a.T = S->T.as<double>();
+  a.Tkin = S->Tkin.as<double>();
+  a.Delta = S->Delta.as<double>();
+  a.rhs = S->rhs.as<double>();
+  a.delta = S->delta.as<double>();
+  a.srcTQ_next = S->srcTQ.as<R>();
+  a.res = S->res.as<unsigned long long>();
+  return a;
+}
+
+CGArgs cg_args(nbte_solver* S, double tol, int max_it) {
+  CGArgs a{};
+  a.N = (int)S->mesh->m.n_cells;
+  a.rp = S->L_rp.as<int32_t>();
+  a.col = S->L_col.as<int32_t>();
+  a.val = S->L_val.as<double>();
+  a.dinv = S->L_dinv.as<double>();
+  a.b = S->rhs.as<double>();
+  a.x = S->delta.as<double>();
+  a.r = S->cg_r.as<double>();
+  a.z = S->cg_z.as<double>();
+  a.p = S->cg_p.as<double>();
+  a.Ap = S->cg_Ap.as<double>();
+  a.partial = S->cg_partial.as<double>();
+  a.bar = S->cg_bar.as<unsigned>();
+  a.err = S->cg_err.as<int32_t>();
+  a.tol = tol;
+  a.max_it = max_it;
+  a.it_out = S->cg_it.as<int32_t>();
+  a.res_out = S->cg_res.as<double>();
+  return a;
+}
+
+// one outer iteration, stream-ordered (capturable)
+template <typename R>
+cudaError_t enqueue_iteration(nbte_solver* S, int scheme, double cg_tol, int cg_max) {
+  cudaStream_t st = S->stream;
+  launch_walls<R>(wall_args<R>(S), st);
+  cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  e = launch_sweep<R>(sweep_args<R>(S, S->srcTQ.p, 0), S->K, S->bpt, S->lanes, S->n_items, S->threads, S->smem, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(S->res.p, 0, 16, st);
+  if (e != cudaSuccess) return e;
+  if (scheme == 0) {
+    launch_update<R>(update_args<R>(S, 0), st);
+  } else {
+    launch_update<R>(update_args<R>(S, 3), st);
+    e = launch_cg(cg_args(S, cg_tol, cg_max), S->cg_grid, st);
+    if (e != cudaSuccess) return e;
+    launch_update<R>(update_args<R>(S, scheme == 1 ? 1 : 2), st);
+  }
+  e = cudaMemcpyAsync(S->h_res, S->res.p, 16, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(S->h_misc, S->cg_err.p ? S->cg_err.p : S->res.p, 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+template <typename R>
+int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
+  const Mesh& m = S->mesh->m;
+  const int64_t N = m.n_cells;
+  cudaStream_t st = S->stream;
+  const double cg_tol = o.cg_tol > 0 ? o.cg_tol : 1e-10;
+  const int cg_max = o.cg_max_iter > 0 ? o.cg_max_iter : 5000;
+  // ---- initial state
+  if (!(o.warm && S->have_state)) {
+    std::vector<double> T0(N, 0.0);
+    if (o.T_init) {
+      for (int64_t c = 0; c < N; ++c) {
+        const double t = o.T_init[m.perm[c]];
+        if (!std::isfinite(t)) return fail(NBTE_ERR_ARG, "non-finite T_init");
+        T0[c] = t - S->T_ref;
+      }
+    }
+    NBTE_CK(cudaMemcpyAsync(S->T.p, T0.data(), N * 8, cudaMemcpyHostToDevice, st));
+    NBTE_CK(cudaMemsetAsync(S->Delta.p, 0, N * 8, st));
+    NBTE_CK(cudaMemsetAsync(S->Tkin.p, 0, N * 8, st));
+    launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)N, st);
+    launch_init_exports<R>(S->expt.as<R>(), S->exp_cell.as<int32_t>(), S->T.as<double>(),
+                           S->band_CoW.as<double>(), S->Bp, S->n_exp, st);
+    NBTE_CK(cudaGetLastError());
+    NBTE_CK(cudaStreamSynchronize(st));
+    S->have_state = true;
+  } else {
+    launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)N, st);
+  }
+  if (S->cg_it.p) NBTE_CK(cudaMemsetAsync(S->cg_it.p, 0, 4, st));
+  const int scheme = o.scheme;
+  const bool fixed = o.n_iter > 0;
+  const int limit = fixed ? o.n_iter : o.max_iter;
+  // ---- graph
+  bool use_graph = o.use_graph != 0;
+  const std::string gkey = S->layout_key + "/" + std::to_string(scheme) + "/" + std::to_string(cg_tol) + "/" +
+                           std::to_string(cg_max) + "/" + std::to_string(S->lap_built) + "/" +
+                           std::to_string((long long)(intptr_t)st);
+  if (use_graph && (S->graph == nullptr || S->graph_key != gkey)) {
+    drop_graph(S);
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = enqueue_iteration<R>(S, scheme, cg_tol, cg_max);
+      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+      if (e == cudaSuccess && e2 == cudaSuccess && gr &&
+          cudaGraphInstantiate(&S->graph, gr, 0) == cudaSuccess) {
+        S->graph_key = gkey;
+      } else {
+        S->graph = nullptr;
+        use_graph = false;
+      }
+      if (gr) cudaGraphDestroy(gr);
+    } else {
+      use_graph = false;
+    }
+    cudaGetLastError();   // clear a failed capture
+  }
+  // ---- iterate
+  auto t0 = std::chrono::steady_clock::now();
+  int it = 0;
+  double r = INFINITY;
+  int status = NBTE_OK;
+  while (it < limit) {
+    if (use_graph) NBTE_CK(cudaGraphLaunch(S->graph, st));
+    else NBTE_CK(enqueue_iteration<R>(S, scheme, cg_tol, cg_max));
+    NBTE_CK(cudaStreamSynchronize(st));
+    ++it;
+    if (S->h_misc[0] != 0 && scheme != 0) {
+      status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the CG correction gave up");
+      cudaMemset(S->cg_err.p, 0, 16);
+      cudaMemset(S->cg_bar.p, 0, 16);
+      break;
+    }
+    double dmax, tmax;
+    std::memcpy(&dmax, &S->h_res[0], 8);
+    std::memcpy(&tmax, &S->h_res[1], 8);
+    if (!std::isfinite(dmax) || !std::isfinite(tmax)) {
+      status = fail(NBTE_ERR_DIVERGED, "non-finite temperature: the iteration diverged");
+      r = INFINITY;
+      break;
+    }
+    r = dmax / std::max(tmax, 1e-300);
+    if (tmax == 0.0 && dmax == 0.0) r = 0.0;
+    if (!fixed && r < o.tol) break;
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  if (status == NBTE_OK && !fixed && !(r < o.tol)) status = NBTE_ERR_NOT_CONVERGED;
+  // ---- moments of the last sweep: replay it with the energy/flux moments on
+  if (status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED) {
+    NBTE_CK(cudaMemsetAsync(S->accE.p, 0, N * 8, st));
+    NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
+    launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
+    NBTE_CK(launch_sweep<R>(sweep_args<R>(S, S->srcTQ_fin.p, 1), S->K, S->bpt, S->lanes, S->n_items, S->threads,
+                            S->smem, st));
+    WallHeatArgs<R> wh{};
+    wh.Bp = S->Bp;
+    wh.n_wf = S->n_wf;
+    wh.wf_ptr = S->wf_ptr.as<int64_t>();
+    wh.wf_val = S->wf_val.as<int64_t>();
+    wh.wf_coef = S->wf_coef.as<double>();
+    wh.exp = S->expt.as<R>();
+    wh.imp = S->impt.as<R>();
+    wh.band_v = S->band_v64.as<double>();
+    wh.heat = S->heat.as<double>();
+    launch_wall_heat<R>(wh, st);
+    NBTE_CK(cudaGetLastError());
+    S->wall_heat_by_face.assign(S->n_wf, 0.0);
+    NBTE_CK(cudaMemcpyAsync(S->wall_heat_by_face.data(), S->heat.p, S->n_wf * 8, cudaMemcpyDeviceToHost, st));
+    NBTE_CK(cudaStreamSynchronize(st));
+    S->have_results = true;
+    // energy balance (FP64)
+    std::map<int32_t, int> type;
+    for (auto& b : S->bcs) type[b.tag] = b.type;
+    double therm = 0, absall = 0, qtot = 0, qabs = 0;
+    for (int64_t f = 0; f < S->n_wf; ++f) {
+      absall += std::fabs(S->wall_heat_by_face[f]);
+      if (type[S->wf_tag_h[f]] == NBTE_THERMALIZING) therm += S->wall_heat_by_face[f];
+    }
+    for (int64_t c = 0; c < N; ++c) {
+      qtot += S->Q[c] * m.V[c];
+      qabs += std::fabs(S->Q[c] * m.V[c]);
+    }
+    S->last_energy_imbalance = std::fabs(therm - qtot) / std::max(std::max(qabs, absall), 1e-300);
+  }
+  if (info) {
+    info->iterations = it;
+    info->residual = r;
+    info->energy_imbalance = S->last_energy_imbalance;
+    info->lagged_faces = S->lagged;
+    info->seconds = std::chrono::duration<double>(t1 - t0).count();
+    int32_t cgi = 0;
+    if (S->cg_it.p) cudaMemcpy(&cgi, S->cg_it.p, 4, cudaMemcpyDeviceToHost);
+    info->cg_iterations = cgi;
+  }
+  return status;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* nbte_last_error(void) { return g_err.c_str(); }
+const char* nbte_version(void) { return "nanobte-b300 1.0 (sm_103a)"; }
+
+int nbte_mesh_create(int dim, int64_t n_nodes, const double* xyz, int cell_type, int64_t n_cells,
+                     const int64_t* cell_nodes, int64_t n_bfaces, const int64_t* bface_nodes,
+                     const int32_t* bface_tag, nbte_mesh** out) {
+  if (!out) return fail(NBTE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<nbte_mesh> M(new (std::nothrow) nbte_mesh());
+  if (!M) return fail(NBTE_ERR_OOM, "host allocation failed");
+  try {
+    Status st = build_mesh(dim, n_nodes, xyz, cell_type, n_cells, cell_nodes, n_bfaces, bface_nodes, bface_tag, M->m);
+    if (!st.good()) return fail(st.code, st.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(NBTE_ERR_OOM, "host allocation failed while building the mesh");
+  }
+  *out = M.release();
+  return NBTE_OK;
+}
+
+int nbte_mesh_destroy(nbte_mesh* mesh) {
+  delete mesh;
+  return NBTE_OK;
+}
+
+int nbte_mesh_info(const nbte_mesh* mesh, int64_t* n_cells, double* volume) {
+  if (!mesh) return fail(NBTE_ERR_ARG, "mesh is NULL");
+  if (n_cells) *n_cells = mesh->m.n_cells;
+  if (volume) *volume = mesh->m.volume;
+  return NBTE_OK;
+}
+
+int nbte_solver_create(const nbte_mesh* mesh, double T_ref, nbte_solver** out) {
+  if (!out) return fail(NBTE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh) return fail(NBTE_ERR_ARG, "mesh is NULL");
+  if (!std::isfinite(T_ref) || T_ref <= 0) return fail(NBTE_ERR_ARG, "T_ref must be a positive temperature");
+  std::unique_ptr<nbte_solver> S(new (std::nothrow) nbte_solver());
+  if (!S) return fail(NBTE_ERR_OOM, "host allocation failed");
+  S->mesh = mesh;
+  S->T_ref = T_ref;
+  // bind to the current device now if there is one; the stream and pinned
+  // words are created on first device use, so argument checks of the set-up
+  // calls work on a host without a GPU
+  if (cudaGetDevice(&S->device) != cudaSuccess) {
+    cudaGetLastError();
+    S->device = -1;
+  }
+  *out = S.release();
+  return NBTE_OK;
+}
+
+static int ensure_device(nbte_solver* S) {
+  if (S->device < 0) {
+    NBTE_CK(cudaGetDevice(&S->device));
+  }
+  if (!S->own_stream) {
+    DeviceGuard g(S->device);
+    NBTE_CK(cudaStreamCreateWithFlags(&S->own_stream, cudaStreamNonBlocking));
+    if (!S->stream) S->stream = S->own_stream;
+    NBTE_CK(cudaMallocHost(&S->h_res, 16));
+    NBTE_CK(cudaMallocHost(&S->h_misc, 16));
+    S->h_misc[0] = 0;
+  }
+  return NBTE_OK;
+}
+
+int nbte_solver_destroy(nbte_solver* solver) {
+  if (!solver) return NBTE_OK;
+  if (solver->device >= 0) {
+    DeviceGuard g(solver->device);
+    if (solver->stream) cudaStreamSynchronize(solver->stream);
+    delete solver;
+  } else {
+    delete solver;
+  }
+  return NBTE_OK;
+}
+
+int nbte_solver_set_stream(nbte_solver* S, void* cuda_stream) {
+  if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
+  int rc = ensure_device(S);
+  if (rc) return rc;
+  S->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : S->own_stream;
+  drop_graph(S);
+  return NBTE_OK;
+}
+
+int nbte_set_bands(nbte_solver* S, int n_bands, const double* C, const double* v, const double* tau) {
+  if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
+  if (n_bands <= 0 || n_bands > 4096) return fail(NBTE_ERR_ARG, "n_bands must be in [1, 4096]");
+  if (!C || !v || !tau) return fail(NBTE_ERR_ARG, "null band array");
+  for (int l = 0; l < n_bands; ++l)
+    if (!(std::isfinite(C[l]) && C[l] > 0 && std::isfinite(v[l]) && v[l] > 0 && std::isfinite(tau[l]) && tau[l] > 0))
+      return fail(NBTE_ERR_ARG, "band " + std::to_string(l) + ": C, v and tau must be positive and finite");
+  S->B = n_bands;
+  S->C.assign(C, C + n_bands);
+  S->v.assign(v, v + n_bands);
+  S->tau.assign(tau, tau + n_bands);
+  S->version_bands++;
+  S->have_results = false;
+  return NBTE_OK;
+}
+
+int nbte_set_quadrature(nbte_solver* S, int n_dirs, const double* s, const double* w) {
+  if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
+  if (n_dirs <= 0 || n_dirs > 100000) return fail(NBTE_ERR_ARG, "n_dirs must be in [1, 100000]");
+  if (!s || !w) return fail(NBTE_ERR_ARG, "null quadrature array");
+  for (int i = 0; i < n_dirs; ++i) {
+    const double n2 = s[3 * i] * s[3 * i] + s[3 * i + 1] * s[3 * i + 1] + s[3 * i + 2] * s[3 * i + 2];
+    if (!std::isfinite(n2) || std::fabs(std::sqrt(n2) - 1.0) > 1e-9)
+      return fail(NBTE_ERR_ARG, "direction " + std::to_string(i) + " is not a unit vector");
+    if (!(std::isfinite(w[i]) && w[i] > 0)) return fail(NBTE_ERR_ARG, "weights must be positive and finite");
+  }
+  S->D = n_dirs;
+  S->s.assign(s, s + 3 * n_dirs);
+  S->w.assign(w, w + n_dirs);
+  S->version_plan++;
+  S->have_results = false;
+  return NBTE_OK;
+}
+
+int nbte_set_boundaries(nbte_solver* S, int n, const nbte_boundary* bcs) {
+  if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
+  if (n <= 0 || !bcs) return fail(NBTE_ERR_ARG, "at least one boundary condition is required");
+  std::vector<BC> v;
+  bool therm = false;
+  for (int k = 0; k < n; ++k) {
+    const nbte_boundary& b = bcs[k];
+    if (b.type < NBTE_THERMALIZING || b.type > NBTE_PARTIAL) return fail(NBTE_ERR_ARG, "unknown boundary type");
+    for (auto& x : v)
+      if (x.tag == b.tag) return fail(NBTE_ERR_ARG, "tag " + std::to_string(b.tag) + " given twice");
+    if (b.type == NBTE_THERMALIZING && !(std::isfinite(b.T_wall) && b.T_wall > 0))
+      return fail(NBTE_ERR_ARG, "thermalizing wall needs a positive T_wall");
+    if (b.type == NBTE_PARTIAL && !(b.specularity >= 0.0 && b.specularity <= 1.0))
+      return fail(NBTE_ERR_ARG, "specularity must be in [0, 1]");
+    v.push_back({b.tag, b.type, b.T_wall, b.specularity});
+  }
+  for (int32_t t : S->mesh->m.tags_present) {
+    bool found = false;
+    for (auto& x : v) {
+      if (x.tag == t) {
+        found = true;
+        if (x.type == NBTE_THERMALIZING) therm = true;
+      }
+    }
+    if (!found) return fail(NBTE_ERR_ARG, "boundary tag " + std::to_string(t) + " has no condition");
+  }
+  if (!therm) return fail(NBTE_ERR_ARG, "no thermalizing wall: the steady problem has no unique solution");
+  S->bcs = v;
+  S->bcs_set = true;
+  S->version_plan++;
+  S->have_results = false;
+  return NBTE_OK;
+}
+
+int nbte_set_heat_source(nbte_solver* S, const double* Qdot) {
+  if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
+  const Mesh& m = S->mesh->m;
+  std::vector<double> q(m.n_cells, 0.0);
+  if (Qdot) {
+    for (int64_t c = 0; c < m.n_cells; ++c) {
+      const double x = Qdot[m.perm[c]];
+      if (!std::isfinite(x)) return fail(NBTE_ERR_ARG, "non-finite heat source");
+      q[c] = x;
+    }
+  }
+  S->Q.swap(q);
+  S->version_q++;
+  S->have_results = false;
+  return NBTE_OK;
+}
+
+int nbte_default_opts(nbte_solve_opts* o) {
+  if (!o) return fail(NBTE_ERR_ARG, "opts is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->scheme = 0;
+  o->precision = 0;
+  o->tol = 1e-10;
+  o->max_iter = 10000;
+  return NBTE_OK;
+}
+
+static int check_opts(const nbte_solve_opts& o) {
+  if (o.scheme < 0 || o.scheme > 2) return fail(NBTE_ERR_ARG, "scheme must be 0, 1 or 2");
+  if (o.precision < 0 || o.precision > 1) return fail(NBTE_ERR_ARG, "precision must be 0 or 1");
+  if (o.n_iter < 0) return fail(NBTE_ERR_ARG, "n_iter must be >= 0");
+  if (o.n_iter == 0 && !(o.tol > 0 && std::isfinite(o.tol))) return fail(NBTE_ERR_ARG, "tol must be positive");
+  if (o.n_iter == 0 && o.max_iter <= 0) return fail(NBTE_ERR_ARG, "max_iter must be positive");
+  return NBTE_OK;
+}
+
+int nbte_plan_stats(nbte_solver* S, const nbte_solve_opts* opts, int64_t stats[8]) {
+  if (!S || !stats) return fail(NBTE_ERR_ARG, "null argument");
+  nbte_solve_opts o;
+  nbte_default_opts(&o);
+  if (opts) o = *opts;
+  int rc = check_opts(o);
+  if (rc) return rc;
+  rc = ensure_device(S);
+  if (rc) return rc;
+  DeviceGuard g(S->device);
+  rc = ensure_plan(S);
+  if (rc) return rc;
+  rc = ensure_layout(S, o);
+  if (rc) return rc;
+  stats[0] = S->total_levels;
+  stats[1] = S->max_levels;
+  stats[2] = S->max_slots;
+  stats[3] = S->lagged;
+  stats[4] = S->n_items;
+  stats[5] = S->G;
+  stats[6] = S->lanes;
+  stats[7] = (int64_t)device_bytes(S);
+  return NBTE_OK;
+}
+
+int nbte_solve_steady(nbte_solver* S, const nbte_solve_opts* opts, nbte_solve_info* info) {
+  if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
+  nbte_solve_opts o;
+  nbte_default_opts(&o);
+  if (opts) o = *opts;
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (S->B <= 0) return fail(NBTE_ERR_STATE, "nbte_set_bands must be called before solving");
+  if (S->D <= 0) return fail(NBTE_ERR_STATE, "nbte_set_quadrature must be called before solving");
+  if (!S->bcs_set) return fail(NBTE_ERR_STATE, "nbte_set_boundaries must be called before solving");
+  rc = ensure_device(S);
+  if (rc) return rc;
+  DeviceGuard g(S->device);
+  try {
+    rc = ensure_plan(S);
+    if (rc) return rc;
+    rc = ensure_layout(S, o);
+    if (rc) return rc;
+    if (S->version_q != -2) {
+      rc = ensure_q(S);
+      if (rc) return rc;
+    }
+    if (o.scheme != 0) {
+      rc = ensure_laplacian(S);
+      if (rc) return rc;
+    }
+    return S->prec ? run_solve<float>(S, o, info) : run_solve<double>(S, o, info);
+  } catch (const std::bad_alloc&) {
+    return fail(NBTE_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(NBTE_ERR_ARG, e.what());
+  }
+}
+
+int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
+  if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
+  if (!S->have_results) return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
+  if (kind < 0 || kind > 2) return fail(NBTE_ERR_ARG, "kind must be 0, 1 or 2");
+  DeviceGuard g(S->device);
+  const Mesh& m = S->mesh->m;
+  const int64_t N = m.n_cells;
+  std::vector<double> tmp(N);
+  const DBuf& src = kind == 0 ? S->T : (kind == 1 ? S->accE : S->Tkin);
+  NBTE_CK(cudaStreamSynchronize(S->stream));
+  NBTE_CK(cudaMemcpy(tmp.data(), src.p, N * 8, cudaMemcpyDeviceToHost));
+  for (int64_t c = 0; c < N; ++c) {
+    const double t = kind == 1 ? tmp[c] / S->Ctot : tmp[c];
+    out[m.perm[c]] = t + S->T_ref;
+  }
+  return NBTE_OK;
+}
+
+int nbte_get_heat_flux(const nbte_solver* S, double* out) {
+  if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
+  if (!S->have_results) return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
+  DeviceGuard g(S->device);
+  const Mesh& m = S->mesh->m;
+  const int64_t N = m.n_cells;
+  std::vector<double> tmp((size_t)N * m.dim);
+  NBTE_CK(cudaStreamSynchronize(S->stream));
+  NBTE_CK(cudaMemcpy(tmp.data(), S->accQ.p, tmp.size() * 8, cudaMemcpyDeviceToHost));
+  for (int64_t c = 0; c < N; ++c)
+    for (int d = 0; d < m.dim; ++d) out[m.perm[c] * m.dim + d] = tmp[c * m.dim + d];
+  return NBTE_OK;
+}
+
+int nbte_get_wall_heat(const nbte_solver* S, int32_t tag, double* out) {
+  if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
+  if (!S->have_results) return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
+  double h = 0;
+  bool found = false;
+  for (size_t f = 0; f < S->wall_heat_by_face.size(); ++f)
+    if (S->wf_tag_h[f] == tag) { h += S->wall_heat_by_face[f]; found = true; }
+  if (!found) return fail(NBTE_ERR_ARG, "no boundary face carries tag " + std::to_string(tag));
+  *out = h;
+  return NBTE_OK;
+}
+
+}  // extern "C"

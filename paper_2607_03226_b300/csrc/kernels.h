@@ -1,0 +1,134 @@
+// Launch interface of the device kernels (internal; no torch types).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace nbte {
+
+// device error word values (written by bounded waits, read by the host)
+enum DevError : int32_t { DEV_OK = 0, DEV_BARRIER_TIMEOUT = 1, DEV_QUEUE_TIMEOUT = 2 };
+
+template <typename R>
+struct SweepArgs {
+  int N, Bp, G, n_groups, dim;
+  int full;                      // also accumulate E and q (atomics)
+  const int32_t* item_dir;       // [n_items]
+  const int32_t* item_grp;       // [n_items]
+  const int64_t* lvl_off;        // [D+1]
+  const int32_t* level_ptr;
+  const int32_t* pos_cell;       // [D*N]
+  const int32_t* pos_slot;
+  const int32_t* pos_exp;
+  const R* pos_G;
+  const int32_t* pos_ref;        // [D*K*N]
+  const R* pos_coef;
+  const int64_t* exp_off;        // [D+1]
+  const int64_t* imp_off;
+  const R* imp;                  // [n_imp*Bp]
+  R* exp;                        // [n_exp*Bp]
+  const R* srcTQ;                // [2*N] (T', Qdot) per cell
+  const R* band_v;               // [Bp]
+  const R* band_inv_tau;
+  const R* band_aT;              // C / (W tau)
+  const R* band_aQ;              // C / (C_tot W)
+  const double* dir_w;           // [D]
+  const double* dir_s;           // [D*3]
+  double* part;                  // [n_items*N] collision-moment partials
+  double* accE;                  // [N]   (full)
+  double* accQ;                  // [N*dim] (full)
+};
+
+template <typename R>
+cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int bpt, int lanes, int n_items, int threads,
+                  size_t smem, cudaStream_t st);
+
+template <typename R>
+void launch_init_exports(R* exp, const int32_t* exp_cell, const double* Tdev, const double* CoW, int Bp,
+                         int64_t n_exp, cudaStream_t st);
+
+template <typename R>
+struct WallArgs {
+  int Bp;
+  int64_t n_imp, n_dbf;
+  const R* exp;
+  R* imp;
+  const int32_t* exp_cell;
+  const double* Delta;           // [N] synthetic correction carried by lagged values
+  const double* CoW;             // [Bp] C / W
+  const int32_t* imp_kind;
+  const int32_t* imp_dbf;
+  const int64_t* imp_src;
+  const double* imp_par;
+  const int64_t* dif_ptr;
+  const int64_t* dif_src;
+  const double* dif_wt;
+  double* dsum;                  // [n_dbf*Bp]
+};
+template <typename R>
+void launch_walls(const WallArgs<R>& a, cudaStream_t st);
+
+// collision-moment reduction + temperature update
+template <typename R>
+struct UpdateArgs {
+  int N, n_items;
+  int mode;                      // 0 sequential, 1 synthetic (DSA), 2 synthetic (literal), 3 rhs only
+  double inv_beta, beta;
+  const double* part;
+  const double* Q;
+  const double* V;
+  double* T;                     // T' iterate (in/out)
+  double* Tkin;                  // kinetic T'_L of this sweep
+  double* Delta;                 // T'^{n+1} - T'_L
+  double* rhs;                   // synthetic right-hand side
+  const double* delta;           // synthetic correction
+  R* srcTQ_next;                 // [2*N]
+  unsigned long long* res;       // [2] max |dT|, max |T'| (as ordered bits)
+};
+template <typename R>
+void launch_update(const UpdateArgs<R>& a, cudaStream_t st);
+
+struct CGArgs {
+  int N;
+  const int32_t* rp;
+  const int32_t* col;
+  const double* val;
+  const double* dinv;
+  const double* b;
+  double* x;
+  double* r;
+  double* z;
+  double* p;
+  double* Ap;
+  double* partial;               // [3*grid]
+  unsigned* bar;                 // [2] count, generation
+  int32_t* err;
+  double tol;
+  int max_it;
+  int32_t* it_out;
+  double* res_out;
+};
+// persistent cooperative PCG; returns cudaError of the launch
+cudaError_t launch_cg(const CGArgs& a, int grid, cudaStream_t st);
+int cg_max_grid(int device);
+
+template <typename R>
+struct WallHeatArgs {
+  int Bp;
+  int64_t n_wf;
+  const int64_t* wf_ptr;
+  const int64_t* wf_val;
+  const double* wf_coef;
+  const R* exp;
+  const R* imp;
+  const double* band_v;          // [Bp] FP64
+  double* heat;                  // [n_wf]
+};
+template <typename R>
+void launch_wall_heat(const WallHeatArgs<R>& a, cudaStream_t st);
+
+template <typename R>
+void launch_fill_srcTQ(R* srcTQ, const double* T, const double* Q, int N, cudaStream_t st);
+
+}  // namespace nbte

@@ -1,0 +1,103 @@
+// Internal structures of libnanobte (host side).  Not part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "nbte.h"
+
+namespace nbte {
+
+void set_error(const std::string& msg);
+
+struct Status {
+  int code = NBTE_OK;
+  std::string msg;
+  static Status ok() { return {}; }
+  static Status err(int c, std::string m) { return {c, std::move(m)}; }
+  bool good() const { return code == NBTE_OK; }
+};
+
+// Finite-volume mesh in the library's internal cell order (space-filling
+// curve).  Half-face h = c * nfc + k is local face k of internal cell c.
+struct Mesh {
+  int dim = 0, cell_type = 0;
+  int nvc = 0;   // nodes per cell
+  int nfc = 0;   // faces per cell
+  int nvf = 0;   // nodes per face
+  int64_t n_nodes = 0, n_cells = 0, n_bfaces = 0;
+  std::vector<int64_t> perm;    // internal -> caller cell index
+  std::vector<int64_t> iperm;   // caller -> internal
+  std::vector<double> V;        // [N]
+  std::vector<double> xc;       // [N*dim]
+  std::vector<int64_t> nb;      // [N*nfc] neighbour (internal) or -1
+  std::vector<int64_t> twin;    // [N*nfc] matching half-face of the neighbour or -1
+  std::vector<double> An;       // [N*nfc*dim] outward area vectors
+  std::vector<double> xf;       // [N*nfc*dim] face centroids
+  std::vector<int32_t> tag;     // [N*nfc] boundary tag (valid when nb < 0)
+  std::vector<int32_t> tags_present;
+  double volume = 0.0;
+};
+
+Status build_mesh(int dim, int64_t n_nodes, const double* xyz, int cell_type, int64_t n_cells,
+                  const int64_t* cell_nodes, int64_t n_bfaces, const int64_t* bface_nodes,
+                  const int32_t* bface_tag, Mesh& m);
+
+// ------------------------------------------------------------------ plan --
+// Import entry kinds (values a sweep reads from outside its direction's DAG).
+enum ImportKind : int32_t { IMP_THERM = 0, IMP_DIFFUSE = 1, IMP_SPECULAR = 2, IMP_PARTIAL = 3, IMP_LAG = 4 };
+
+struct Plan {
+  int D = 0, N = 0, K = 0;                 // directions, cells, inflow entries per cell
+  std::vector<int64_t> lvl_off;            // [D+1] offsets into level_ptr
+  std::vector<int32_t> level_ptr;          // per direction: n_levels+1 positions
+  std::vector<int32_t> n_slots;            // [D] ring slots used (excluding the zero slot)
+  std::vector<int32_t> max_width;          // [D] widest level (cells)
+  // position records, direction-major, N per direction
+  std::vector<int32_t> pos_cell, pos_slot, pos_exp;   // [D*N]
+  std::vector<double> pos_G;                          // [D*N]
+  std::vector<int32_t> pos_ref;                       // [D*K*N]
+  std::vector<double> pos_coef;                       // [D*K*N]
+  // exports (values the sweep writes) and imports (values it reads)
+  std::vector<int64_t> exp_off, imp_off;    // [D+1]
+  std::vector<int32_t> exp_cell;            // [n_exp]
+  std::vector<int32_t> imp_kind;            // [n_imp]
+  std::vector<int32_t> imp_dbf;             // [n_imp] diffuse-face index (diffuse/partial)
+  std::vector<int64_t> imp_src;             // [n_imp] export index (specular/partial/lag)
+  std::vector<double> imp_par;              // [n_imp] T_wall' (therm) or p (partial)
+  // diffuse re-emission: per diffuse/partial boundary half-face, CSR over the
+  // outgoing directions: export index and weight w_j (s_j.n) / sum_in w |s.n|
+  std::vector<int64_t> dif_ptr;             // [n_dbf+1]
+  std::vector<int64_t> dif_src;
+  std::vector<double> dif_wt;
+  // energy balance: per boundary half-face in the wall-flux table
+  std::vector<int32_t> wf_tag;              // [n_wf] tag of the face
+  std::vector<int32_t> wf_cell;             // [n_wf]
+  std::vector<int64_t> wf_ptr;              // [n_wf+1] CSR over directions
+  std::vector<int64_t> wf_val;              // export index (>=0) or -(1+import index)
+  std::vector<double> wf_coef;              // w_i (s_i . An) (signed)
+  int64_t lagged_faces = 0;
+  int64_t total_levels = 0;
+  int max_levels = 0, max_slots = 0, max_width_all = 0;
+};
+
+struct BC {
+  int32_t tag;
+  int32_t type;
+  double T_wall;
+  double p;
+};
+
+Status build_plan(const Mesh& m, int D, const double* s, const double* w, const std::vector<BC>& bcs,
+                  double T_ref, Plan& plan, int n_threads);
+
+// TPFA Laplacian of the synthetic correction (CSR, internal cell order).
+struct Laplacian {
+  std::vector<int32_t> row_ptr, col;
+  std::vector<double> val, diag;
+};
+void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bulk, double k1,
+                     Laplacian& L);
+
+}  // namespace nbte

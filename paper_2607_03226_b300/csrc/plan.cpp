@@ -1,0 +1,491 @@
+// Direction planner: everything about a (mesh, direction set, walls) that does
+// not change between outer iterations -- "precompute what is
+// iteration-independent" (Sec. II, after Eq. (13)).
+//
+// For every direction i the first-order upwind system I/tau + v K_i of
+// Eq. (13) is lower-triangular in a topological order of the upwind graph
+// (edge u -> c when a face of c has s_i . An < 0 and u is across it), so its
+// LU factorisation is the graph order itself and "triangular substitution" is
+// a sweep.  The planner computes, per direction:
+//
+//  * Kahn levels of the upwind graph: cells of one level depend only on
+//    earlier levels.  If no cell is ready (a cycle, possible on unstructured
+//    3D meshes) the lowest-numbered unprocessed cell is released and its
+//    inflow faces from unprocessed cells are marked "lagged": their upwind
+//    value is taken from the previous iteration.  Structured and 2D meshes
+//    have none.
+//  * ring slots: a cell's value lives in shared memory from its own level to
+//    the last level that reads it; slots are reused (interval colouring), so
+//    a sweep needs only max-live-cells slots, not N.
+//  * per-position records (cell, slot, diagonal G, inflow references and
+//    coefficients |s.An|/V), in level order.
+//  * exports (cells whose value is needed after the sweep: outgoing wall
+//    faces and lagged upstream cells) and imports (wall and lagged inflow
+//    values read by the sweep), with everything the wall kernel needs to
+//    turn exports into imports.
+#include <algorithm>
+#include <array>
+#include <climits>
+#include <cmath>
+#include <map>
+#include <thread>
+
+#include "nbte_internal.h"
+
+namespace nbte {
+
+namespace {
+
+struct LocalImport {
+  int32_t kind;
+  int32_t dbf;        // diffuse face index
+  int32_t src_dir;    // export direction (specular / partial / lag)
+  int32_t src_cell;   // export cell
+  double par;
+};
+
+struct DirOut {
+  std::vector<int32_t> lp;          // level pointer
+  int32_t n_slots = 0, max_width = 0;
+  int64_t lagged = 0;
+  std::vector<int32_t> exp_cells;   // sorted
+  std::vector<LocalImport> imps;
+  std::vector<std::pair<int64_t, int32_t>> bimp;  // (boundary half-face, local import), sorted
+  std::string error;
+};
+
+constexpr double kTangent = 1e-12;   // |s.An| <= kTangent |An| counts as no flux
+
+}  // namespace
+
+Status build_plan(const Mesh& m, int D, const double* s, const double* w, const std::vector<BC>& bcs,
+                  double T_ref, Plan& P, int n_threads) {
+  const int dim = m.dim, nfc = m.nfc;
+  const int64_t N = m.n_cells, H = N * nfc;
+  P = Plan();
+  P.D = D;
+  P.N = (int)N;
+  // inflow entries per cell: at most nfc - 1 faces of a closed convex cell
+  // face a given direction
+  P.K = nfc - 1;
+  const int K = P.K;
+
+  std::map<int32_t, BC> bcmap;
+  for (auto& b : bcs) bcmap[b.tag] = b;
+
+  // boundary half-faces, their unit normals and diffuse-face numbering
+  std::vector<int64_t> bhf;
+  for (int64_t h = 0; h < H; ++h)
+    if (m.nb[h] < 0) bhf.push_back(h);
+  std::vector<int32_t> dbf_of_h(H, -1);
+  std::vector<int64_t> dbf_h;
+  for (int64_t h : bhf) {
+    const BC& b = bcmap.at(m.tag[h]);
+    if (b.type == NBTE_DIFFUSE || b.type == NBTE_PARTIAL) {
+      dbf_of_h[h] = (int32_t)dbf_h.size();
+      dbf_h.push_back(h);
+    }
+  }
+  auto unit_normal = [&](int64_t h, double n[3]) {
+    double a = 0;
+    for (int d = 0; d < dim; ++d) a += m.An[h * dim + d] * m.An[h * dim + d];
+    a = std::sqrt(a);
+    n[0] = n[1] = n[2] = 0;
+    for (int d = 0; d < dim; ++d) n[d] = m.An[h * dim + d] / a;
+  };
+  auto dotsa = [&](int i, int64_t h) {
+    double a = 0;
+    for (int d = 0; d < dim; ++d) a += s[i * 3 + d] * m.An[h * dim + d];
+    return a;
+  };
+  std::vector<double> area(H);
+  for (int64_t h = 0; h < H; ++h) {
+    double a = 0;
+    for (int d = 0; d < dim; ++d) a += m.An[h * dim + d] * m.An[h * dim + d];
+    area[h] = std::sqrt(a);
+  }
+  auto cls = [&](double a, int64_t h) { return a > kTangent * area[h] ? 1 : (a < -kTangent * area[h] ? -1 : 0); };
+
+  // mirror maps, cached per distinct normal: R[i] = direction nearest to
+  // s_i - 2 (s_i . n) n among those leaving through the face
+  std::map<std::array<long long, 3>, std::vector<int32_t>> mirror_cache;
+  auto mirror_map = [&](int64_t h) -> const std::vector<int32_t>& {
+    double n[3];
+    unit_normal(h, n);
+    std::array<long long, 3> key = {std::llround(n[0] * 1e12), std::llround(n[1] * 1e12), std::llround(n[2] * 1e12)};
+    auto it = mirror_cache.find(key);
+    if (it != mirror_cache.end()) return it->second;
+    std::vector<int32_t> R(D);
+    for (int i = 0; i < D; ++i) {
+      const double sn = s[i * 3] * n[0] + s[i * 3 + 1] * n[1] + s[i * 3 + 2] * n[2];
+      double mir[3];
+      for (int d = 0; d < 3; ++d) mir[d] = s[i * 3 + d] - 2.0 * sn * n[d];
+      int best = -1;
+      double bd = 1e300;
+      for (int j = 0; j < D; ++j) {
+        const double sj = s[j * 3] * n[0] + s[j * 3 + 1] * n[1] + s[j * 3 + 2] * n[2];
+        if (!(sj > kTangent)) continue;   // must leave through the wall
+        double dd = 0;
+        for (int d = 0; d < 3; ++d) dd += (s[j * 3 + d] - mir[d]) * (s[j * 3 + d] - mir[d]);
+        if (dd < bd) { bd = dd; best = j; }
+      }
+      R[i] = best;
+    }
+    return mirror_cache.emplace(key, std::move(R)).first->second;
+  };
+  // fill the cache serially (it is read by the worker threads)
+  for (int64_t h : bhf) {
+    const BC& b = bcmap.at(m.tag[h]);
+    if (b.type == NBTE_SPECULAR || b.type == NBTE_PARTIAL) mirror_map(h);
+  }
+
+  P.pos_cell.assign((size_t)D * N, 0);
+  P.pos_slot.assign((size_t)D * N, -1);
+  P.pos_exp.assign((size_t)D * N, -1);
+  P.pos_G.assign((size_t)D * N, 0.0);
+  P.pos_ref.assign((size_t)D * K * N, 0);
+  P.pos_coef.assign((size_t)D * K * N, 0.0);
+  std::vector<DirOut> outs(D);
+
+  auto work = [&](int tid, int nt) {
+    std::vector<int32_t> indeg(N), level(N), slot(N), last_use(N), exp_local(N);
+    std::vector<char> lagged(H);
+    std::vector<int32_t> order, cur, next, free_slots;
+    std::vector<std::vector<int32_t>> release;
+    for (int i = tid; i < D; i += nt) {
+      DirOut& o = outs[i];
+      std::fill(indeg.begin(), indeg.end(), 0);
+      std::fill(level.begin(), level.end(), -1);
+      std::fill(lagged.begin(), lagged.end(), 0);
+      for (int64_t c = 0; c < N; ++c)
+        for (int k = 0; k < nfc; ++k) {
+          const int64_t h = c * nfc + k;
+          if (m.nb[h] >= 0 && cls(dotsa(i, h), h) < 0) indeg[c]++;
+        }
+      // ---- Kahn levels with deterministic cycle breaking
+      order.clear();
+      cur.clear();
+      o.lp.assign(1, 0);
+      for (int64_t c = 0; c < N; ++c)
+        if (indeg[c] == 0) cur.push_back((int32_t)c);
+      int64_t processed = 0, scan = 0;
+      while (processed < N) {
+        if (cur.empty()) {
+          while (level[scan] >= 0) ++scan;
+          const int64_t c = scan;
+          for (int k = 0; k < nfc; ++k) {
+            const int64_t h = c * nfc + k;
+            if (m.nb[h] >= 0 && level[m.nb[h]] < 0 && cls(dotsa(i, h), h) < 0) {
+              lagged[h] = 1;
+              o.lagged++;
+            }
+          }
+          indeg[c] = 0;
+          cur.push_back((int32_t)c);
+        }
+        const int32_t lev = (int32_t)o.lp.size() - 1;
+        for (int32_t c : cur) {
+          level[c] = lev;
+          order.push_back(c);
+        }
+        processed += (int64_t)cur.size();
+        o.max_width = std::max(o.max_width, (int32_t)cur.size());
+        o.lp.push_back((int32_t)order.size());
+        next.clear();
+        for (int32_t u : cur)
+          for (int k = 0; k < nfc; ++k) {
+            const int64_t h = (int64_t)u * nfc + k;
+            const int64_t v = m.nb[h];
+            if (v < 0 || cls(dotsa(i, h), h) <= 0) continue;
+            if (level[v] >= 0) continue;   // edge into an already released cell: lagged
+            if (--indeg[v] == 0) next.push_back((int32_t)v);
+          }
+        std::sort(next.begin(), next.end());
+        cur.swap(next);
+      }
+      const int L = (int)o.lp.size() - 1;
+      // ---- push producers down to just before their first consumer (as
+      // late as possible), visiting cells in reverse level order: a value then
+      // lives in the ring for fewer levels, and the dependency order is kept
+      // because every consumer's final level is already fixed
+      {
+        for (int64_t p = N - 1; p >= 0; --p) {
+          const int32_t u = order[p];
+          int32_t first = INT32_MAX;
+          for (int k = 0; k < nfc; ++k) {
+            const int64_t h = (int64_t)u * nfc + k;
+            const int64_t v = m.nb[h];
+            if (v < 0 || cls(dotsa(i, h), h) <= 0 || lagged[m.twin[h]]) continue;
+            first = std::min(first, level[v]);
+          }
+          if (first != INT32_MAX && first - 1 > level[u]) level[u] = first - 1;
+        }
+        // rebuild the level lists (stable in cell index within a level)
+        std::vector<int32_t> cnt(L + 1, 0);
+        for (int64_t c = 0; c < N; ++c) cnt[level[c] + 1]++;
+        for (int l = 0; l < L; ++l) cnt[l + 1] += cnt[l];
+        for (int l = 0; l <= L; ++l) o.lp[l] = cnt[l];
+        for (int64_t c = 0; c < N; ++c) order[cnt[level[c]]++] = (int32_t)c;
+        o.max_width = 0;
+        for (int l = 0; l < L; ++l) o.max_width = std::max(o.max_width, o.lp[l + 1] - o.lp[l]);
+      }
+      // ---- ring slots
+      std::fill(last_use.begin(), last_use.end(), -1);
+      for (int64_t c = 0; c < N; ++c)
+        for (int k = 0; k < nfc; ++k) {
+          const int64_t h = c * nfc + k;
+          const int64_t v = m.nb[h];
+          if (v < 0 || cls(dotsa(i, h), h) <= 0) continue;
+          if (lagged[m.twin[h]]) continue;
+          last_use[c] = std::max(last_use[c], level[v]);
+        }
+      release.assign(L + 1, {});
+      for (int64_t c = 0; c < N; ++c)
+        if (last_use[c] >= 0) release[last_use[c] + 1 <= L ? last_use[c] + 1 : L].push_back((int32_t)c);
+      free_slots.clear();
+      int32_t next_new = 1;   // slot 0 is the permanent zero slot
+      for (int l = 0; l < L; ++l) {
+        for (int32_t c : release[l]) free_slots.push_back(slot[c]);
+        for (int32_t p = o.lp[l]; p < o.lp[l + 1]; ++p) {
+          const int32_t c = order[p];
+          if (last_use[c] >= 0) {
+            if (!free_slots.empty()) {
+              slot[c] = free_slots.back();
+              free_slots.pop_back();
+            } else {
+              slot[c] = next_new++;
+            }
+          } else {
+            slot[c] = -1;
+          }
+        }
+      }
+      o.n_slots = next_new - 1;
+      // ---- exports: outgoing wall faces and upstream ends of lagged faces
+      std::fill(exp_local.begin(), exp_local.end(), -1);
+      o.exp_cells.clear();
+      std::vector<char> is_exp(N, 0);
+      for (int64_t h : bhf)
+        if (cls(dotsa(i, h), h) > 0) is_exp[h / nfc] = 1;
+      for (int64_t h = 0; h < H; ++h)
+        if (lagged[h]) is_exp[m.nb[h]] = 1;
+      for (int64_t c = 0; c < N; ++c)
+        if (is_exp[c]) {
+          exp_local[c] = (int32_t)o.exp_cells.size();
+          o.exp_cells.push_back((int32_t)c);
+        }
+      // ---- records in level order, imports on first use
+      o.imps.clear();
+      const size_t base = (size_t)i * N;
+      for (int32_t p = 0; p < (int32_t)N; ++p) {
+        const int32_t c = order[p];
+        P.pos_cell[base + p] = c;
+        P.pos_slot[base + p] = slot[c];
+        P.pos_exp[base + p] = exp_local[c];
+        double G = 0.0;
+        int kk = 0;
+        for (int k = 0; k < nfc; ++k) {
+          const int64_t h = (int64_t)c * nfc + k;
+          const double a = dotsa(i, h);
+          const int cl = cls(a, h);
+          if (cl > 0) {
+            G += a;
+            continue;
+          }
+          if (cl == 0) continue;
+          int32_t ref;
+          if (m.nb[h] >= 0 && !lagged[h]) {
+            ref = slot[m.nb[h]];
+            if (ref < 1) { o.error = "internal: upstream cell without a ring slot"; return; }
+          } else {
+            LocalImport im{};
+            if (m.nb[h] >= 0) {
+              im.kind = IMP_LAG;
+              im.src_dir = i;
+              im.src_cell = (int32_t)m.nb[h];
+            } else {
+              const BC& b = bcmap.at(m.tag[h]);
+              im.dbf = dbf_of_h[h];
+              if (b.type == NBTE_THERMALIZING) {
+                im.kind = IMP_THERM;
+                im.par = b.T_wall - T_ref;
+              } else if (b.type == NBTE_DIFFUSE) {
+                im.kind = IMP_DIFFUSE;
+              } else {
+                im.kind = b.type == NBTE_SPECULAR ? IMP_SPECULAR : IMP_PARTIAL;
+                im.par = b.p;
+                im.src_dir = mirror_cache.at([&] {
+                  double n[3];
+                  unit_normal(h, n);
+                  return std::array<long long, 3>{std::llround(n[0] * 1e12), std::llround(n[1] * 1e12),
+                                                  std::llround(n[2] * 1e12)};
+                }())[i];
+                im.src_cell = c;
+                if (im.src_dir < 0) { o.error = "no direction leaves through a specular wall"; return; }
+              }
+            }
+            ref = -(1 + (int32_t)o.imps.size());
+            if (m.nb[h] < 0) o.bimp.emplace_back(h, (int32_t)o.imps.size());
+            o.imps.push_back(im);
+          }
+          if (kk >= K) { o.error = "internal: more inflow faces than K"; return; }
+          P.pos_ref[((size_t)i * K + kk) * N + p] = ref;
+          P.pos_coef[((size_t)i * K + kk) * N + p] = -a / m.V[c];
+          ++kk;
+        }
+        P.pos_G[base + p] = G / m.V[c];
+      }
+      std::sort(o.bimp.begin(), o.bimp.end());
+    }
+  };
+  n_threads = std::max(1, std::min(n_threads, D));
+  std::vector<std::thread> th;
+  for (int t = 1; t < n_threads; ++t) th.emplace_back(work, t, n_threads);
+  work(0, n_threads);
+  for (auto& t : th) t.join();
+  for (auto& o : outs)
+    if (!o.error.empty()) return Status::err(NBTE_ERR_MESH, o.error);
+
+  // ---- flatten per-direction results
+  P.lvl_off.assign(D + 1, 0);
+  P.exp_off.assign(D + 1, 0);
+  P.imp_off.assign(D + 1, 0);
+  P.n_slots.resize(D);
+  P.max_width.resize(D);
+  for (int i = 0; i < D; ++i) {
+    const DirOut& o = outs[i];
+    P.lvl_off[i + 1] = P.lvl_off[i] + (int64_t)o.lp.size();
+    P.exp_off[i + 1] = P.exp_off[i] + (int64_t)o.exp_cells.size();
+    P.imp_off[i + 1] = P.imp_off[i] + (int64_t)o.imps.size();
+    P.n_slots[i] = o.n_slots;
+    P.max_width[i] = o.max_width;
+    P.lagged_faces += o.lagged;
+    const int L = (int)o.lp.size() - 1;
+    P.total_levels += L;
+    P.max_levels = std::max(P.max_levels, L);
+    P.max_slots = std::max(P.max_slots, o.n_slots);
+    P.max_width_all = std::max(P.max_width_all, o.max_width);
+  }
+  P.level_ptr.resize(P.lvl_off[D]);
+  P.exp_cell.resize(P.exp_off[D]);
+  for (int i = 0; i < D; ++i) {
+    std::copy(outs[i].lp.begin(), outs[i].lp.end(), P.level_ptr.begin() + P.lvl_off[i]);
+    std::copy(outs[i].exp_cells.begin(), outs[i].exp_cells.end(), P.exp_cell.begin() + P.exp_off[i]);
+  }
+  auto export_index = [&](int dir, int32_t cell) -> int64_t {
+    const auto& v = outs[dir].exp_cells;
+    auto it = std::lower_bound(v.begin(), v.end(), cell);
+    if (it == v.end() || *it != cell) return -1;
+    return P.exp_off[dir] + (it - v.begin());
+  };
+  const int64_t n_imp = P.imp_off[D];
+  P.imp_kind.resize(n_imp);
+  P.imp_dbf.resize(n_imp);
+  P.imp_src.resize(n_imp);
+  P.imp_par.resize(n_imp);
+  for (int i = 0; i < D; ++i)
+    for (size_t k = 0; k < outs[i].imps.size(); ++k) {
+      const LocalImport& im = outs[i].imps[k];
+      const int64_t x = P.imp_off[i] + (int64_t)k;
+      P.imp_kind[x] = im.kind;
+      P.imp_dbf[x] = im.dbf;
+      P.imp_par[x] = im.par;
+      P.imp_src[x] = -1;
+      if (im.kind == IMP_SPECULAR || im.kind == IMP_PARTIAL || im.kind == IMP_LAG) {
+        P.imp_src[x] = export_index(im.src_dir, im.src_cell);
+        if (P.imp_src[x] < 0) return Status::err(NBTE_ERR_MESH, "internal: missing export for a wall/lag import");
+      }
+    }
+
+  // ---- diffuse re-emission weights per diffuse/partial face
+  P.dif_ptr.assign(dbf_h.size() + 1, 0);
+  for (size_t f = 0; f < dbf_h.size(); ++f) {
+    const int64_t h = dbf_h[f];
+    double n[3];
+    unit_normal(h, n);
+    double denom = 0.0;
+    for (int j = 0; j < D; ++j) {
+      const double sn = s[j * 3] * n[0] + s[j * 3 + 1] * n[1] + s[j * 3 + 2] * n[2];
+      if (cls(dotsa(j, h), h) < 0) denom += w[j] * (-sn);
+    }
+    for (int j = 0; j < D; ++j) {
+      if (cls(dotsa(j, h), h) <= 0) continue;
+      const double sn = s[j * 3] * n[0] + s[j * 3 + 1] * n[1] + s[j * 3 + 2] * n[2];
+      const int64_t e = export_index(j, (int32_t)(h / nfc));
+      if (e < 0) return Status::err(NBTE_ERR_MESH, "internal: missing export for a diffuse wall");
+      P.dif_src.push_back(e);
+      P.dif_wt.push_back(w[j] * sn / denom);
+    }
+    P.dif_ptr[f + 1] = (int64_t)P.dif_src.size();
+  }
+
+  // ---- wall heat table: every boundary half-face, every non-tangent
+  // direction: the upwind value on the face (export when leaving, import when
+  // entering) and its weight w_i (s_i . An)
+  P.wf_ptr.assign(1, 0);
+  for (int64_t h : bhf) {
+    const int64_t c = h / nfc;
+    P.wf_tag.push_back(m.tag[h]);
+    P.wf_cell.push_back((int32_t)c);
+    for (int i = 0; i < D; ++i) {
+      const double a = dotsa(i, h);
+      const int cl = cls(a, h);
+      if (cl == 0) continue;
+      int64_t val;
+      if (cl > 0) {
+        val = export_index(i, (int32_t)c);
+        if (val < 0) return Status::err(NBTE_ERR_MESH, "internal: missing wall export");
+      } else {
+        const auto& v = outs[i].bimp;
+        auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(h, (int32_t)INT32_MIN));
+        if (it == v.end() || it->first != h) return Status::err(NBTE_ERR_MESH, "internal: missing wall import");
+        val = -(1 + (P.imp_off[i] + it->second));
+      }
+      P.wf_val.push_back(val);
+      P.wf_coef.push_back(w[i] * a);
+    }
+    P.wf_ptr.push_back((int64_t)P.wf_val.size());
+  }
+  return Status::ok();
+}
+
+void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bulk, double k1, Laplacian& L) {
+  const int dim = m.dim, nfc = m.nfc;
+  const int64_t N = m.n_cells;
+  std::map<int32_t, int> type;
+  for (auto& b : bcs) type[b.tag] = b.type;
+  L.row_ptr.assign(N + 1, 0);
+  L.col.clear();
+  L.val.clear();
+  L.diag.assign(N, 0.0);
+  for (int64_t c = 0; c < N; ++c) {
+    double dg = 0.0;
+    for (int k = 0; k < nfc; ++k) {
+      const int64_t h = c * nfc + k;
+      double area = 0;
+      for (int d = 0; d < dim; ++d) area += m.An[h * dim + d] * m.An[h * dim + d];
+      area = std::sqrt(area);
+      const int64_t v = m.nb[h];
+      if (v >= 0) {
+        double dist = 0;
+        for (int d = 0; d < dim; ++d) dist += (m.xc[v * dim + d] - m.xc[c * dim + d]) * m.An[h * dim + d] / area;
+        dist = std::fabs(dist);
+        const double g = (kappa_bulk + k1 * dist) * area / dist;
+        dg += g;
+        L.col.push_back((int32_t)v);
+        L.val.push_back(-g);
+      } else if (type.at(m.tag[h]) == NBTE_THERMALIZING) {
+        double dist = 0;
+        for (int d = 0; d < dim; ++d) dist += (m.xf[h * dim + d] - m.xc[c * dim + d]) * m.An[h * dim + d] / area;
+        dist = std::fabs(dist);
+        dg += (kappa_bulk + k1 * 2.0 * dist) * area / dist;
+      }
+    }
+    L.col.push_back((int32_t)c);
+    L.val.push_back(dg);
+    L.diag[c] = dg;
+    L.row_ptr[c + 1] = (int64_t)L.col.size();
+  }
+}
+
+}  // namespace nbte

@@ -1,0 +1,312 @@
+"""Python binding of libnanobte (ctypes; argument marshalling only).
+
+Every function mirrors one ``nbte_*`` call of ``include/nbte.h`` and converts
+NumPy arrays to the C layout; every computation runs in the library's CUDA
+kernels.  There is no fallback: if the library is not built, :func:`load`
+raises.  :class:`Solver` bundles the calls for one problem.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnanobte.so")
+
+NBTE_OK = 0
+NBTE_ERR_ARG = -1
+NBTE_ERR_MESH = -2
+NBTE_ERR_OOM = -3
+NBTE_ERR_CUDA = -4
+NBTE_ERR_NOT_CONVERGED = -5
+NBTE_ERR_DIVERGED = -6
+NBTE_ERR_DEVICE_TIMEOUT = -7
+NBTE_ERR_STATE = -8
+ERR_NAMES = {0: "OK", -1: "ARG", -2: "MESH", -3: "OOM", -4: "CUDA", -5: "NOT_CONVERGED", -6: "DIVERGED",
+             -7: "DEVICE_TIMEOUT", -8: "STATE"}
+
+NBTE_TRI, NBTE_QUAD, NBTE_TET, NBTE_HEX = 3, 4, 10, 12
+NBTE_THERMALIZING, NBTE_DIFFUSE, NBTE_SPECULAR, NBTE_PARTIAL = 0, 1, 2, 3
+SCHEMES = {"sequential": 0, "synthetic": 1, "synthetic_literal": 2}
+
+# every symbol include/nbte.h declares
+EXPORTS = [
+    "nbte_mesh_create", "nbte_mesh_destroy", "nbte_mesh_info", "nbte_solver_create", "nbte_solver_destroy",
+    "nbte_solver_set_stream", "nbte_set_bands", "nbte_set_quadrature", "nbte_set_boundaries",
+    "nbte_set_heat_source", "nbte_default_opts", "nbte_solve_steady", "nbte_get_temperature",
+    "nbte_get_heat_flux", "nbte_get_wall_heat", "nbte_plan_stats", "nbte_last_error", "nbte_version",
+]
+
+
+class nbte_boundary(C.Structure):
+    _fields_ = [("tag", C.c_int32), ("type", C.c_int32), ("T_wall", C.c_double), ("specularity", C.c_double)]
+
+
+class nbte_solve_opts(C.Structure):
+    _fields_ = [("scheme", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
+                ("max_iter", C.c_int32), ("n_iter", C.c_int32), ("T_init", C.POINTER(C.c_double)),
+                ("warm", C.c_int32), ("band_group", C.c_int32), ("threads_per_cell", C.c_int32),
+                ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class nbte_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("residual", C.c_double), ("energy_imbalance", C.c_double),
+                ("lagged_faces", C.c_int64), ("seconds", C.c_double), ("cg_iterations", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class NbteError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nbte error {code} ({ERR_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I64 = C.POINTER(C.c_int64)
+_I32 = C.POINTER(C.c_int32)
+
+
+def load(path: str | None = None):
+    """Load the built library (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run `python -m paper_2607_03226_b300.build`")
+    lib = C.CDLL(path)
+    sig = {
+        "nbte_mesh_create": ([C.c_int, C.c_int64, _D, C.c_int, C.c_int64, _I64, C.c_int64, _I64, _I32,
+                              C.POINTER(_P)], C.c_int),
+        "nbte_mesh_destroy": ([_P], C.c_int),
+        "nbte_mesh_info": ([_P, _I64, _D], C.c_int),
+        "nbte_solver_create": ([_P, C.c_double, C.POINTER(_P)], C.c_int),
+        "nbte_solver_destroy": ([_P], C.c_int),
+        "nbte_solver_set_stream": ([_P, _P], C.c_int),
+        "nbte_set_bands": ([_P, C.c_int, _D, _D, _D], C.c_int),
+        "nbte_set_quadrature": ([_P, C.c_int, _D, _D], C.c_int),
+        "nbte_set_boundaries": ([_P, C.c_int, C.POINTER(nbte_boundary)], C.c_int),
+        "nbte_set_heat_source": ([_P, _D], C.c_int),
+        "nbte_default_opts": ([C.POINTER(nbte_solve_opts)], C.c_int),
+        "nbte_solve_steady": ([_P, C.POINTER(nbte_solve_opts), C.POINTER(nbte_solve_info)], C.c_int),
+        "nbte_get_temperature": ([_P, C.c_int, _D], C.c_int),
+        "nbte_get_heat_flux": ([_P, _D], C.c_int),
+        "nbte_get_wall_heat": ([_P, C.c_int32, _D], C.c_int),
+        "nbte_plan_stats": ([_P, C.POINTER(nbte_solve_opts), _I64], C.c_int),
+        "nbte_last_error": ([], C.c_char_p),
+        "nbte_version": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc, allow=()):
+    if rc != NBTE_OK and rc not in allow:
+        raise NbteError(rc, load().nbte_last_error().decode())
+    return rc
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_D)
+
+
+def _i64(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(_I64)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_I32)
+
+
+# ------------------------------------------------------------------ thin calls
+def nbte_mesh_create(dim, nodes, cell_type, cells, bfaces, btags):
+    lib = load()
+    nodes, pn = _d(nodes)
+    cells, pc = _i64(cells)
+    bfaces, pb = _i64(bfaces)
+    btags, pt = _i32(btags)
+    out = _P()
+    _check(lib.nbte_mesh_create(int(dim), nodes.shape[0], pn, int(cell_type), cells.shape[0], pc,
+                                bfaces.shape[0], pb, pt, C.byref(out)))
+    return out
+
+
+def nbte_mesh_destroy(mesh):
+    return _check(load().nbte_mesh_destroy(mesh))
+
+
+def nbte_mesh_info(mesh):
+    n = C.c_int64()
+    v = C.c_double()
+    _check(load().nbte_mesh_info(mesh, C.byref(n), C.byref(v)))
+    return n.value, v.value
+
+
+def nbte_solver_create(mesh, T_ref):
+    out = _P()
+    _check(load().nbte_solver_create(mesh, float(T_ref), C.byref(out)))
+    return out
+
+
+def nbte_solver_destroy(solver):
+    return _check(load().nbte_solver_destroy(solver))
+
+
+def nbte_solver_set_stream(solver, stream_ptr):
+    return _check(load().nbte_solver_set_stream(solver, _P(stream_ptr) if stream_ptr else None))
+
+
+def nbte_set_bands(solver, C_, v, tau):
+    C_, pc = _d(C_)
+    v, pv = _d(v)
+    tau, pt = _d(tau)
+    return _check(load().nbte_set_bands(solver, C_.size, pc, pv, pt))
+
+
+def nbte_set_quadrature(solver, s, w):
+    s, ps = _d(np.asarray(s, dtype=np.float64).reshape(-1, 3))
+    w, pw = _d(w)
+    return _check(load().nbte_set_quadrature(solver, w.size, ps, pw))
+
+
+def nbte_set_boundaries(solver, bcs):
+    arr = (nbte_boundary * len(bcs))()
+    for k, b in enumerate(bcs):
+        arr[k].tag, arr[k].type = int(b.tag), int(b.type)
+        arr[k].T_wall, arr[k].specularity = float(b.T_wall), float(b.specularity)
+    return _check(load().nbte_set_boundaries(solver, len(bcs), arr))
+
+
+def nbte_set_heat_source(solver, Qdot):
+    if Qdot is None:
+        return _check(load().nbte_set_heat_source(solver, None))
+    Qdot, pq = _d(Qdot)
+    return _check(load().nbte_set_heat_source(solver, pq))
+
+
+def nbte_default_opts():
+    o = nbte_solve_opts()
+    _check(load().nbte_default_opts(C.byref(o)))
+    return o
+
+
+def make_opts(scheme="sequential", precision="fp64", tol=1e-10, max_iter=10000, n_iter=0, T_init=None,
+              warm=False, band_group=0, threads_per_cell=0, cg_tol=0.0, cg_max_iter=0, use_graph=False):
+    o = nbte_default_opts()
+    o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    o.precision = {"fp64": 0, "fp32": 1}[precision] if isinstance(precision, str) else int(precision)
+    o.tol, o.max_iter, o.n_iter = float(tol), int(max_iter), int(n_iter)
+    o.warm, o.band_group, o.threads_per_cell = int(bool(warm)), int(band_group), int(threads_per_cell)
+    o.cg_tol, o.cg_max_iter, o.use_graph = float(cg_tol), int(cg_max_iter), int(bool(use_graph))
+    keep = None
+    if T_init is not None:
+        keep, o.T_init = _d(T_init)
+    o._keep = keep  # keeps T_init alive for the call
+    return o
+
+
+def nbte_solve_steady(solver, opts):
+    info = nbte_solve_info()
+    rc = _check(load().nbte_solve_steady(solver, C.byref(opts), C.byref(info)),
+                allow=(NBTE_ERR_NOT_CONVERGED,))
+    return rc, info
+
+
+def nbte_get_temperature(solver, kind, n_cells):
+    out = np.empty(n_cells, dtype=np.float64)
+    _check(load().nbte_get_temperature(solver, int(kind), out.ctypes.data_as(_D)))
+    return out
+
+
+def nbte_get_heat_flux(solver, n_cells, dim):
+    out = np.empty((n_cells, dim), dtype=np.float64)
+    _check(load().nbte_get_heat_flux(solver, out.ctypes.data_as(_D)))
+    return out
+
+
+def nbte_get_wall_heat(solver, tag):
+    v = C.c_double()
+    _check(load().nbte_get_wall_heat(solver, int(tag), C.byref(v)))
+    return v.value
+
+
+def nbte_plan_stats(solver, opts=None):
+    st = np.zeros(8, dtype=np.int64)
+    _check(load().nbte_plan_stats(solver, C.byref(opts) if opts is not None else None, st.ctypes.data_as(_I64)))
+    keys = ["total_levels", "max_levels", "max_slots", "lagged_faces", "items", "band_group",
+            "threads_per_cell", "device_bytes"]
+    return dict(zip(keys, (int(x) for x in st)))
+
+
+def nbte_last_error():
+    return load().nbte_last_error().decode()
+
+
+def nbte_version():
+    return load().nbte_version().decode()
+
+
+# ------------------------------------------------------------------ helper
+class Solver:
+    """One mesh + solver pair set up from a problem description (any object
+    with ``mesh, C, v, tau, s, w, boundaries, Q, T_ref``)."""
+
+    def __init__(self, problem, stream=None):
+        m = problem.mesh
+        self.dim = int(m.dim)
+        self.n_cells = int(m.cells.shape[0])
+        self.mesh = nbte_mesh_create(m.dim, m.nodes, m.cell_type, m.cells, m.bfaces, m.btags)
+        self.solver = nbte_solver_create(self.mesh, problem.T_ref)
+        if stream is not None:
+            nbte_solver_set_stream(self.solver, stream)
+        nbte_set_bands(self.solver, problem.C, problem.v, problem.tau)
+        nbte_set_quadrature(self.solver, problem.s, problem.w)
+        nbte_set_boundaries(self.solver, problem.boundaries)
+        nbte_set_heat_source(self.solver, problem.Q)
+        self.tags = sorted({int(b.tag) for b in problem.boundaries})
+
+    def solve(self, **kw):
+        opts = make_opts(**kw)
+        rc, info = nbte_solve_steady(self.solver, opts)
+        d = info.as_dict()
+        d["status"] = rc
+        return d
+
+    def temperature(self, kind=0):
+        return nbte_get_temperature(self.solver, kind, self.n_cells)
+
+    def heat_flux(self):
+        return nbte_get_heat_flux(self.solver, self.n_cells, self.dim)
+
+    def wall_heat(self, tag):
+        return nbte_get_wall_heat(self.solver, tag)
+
+    def plan_stats(self, **kw):
+        return nbte_plan_stats(self.solver, make_opts(**kw))
+
+    def close(self):
+        if getattr(self, "solver", None):
+            nbte_solver_destroy(self.solver)
+            self.solver = None
+        if getattr(self, "mesh", None):
+            nbte_mesh_destroy(self.mesh)
+            self.mesh = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,88 @@
+"""Write the stored oracle results the GPU parity tests compare against.
+
+Calls only ``oracle/`` and the seeded generators in ``workloads/``.  Each
+output file records the command, the problem parameters and the oracle's
+iteration count; values are absolute temperatures (K) and heat fluxes (W/m^2).
+
+Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_converged ...]
+
+* ``square``              - the 40x40 in-plane square, sequential to 1e-12
+                            (all 1600 cells).
+* ``finfet2d_steps``      - the ~50k-triangle fin, 20 bands, 64 directions:
+                            the lattice temperature after sequential iterations
+                            1 and 2 from T_ref, on 4096 seeded sample cells.
+* ``finfet2d_converged``  - the same problem converged (sequential, 1e-10),
+                            T_L and q on the sample cells.
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import workloads as W  # noqa: E402
+from oracle import OracleSolver  # noqa: E402
+
+SAMPLE_SEED = 7
+N_SAMPLE = 4096
+
+
+def _write(name, payload):
+    path = os.path.join(HERE, name)
+    with open(path, "w") as f:
+        json.dump(payload, f, indent=None, separators=(",", ":"))
+    print("wrote", path)
+
+
+def square():
+    p = W.problems.square_inplane()
+    t = time.time()
+    r = OracleSolver(p).solve(scheme="sequential", tol=1e-12)
+    _write("square_inplane_converged.json", dict(
+        problem="square_inplane()", scheme="sequential", tol=1e-12, iterations=r["iterations"],
+        seconds=time.time() - t, T=r["T"].tolist(), q=r["q"].tolist(),
+        T_energy=r["T_energy"].tolist()))
+
+
+def _sample(n_cells):
+    rng = np.random.default_rng(SAMPLE_SEED)
+    return np.sort(rng.choice(n_cells, size=min(N_SAMPLE, n_cells), replace=False))
+
+
+def finfet2d_steps():
+    p = W.problems.finfet2d()
+    o = OracleSolver(p)
+    idx = _sample(p.n_cells)
+    out = dict(problem="finfet2d()", scheme="sequential", sample_seed=SAMPLE_SEED, cells=idx.tolist())
+    for n in (1, 2):
+        t = time.time()
+        r = o.solve(scheme="sequential", n_iter=n)
+        out[f"T_iter{n}"] = r["T"][idx].tolist()
+        out[f"T_iter{n}_max_dev"] = float(np.abs(r["T"] - p.T_ref).max())
+        out[f"seconds_iter{n}"] = time.time() - t
+        print("iter", n, "done", time.time() - t)
+    _write("finfet2d_steps.json", out)
+
+
+def finfet2d_converged():
+    p = W.problems.finfet2d()
+    o = OracleSolver(p)
+    idx = _sample(p.n_cells)
+    t = time.time()
+    r = o.solve(scheme="sequential", tol=1e-10, verbose=True)
+    _write("finfet2d_converged.json", dict(
+        problem="finfet2d()", scheme="sequential", tol=1e-10, iterations=r["iterations"],
+        converged=r["converged"], seconds=time.time() - t, sample_seed=SAMPLE_SEED,
+        cells=idx.tolist(), T=r["T"][idx].tolist(), q=r["q"][idx].tolist(),
+        T_max=float(r["T"].max()), energy_imbalance=r["energy_imbalance"]))
+
+
+if __name__ == "__main__":
+    for name in (sys.argv[1:] or ["square"]):
+        globals()[name]()

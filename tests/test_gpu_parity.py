@@ -1,0 +1,156 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (written here, from the stated targets): FP64 path, converged
+fields: temperature 1e-9 and heat flux 1e-8 relative (|.|_inf over the
+oracle's deviation / flux magnitude); single iterations from the same state
+agree to rounding (1e-11).  FP32-sweep path: temperature 1e-6.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import OracleSolver
+import workloads as W
+from cases import CASES, rel_T, rel_q
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def nbte_mod(gpu_lib):
+    from paper_2607_03226_b300 import nbte
+    return nbte
+
+
+_oracle_cache = {}
+
+
+def oracle_run(name, **kw):
+    key = (name, tuple(sorted(kw.items())))
+    if key not in _oracle_cache:
+        p = CASES[name]()
+        _oracle_cache[key] = OracleSolver(p).solve(**kw)
+    return _oracle_cache[key]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("n_iter", [1, 3])
+def test_single_iterations_fp64(nbte_mod, name, n_iter):
+    """Same start state, same number of sequential iterations: every moment
+    agrees with the oracle to rounding (no cycle-breaking lag on these meshes)."""
+    p = CASES[name]()
+    s = nbte_mod.Solver(p)
+    info = s.solve(scheme="sequential", precision="fp64", n_iter=n_iter)
+    assert info["iterations"] == n_iter and info["lagged_faces"] == 0
+    r = oracle_run(name, scheme="sequential", n_iter=n_iter)
+    assert rel_T(s.temperature(0), r["T"], p.T_ref) < 1e-11
+    assert rel_T(s.temperature(2), r["T_kinetic"], p.T_ref) < 1e-11
+    assert rel_T(s.temperature(1), r["T_energy"], p.T_ref) < 1e-11
+    assert rel_q(s.heat_flux(), r["q"]) < 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_single_iterations_synthetic_fp64(nbte_mod, name):
+    """Two synthetic (diffusion-corrected) iterations, CG converged tightly:
+    the correction, the corrected wall values and the update agree."""
+    p = CASES[name]()
+    s = nbte_mod.Solver(p)
+    s.solve(scheme="synthetic", precision="fp64", n_iter=2, cg_tol=1e-14, cg_max_iter=20000)
+    r = oracle_run(name, scheme="synthetic", n_iter=2)
+    assert rel_T(s.temperature(0), r["T"], p.T_ref) < 1e-9
+    assert rel_T(s.temperature(2), r["T_kinetic"], p.T_ref) < 1e-9
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("scheme", ["sequential", "synthetic"])
+def test_converged_fp64(nbte_mod, name, scheme):
+    """Converged FP64 fields: T within 1e-9 and q within 1e-8 of the oracle;
+    the energy balance closes."""
+    p = CASES[name]()
+    s = nbte_mod.Solver(p)
+    info = s.solve(scheme=scheme, precision="fp64", tol=1e-13, max_iter=20000)
+    assert info["status"] == 0
+    r = oracle_run(name, scheme="synthetic", tol=1e-14, max_iter=20000)
+    assert rel_T(s.temperature(0), r["T"], p.T_ref) < 1e-9
+    assert rel_q(s.heat_flux(), r["q"]) < 1e-8
+    assert info["energy_imbalance"] < 1e-8
+    for tag, f in r["wall_flux"].items():
+        assert abs(s.wall_heat(tag) - f) <= 1e-8 * max(abs(v) for v in r["wall_flux"].values())
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_converged_fp32_sweep(nbte_mod, name):
+    """FP32 sweep with FP64 moments, update and residual: temperature within
+    1e-6 of the FP64 oracle (heat-flux error recorded, bounded at 1e-4)."""
+    p = CASES[name]()
+    s = nbte_mod.Solver(p)
+    info = s.solve(scheme="synthetic", precision="fp32", tol=1e-10, max_iter=20000)
+    assert info["status"] == 0
+    r = oracle_run(name, scheme="synthetic", tol=1e-14, max_iter=20000)
+    assert rel_T(s.temperature(0), r["T"], p.T_ref) < 1e-6
+    assert rel_q(s.heat_flux(), r["q"]) < 1e-4
+    s.close()
+
+
+def test_square_full_size_golden(nbte_mod):
+    """The 40x40 in-plane square (FP64 sequential to 1e-10, and FP32) against
+    the stored oracle solution."""
+    g = json.load(open(os.path.join(GOLDEN, "square_inplane_converged.json")))
+    p = W.problems.square_inplane()
+    s = nbte_mod.Solver(p)
+    info = s.solve(scheme="sequential", precision="fp64", tol=1e-12)
+    assert info["status"] == 0
+    assert rel_T(s.temperature(0), np.array(g["T"]), p.T_ref) < 1e-9
+    assert rel_q(s.heat_flux(), np.array(g["q"])) < 1e-8
+    info = s.solve(scheme="sequential", precision="fp32", tol=1e-10)
+    assert rel_T(s.temperature(0), np.array(g["T"]), p.T_ref) < 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("variant", [dict(band_group=1), dict(band_group=2, threads_per_cell=2),
+                                     dict(use_graph=True), dict(band_group=4, threads_per_cell=4, use_graph=True)])
+def test_launch_variants_identical(nbte_mod, variant):
+    """Band grouping, threads per cell and graph replay change only the launch
+    shape: FP64 results are identical to the default to rounding."""
+    p = CASES["fin2d_mixed"]()
+    p.C, p.v, p.tau = (np.tile(x, 2)[:4] for x in (p.C, p.v, p.tau))
+    s = nbte_mod.Solver(p)
+    s.solve(scheme="sequential", precision="fp64", n_iter=4)
+    T0, q0 = s.temperature(0), s.heat_flux()
+    s.solve(scheme="sequential", precision="fp64", n_iter=4, **variant)
+    assert np.abs(s.temperature(0) - T0).max() <= 1e-12 * np.abs(T0 - 300).max()
+    assert np.abs(s.heat_flux() - q0).max() <= 1e-11 * np.abs(q0).max()
+    s.close()
+
+
+def test_warm_start_continues(nbte_mod):
+    """Two solves of n iterations with warm=True equal one solve of 2n."""
+    p = CASES["cube_hex"]()
+    s = nbte_mod.Solver(p)
+    s.solve(scheme="sequential", precision="fp64", n_iter=6)
+    Ta = s.temperature(0)
+    s.solve(scheme="sequential", precision="fp64", n_iter=3)
+    s.solve(scheme="sequential", precision="fp64", n_iter=3, warm=True)
+    assert np.abs(s.temperature(0) - Ta).max() <= 1e-12 * np.abs(Ta - 300).max()
+    s.close()
+
+
+def test_uniform_temperature_invariant_fp32(nbte_mod):
+    """All thermalizing walls at one temperature and no source: the converged
+    field is that temperature everywhere, on a mixed-wall tet mesh, in FP32."""
+    p = W.problems.finfet3d(h=15e-9, B=4, n_pol=2, n_az=8, q_fin=0.0)
+    for b in p.boundaries:
+        if b.type == 0:
+            b.T_wall = 303.0
+    p.Q = None
+    s = nbte_mod.Solver(p)
+    info = s.solve(scheme="synthetic", precision="fp32", tol=1e-9, max_iter=5000)
+    assert info["status"] == 0
+    assert np.abs(s.temperature(0) - 303.0).max() < 3e-6 * 3.0
+    s.close()
