@@ -1,0 +1,273 @@
+"""Throughput benchmark: band-direction cell updates per second on the 2D
+FinFET-like workload (~50k triangles, 20 bands, 64 directions).
+
+A step is one outer iteration of the whole hot path: wall coupling, the
+level-scheduled sweep over every (direction, band) with the fused collision
+moment, the moment reduction and temperature update, and the CG-solved
+synthetic correction (scheme 1), on inputs resident in device memory.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--precision fp32|fp64] [--scheme synthetic|sequential]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank solves its own
+replica (no data exchange); rank 0 prints the aggregate over all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "band-dir cell updates/s"
+UNIT = "updates/s"
+WORKLOAD = "finfet2d: ~50k-triangle fin-on-substrate, 20 bands, 64 directions, Gaussian hot spot"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        busy = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes_per_item_cell(prec_bytes, K, G):
+    """HBM bytes one work item (direction, band group of G bands) must move per
+    cell it sweeps: the position record (cell, slot, export index, G: 4 words;
+    K inflow references and coefficients), the cell's (T', Qdot) pair, and the
+    FP64 collision-moment partial it writes.  Ring values stay in shared memory."""
+    return 3 * 4 + prec_bytes + K * (4 + prec_bytes) + 2 * prec_bytes + 8
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2607_03226_b300 import nbte
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = W.problems.finfet2d()
+    stream = torch.cuda.Stream()
+    solver = nbte.Solver(p, stream=stream.cuda_stream)
+    kw = dict(scheme=args.scheme, precision=args.precision, cg_tol=args.cg_tol, cg_max_iter=args.cg_max_iter,
+              band_group=args.band_group, threads_per_cell=args.threads_per_cell, use_graph=True,
+              skip_outputs=True)
+    stats = solver.plan_stats(**kw)
+    upd = p.updates_per_iteration
+    # warm-up (includes planning, upload and graph capture) then the timed steps
+    solver.solve(n_iter=max(args.warmup, 3), **kw)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        info = solver.solve(n_iter=args.steps, warm=True, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = upd * args.steps * ws / (t_max * 1e-3)
+
+    # sweep-kernel duration with events around each launch (same stream)
+    prof = solver.solve(n_iter=args.steps, warm=True, profile=True, **{k: v for k, v in kw.items()
+                                                                        if k != "use_graph"})
+    sweep_ms = prof["sweep_seconds"] * 1e3 / max(1, prof["sweep_launches"])
+    prec_b = 4 if args.precision == "fp32" else 8
+    K = 2
+    G = stats["band_group"]
+    n_items = stats["items"]
+    bytes_launch = n_items * p.n_cells * algorithmic_bytes_per_item_cell(prec_b, K, G)
+    peak, peak_kind = _peaks()
+    achieved = bytes_launch / (sweep_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: per step the heat
+    # source goes host->device, one iteration runs, the temperature comes back
+    Qh = np.ascontiguousarray(p.Q, dtype=np.float64)
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        nbte.nbte_set_heat_source(solver.solver, Qh)
+        solver.solve(n_iter=1, warm=True, **kw)
+        T = solver.temperature(0)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": upd * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Qh.nbytes),
+           "d2h_bytes_per_step": int(T.nbytes)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 sweep / f64 moments+update+CG" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded mesh, spectrum and hot spot)",
+        "config": {"workload": WORKLOAD, "n_cells": p.n_cells, "bands": p.n_bands, "directions": p.n_dirs,
+                   "updates_per_step": upd, "scheme": args.scheme, "precision": args.precision,
+                   "band_group": G, "items": n_items, "levels_max": stats["max_levels"],
+                   "ring_slots_max": stats["max_slots"], "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2: per-step device footprint %.0f MB > 126 MB" % (
+                       stats["device_bytes"] / 1e6)},
+        "e2e": e2e,
+        "gpu_launches": int(info["kernel_launches"]),
+        "cg_iterations_per_step": info["cg_iterations"] / max(1, args.steps),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": "sweep_kernel", "sweep_ms": sweep_ms,
+                     "algorithmic_bytes_per_launch": bytes_launch},
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(max_seconds=args.cpu_seconds)
+    solver.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def cpu_baseline(max_seconds=20.0, steps=1, warmup=1):
+    """The FP64 oracle on this host's cores, on a bounded sample of the same
+    workload: one transport pass over a subset of (direction, band) tasks (the
+    LU factorisations are built in an untimed warm-up pass), scaled to
+    updates/s."""
+    import numpy as np
+    import workloads as W
+    from oracle import OracleSolver
+
+    p = W.problems.finfet2d()
+    o = OracleSolver(p)
+    T = np.zeros(p.n_cells)
+    eb = o.equilibrium_walls(T)
+    # size the sample from one factor+solve timing
+    t0 = time.perf_counter()
+    o.sweep(T, eb, tasks=[(0, 0)])
+    o.sweep(T, eb, tasks=[(0, 0)])
+    one = (time.perf_counter() - t0) / 2
+    n_tasks = int(max(2, min(p.n_dirs * p.n_bands, max_seconds / (2.5 * max(one, 1e-3)))))
+    tasks = [(i, l) for i in range(p.n_dirs) for l in range(p.n_bands)][:n_tasks]
+    for _ in range(warmup):
+        o.sweep(T, eb, tasks=tasks)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.sweep(T, eb, tasks=tasks)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": n_tasks * p.n_cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_tasks} of {p.n_dirs * p.n_bands} (direction, band) tasks of one iteration, "
+                      f"{p.n_cells} cells each, cached sparse LU solves (SciPy SuperLU, single thread)",
+            "seconds_per_step": dt}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    cb = cpu_baseline(max_seconds=args.cpu_seconds, steps=args.steps, warmup=args.warmup)
+    out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": cb["seconds_per_step"] * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "scheme": "sequential transport pass (oracle)"},
+           "impl": "reference", "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+           "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="nbte", choices=["nbte", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--scheme", default="synthetic", choices=["synthetic", "sequential"])
+    ap.add_argument("--band-group", type=int, default=0)
+    ap.add_argument("--threads-per-cell", type=int, default=0)
+    ap.add_argument("--cg-tol", type=float, default=1e-6)
+    ap.add_argument("--cg-max-iter", type=int, default=5000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

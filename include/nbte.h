@@ -144,6 +144,14 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  *            solve of the synthetic correction (0 = defaults 1e-10, 5000); the
  *            correction only changes the rate of convergence, not the limit.
  * use_graph: 1 = replay each iteration from a captured CUDA graph.
+ * skip_outputs: 1 = do not compute the energy temperature, heat flux and wall
+ *            heat of the last sweep (kind-0 and kind-2 temperatures remain
+ *            readable); saves one extra sweep per call.
+ * profile:   1 = time every sweep launch with CUDA events on the solver's
+ *            stream (reported in nbte_solve_info); adds a host sync per
+ *            iteration.
+ * With n_iter > 0 (and profile 0) the iterations are enqueued back to back
+ * and the host synchronises once at the end.
  */
 typedef struct {
   int32_t scheme;
@@ -158,6 +166,8 @@ typedef struct {
   double cg_tol;
   int32_t cg_max_iter;
   int32_t use_graph;
+  int32_t skip_outputs;
+  int32_t profile;
 } nbte_solve_opts;
 
 /* Filled on return from nbte_solve_steady (also on NOT_CONVERGED):
@@ -168,7 +178,11 @@ typedef struct {
  *   lagged_faces      inflow faces whose upwind value is taken from the
  *                     previous iteration to break upwind-graph cycles;
  *   seconds           wall time of the iteration loop;
- *   cg_iterations     total CG iterations (synthetic schemes).            */
+ *   cg_iterations     total CG iterations (synthetic schemes);
+ *   sweep_seconds     summed device time of the sweep launches (profile=1);
+ *   sweep_launches    sweep launches timed (profile=1);
+ *   kernel_launches   kernels this call launched (graph replays counted by
+ *                     their kernel nodes).                                  */
 typedef struct {
   int32_t iterations;
   double residual;
@@ -176,6 +190,9 @@ typedef struct {
   int64_t lagged_faces;
   double seconds;
   int64_t cg_iterations;
+  double sweep_seconds;
+  int64_t sweep_launches;
+  int64_t kernel_launches;
 } nbte_solve_info;
 
 /* Default options: sequential, FP64, tol 1e-10, max_iter 10000.           */

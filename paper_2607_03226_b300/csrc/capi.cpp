@@ -128,7 +128,8 @@ struct nbte_solver {
   DBuf L_rp, L_col, L_val, L_dinv;
   // ---- state
   bool have_state = false;
-  bool have_results = false;
+  bool have_results = false;   // T (kind 0, 2) of the last solve
+  bool have_outputs = false;   // E, q, wall heat of the last sweep
   unsigned long long* h_res = nullptr;   // pinned: [2] residual words
   int32_t* h_misc = nullptr;             // pinned: [2] device error, cg iterations
   cudaGraphExec_t graph = nullptr;
@@ -328,7 +329,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   for (int l = 0; l < S->B; ++l) {
     bv[l] = S->v[l];
     bit[l] = 1.0 / S->tau[l];
-    baT[l] = S->C[l] / (S->W * S->tau[l]);
+    baT[l] = S->C[l] / S->W;   // e0 = (C/W) T' of Eq. (11)
     baQ[l] = S->C[l] / (S->Ctot * S->W);
     bCoW[l] = S->C[l] / S->W;
   }
@@ -458,7 +459,7 @@ SweepArgs<R> sweep_args(nbte_solver* S, const void* srcTQ, int full) {
   a.srcTQ = static_cast<const R*>(srcTQ);
   a.band_v = S->band_v.as<R>();
   a.band_inv_tau = S->band_itau.as<R>();
-  a.band_aT = S->band_aT.as<R>();
+  a.band_cw = S->band_aT.as<R>();
   a.band_aQ = S->band_aQ.as<R>();
   a.dir_w = S->dir_w.as<double>();
   a.dir_s = S->dir_s.as<double>();
@@ -536,13 +537,16 @@ CGArgs cg_args(nbte_solver* S, double tol, int max_it) {
 
 // one outer iteration, stream-ordered (capturable)
 template <typename R>
-cudaError_t enqueue_iteration(nbte_solver* S, int scheme, double cg_tol, int cg_max) {
+cudaError_t enqueue_iteration(nbte_solver* S, int scheme, double cg_tol, int cg_max, cudaEvent_t ev0 = nullptr,
+                              cudaEvent_t ev1 = nullptr) {
   cudaStream_t st = S->stream;
   launch_walls<R>(wall_args<R>(S), st);
   cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
+  if (ev0) cudaEventRecord(ev0, st);
   e = launch_sweep<R>(sweep_args<R>(S, S->srcTQ.p, 0), S->K, S->bpt, S->lanes, S->n_items, S->threads, S->smem, st);
   if (e != cudaSuccess) return e;
+  if (ev1) cudaEventRecord(ev1, st);
   e = cudaMemsetAsync(S->res.p, 0, 16, st);
   if (e != cudaSuccess) return e;
   if (scheme == 0) {
@@ -567,8 +571,10 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   cudaStream_t st = S->stream;
   const double cg_tol = o.cg_tol > 0 ? o.cg_tol : 1e-10;
   const int cg_max = o.cg_max_iter > 0 ? o.cg_max_iter : 5000;
+  int64_t kernels = 0;
   // ---- initial state
   if (!(o.warm && S->have_state)) {
+    kernels += 2;
     std::vector<double> T0(N, 0.0);
     if (o.T_init) {
       for (int64_t c = 0; c < N; ++c) {
@@ -587,6 +593,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     NBTE_CK(cudaStreamSynchronize(st));
     S->have_state = true;
   } else {
+    kernels += 1;
     launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)N, st);
   }
   if (S->cg_it.p) NBTE_CK(cudaMemsetAsync(S->cg_it.p, 0, 4, st));
@@ -618,20 +625,28 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     cudaGetLastError();   // clear a failed capture
   }
   // ---- iterate
+  const bool profile = o.profile != 0;
+  if (profile) use_graph = false;   // events bracket each sweep launch
+  const int64_t kernels_per_iter = (S->n_dbf > 0) + (S->n_imp > 0) + 1 + (scheme == 0 ? 1 : 3);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (profile) {
+    NBTE_CK(cudaEventCreate(&ev0));
+    NBTE_CK(cudaEventCreate(&ev1));
+  }
+  double sweep_ms = 0.0;
+  int64_t sweeps_timed = 0;
   auto t0 = std::chrono::steady_clock::now();
   int it = 0;
   double r = INFINITY;
   int status = NBTE_OK;
-  while (it < limit) {
-    if (use_graph) NBTE_CK(cudaGraphLaunch(S->graph, st));
-    else NBTE_CK(enqueue_iteration<R>(S, scheme, cg_tol, cg_max));
-    NBTE_CK(cudaStreamSynchronize(st));
-    ++it;
+  // with a fixed iteration count the host only looks at the device once
+  const bool check_each = !fixed || profile;
+  auto check = [&]() -> bool {   // returns true to stop
     if (S->h_misc[0] != 0 && scheme != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the CG correction gave up");
       cudaMemset(S->cg_err.p, 0, 16);
       cudaMemset(S->cg_bar.p, 0, 16);
-      break;
+      return true;
     }
     double dmax, tmax;
     std::memcpy(&dmax, &S->h_res[0], 8);
@@ -639,16 +654,40 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     if (!std::isfinite(dmax) || !std::isfinite(tmax)) {
       status = fail(NBTE_ERR_DIVERGED, "non-finite temperature: the iteration diverged");
       r = INFINITY;
-      break;
+      return true;
     }
     r = dmax / std::max(tmax, 1e-300);
     if (tmax == 0.0 && dmax == 0.0) r = 0.0;
-    if (!fixed && r < o.tol) break;
+    return !fixed && r < o.tol;
+  };
+  while (it < limit) {
+    if (use_graph) NBTE_CK(cudaGraphLaunch(S->graph, st));
+    else NBTE_CK(enqueue_iteration<R>(S, scheme, cg_tol, cg_max, ev0, ev1));
+    kernels += kernels_per_iter;
+    ++it;
+    if (!check_each) continue;
+    NBTE_CK(cudaStreamSynchronize(st));
+    if (profile) {
+      float ms = 0.f;
+      NBTE_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+      sweep_ms += ms;
+      ++sweeps_timed;
+    }
+    if (check()) break;
+  }
+  if (!check_each) {
+    NBTE_CK(cudaStreamSynchronize(st));
+    check();
   }
   auto t1 = std::chrono::steady_clock::now();
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
   if (status == NBTE_OK && !fixed && !(r < o.tol)) status = NBTE_ERR_NOT_CONVERGED;
+  S->have_results = status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED;
+  S->have_outputs = false;
   // ---- moments of the last sweep: replay it with the energy/flux moments on
-  if (status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED) {
+  if ((status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED) && !o.skip_outputs) {
+    kernels += 3;
     NBTE_CK(cudaMemsetAsync(S->accE.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
     launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
@@ -669,7 +708,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     S->wall_heat_by_face.assign(S->n_wf, 0.0);
     NBTE_CK(cudaMemcpyAsync(S->wall_heat_by_face.data(), S->heat.p, S->n_wf * 8, cudaMemcpyDeviceToHost, st));
     NBTE_CK(cudaStreamSynchronize(st));
-    S->have_results = true;
+    S->have_outputs = true;
     // energy balance (FP64)
     std::map<int32_t, int> type;
     for (auto& b : S->bcs) type[b.tag] = b.type;
@@ -691,8 +730,11 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     info->lagged_faces = S->lagged;
     info->seconds = std::chrono::duration<double>(t1 - t0).count();
     int32_t cgi = 0;
-    if (S->cg_it.p) cudaMemcpy(&cgi, S->cg_it.p, 4, cudaMemcpyDeviceToHost);
+    if (S->cg_it.p && scheme != 0) cudaMemcpy(&cgi, S->cg_it.p, 4, cudaMemcpyDeviceToHost);
     info->cg_iterations = cgi;
+    info->sweep_seconds = sweep_ms * 1e-3;
+    info->sweep_launches = sweeps_timed;
+    info->kernel_launches = kernels;
   }
   return status;
 }
@@ -957,13 +999,14 @@ int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
   if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
   if (!S->have_results) return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
   if (kind < 0 || kind > 2) return fail(NBTE_ERR_ARG, "kind must be 0, 1 or 2");
+  if (kind == 1 && !S->have_outputs) return fail(NBTE_ERR_STATE, "the last solve skipped its outputs");
   DeviceGuard g(S->device);
   const Mesh& m = S->mesh->m;
   const int64_t N = m.n_cells;
   std::vector<double> tmp(N);
   const DBuf& src = kind == 0 ? S->T : (kind == 1 ? S->accE : S->Tkin);
+  NBTE_CK(cudaMemcpyAsync(tmp.data(), src.p, N * 8, cudaMemcpyDeviceToHost, S->stream));
   NBTE_CK(cudaStreamSynchronize(S->stream));
-  NBTE_CK(cudaMemcpy(tmp.data(), src.p, N * 8, cudaMemcpyDeviceToHost));
   for (int64_t c = 0; c < N; ++c) {
     const double t = kind == 1 ? tmp[c] / S->Ctot : tmp[c];
     out[m.perm[c]] = t + S->T_ref;
@@ -974,12 +1017,13 @@ int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
 int nbte_get_heat_flux(const nbte_solver* S, double* out) {
   if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
   if (!S->have_results) return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
+  if (!S->have_outputs) return fail(NBTE_ERR_STATE, "the last solve skipped its outputs");
   DeviceGuard g(S->device);
   const Mesh& m = S->mesh->m;
   const int64_t N = m.n_cells;
   std::vector<double> tmp((size_t)N * m.dim);
+  NBTE_CK(cudaMemcpyAsync(tmp.data(), S->accQ.p, tmp.size() * 8, cudaMemcpyDeviceToHost, S->stream));
   NBTE_CK(cudaStreamSynchronize(S->stream));
-  NBTE_CK(cudaMemcpy(tmp.data(), S->accQ.p, tmp.size() * 8, cudaMemcpyDeviceToHost));
   for (int64_t c = 0; c < N; ++c)
     for (int d = 0; d < m.dim; ++d) out[m.perm[c] * m.dim + d] = tmp[c * m.dim + d];
   return NBTE_OK;
@@ -988,6 +1032,7 @@ int nbte_get_heat_flux(const nbte_solver* S, double* out) {
 int nbte_get_wall_heat(const nbte_solver* S, int32_t tag, double* out) {
   if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
   if (!S->have_results) return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
+  if (!S->have_outputs) return fail(NBTE_ERR_STATE, "the last solve skipped its outputs");
   double h = 0;
   bool found = false;
   for (size_t f = 0; f < S->wall_heat_by_face.size(); ++f)

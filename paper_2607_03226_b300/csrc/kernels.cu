@@ -94,10 +94,14 @@ __device__ __forceinline__ R lane_sum(R x) {
 // of direction i in order; a __syncthreads() between levels makes level l's
 // values visible to level l+1.  Thread t serves lane (t % LANES) of cells
 // (t / LANES), (t / LANES) + blockDim/LANES, ... of each level; lane j holds
-// bands [g*G + j*BPT, g*G + (j+1)*BPT) in registers.  Per cell and band:
-//   e = (C T'/(W tau) + Qdot C/(C_tot W) + v sum_in (|s.An|/V) e_up)
-//       / (1/tau + v sum_out (s.An)/V)
-// which is the upwind balance of Eq. (4) solved for the cell value.
+// bands [g*G + j*BPT, g*G + (j+1)*BPT) in registers.  Per cell and band the
+// upwind balance of Eq. (4) is solved for the deviation from the cell's own
+// equilibrium e0 = C T'/W (Eq. (11)):
+//   e = e0 + (Qdot C/(C_tot W) + v sum_in c_k (e_up,k - e0)) / (1/tau + v G),
+//   c_k = |s.An_k|/V,  G = sum_in c_k  (= sum_out (s.An)/V for a closed cell),
+// which equals e = (e0/tau + S + v sum_in c_k e_up)/(1/tau + v G).  Written
+// this way a uniform equilibrium is reproduced exactly in any precision and
+// rounding errors scale with the local differences e_up - e0.
 template <typename R, int K, int BPT, int LANES>
 __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -113,12 +117,12 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
   for (int t = threadIdx.x; t < G; t += blockDim.x) ring[t] = R(0);   // zero slot
 
   const double wi = a.dir_w[i];
-  R vb[BPT], itau[BPT], aT[BPT], aQ[BPT], wt[BPT];
+  R vb[BPT], itau[BPT], cw[BPT], aQ[BPT], wt[BPT];
 #pragma unroll
   for (int b = 0; b < BPT; ++b) {
     vb[b] = a.band_v[band0 + b];
     itau[b] = a.band_inv_tau[band0 + b];
-    aT[b] = a.band_aT[band0 + b];
+    cw[b] = a.band_cw[band0 + b];
     aQ[b] = a.band_aQ[band0 + b];
     wt[b] = (R)(wi * (double)itau[b]);
   }
@@ -143,12 +147,12 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
       const int ex = a.pos_exp[q];
       const R Gc = a.pos_G[q];
       const typename Vec2<R>::T src = tq[cell];
-      R acc[BPT];
+      R e0[BPT], up[BPT];
 #pragma unroll
-      for (int b = 0; b < BPT; ++b) acc[b] = aT[b] * src.x + aQ[b] * src.y;
-      R up[BPT];
-#pragma unroll
-      for (int b = 0; b < BPT; ++b) up[b] = R(0);
+      for (int b = 0; b < BPT; ++b) {
+        e0[b] = cw[b] * src.x;
+        up[b] = R(0);
+      }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int64_t qk = ((int64_t)i * K + k) * N + p;
@@ -158,13 +162,13 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
         R e_up[BPT];
         load_bands<R, BPT>(sp, e_up);
 #pragma unroll
-        for (int b = 0; b < BPT; ++b) up[b] += cf * e_up[b];
+        for (int b = 0; b < BPT; ++b) up[b] += cf * (e_up[b] - e0[b]);
       }
       R e[BPT];
       R nl = R(0);
 #pragma unroll
       for (int b = 0; b < BPT; ++b) {
-        e[b] = (acc[b] + vb[b] * up[b]) * recip(itau[b] + vb[b] * Gc);
+        e[b] = e0[b] + (aQ[b] * src.y + vb[b] * up[b]) * recip(itau[b] + vb[b] * Gc);
         nl += wt[b] * e[b];
       }
       if (slot >= 0) store_bands<R, BPT>(ring + slot * G + lane * BPT, e);

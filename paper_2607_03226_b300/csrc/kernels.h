@@ -31,7 +31,7 @@ struct SweepArgs {
   const R* srcTQ;                // [2*N] (T', Qdot) per cell
   const R* band_v;               // [Bp]
   const R* band_inv_tau;
-  const R* band_aT;              // C / (W tau)
+  const R* band_cw;              // C / W
   const R* band_aQ;              // C / (C_tot W)
   const double* dir_w;           // [D]
   const double* dir_s;           // [D*3]

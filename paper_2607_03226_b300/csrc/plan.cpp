@@ -288,11 +288,8 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
           const int64_t h = (int64_t)c * nfc + k;
           const double a = dotsa(i, h);
           const int cl = cls(a, h);
-          if (cl > 0) {
-            G += a;
-            continue;
-          }
-          if (cl == 0) continue;
+          if (cl >= 0) continue;
+          G -= a;   // G = sum over inflow faces of |s.An| (= outflow sum for a closed cell)
           int32_t ref;
           if (m.nb[h] >= 0 && !lagged[h]) {
             ref = slot[m.nb[h]];

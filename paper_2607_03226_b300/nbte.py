@@ -48,12 +48,14 @@ class nbte_solve_opts(C.Structure):
     _fields_ = [("scheme", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double),
                 ("max_iter", C.c_int32), ("n_iter", C.c_int32), ("T_init", C.POINTER(C.c_double)),
                 ("warm", C.c_int32), ("band_group", C.c_int32), ("threads_per_cell", C.c_int32),
-                ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("use_graph", C.c_int32)]
+                ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("use_graph", C.c_int32),
+                ("skip_outputs", C.c_int32), ("profile", C.c_int32)]
 
 
 class nbte_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("residual", C.c_double), ("energy_imbalance", C.c_double),
-                ("lagged_faces", C.c_int64), ("seconds", C.c_double), ("cg_iterations", C.c_int64)]
+                ("lagged_faces", C.c_int64), ("seconds", C.c_double), ("cg_iterations", C.c_int64),
+                ("sweep_seconds", C.c_double), ("sweep_launches", C.c_int64), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -204,13 +206,15 @@ def nbte_default_opts():
 
 
 def make_opts(scheme="sequential", precision="fp64", tol=1e-10, max_iter=10000, n_iter=0, T_init=None,
-              warm=False, band_group=0, threads_per_cell=0, cg_tol=0.0, cg_max_iter=0, use_graph=False):
+              warm=False, band_group=0, threads_per_cell=0, cg_tol=0.0, cg_max_iter=0, use_graph=False,
+              skip_outputs=False, profile=False):
     o = nbte_default_opts()
     o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     o.precision = {"fp64": 0, "fp32": 1}[precision] if isinstance(precision, str) else int(precision)
     o.tol, o.max_iter, o.n_iter = float(tol), int(max_iter), int(n_iter)
     o.warm, o.band_group, o.threads_per_cell = int(bool(warm)), int(band_group), int(threads_per_cell)
     o.cg_tol, o.cg_max_iter, o.use_graph = float(cg_tol), int(cg_max_iter), int(bool(use_graph))
+    o.skip_outputs, o.profile = int(bool(skip_outputs)), int(bool(profile))
     keep = None
     if T_init is not None:
         keep, o.T_init = _d(T_init)

@@ -90,11 +90,16 @@ def test_converged_fp32_sweep(nbte_mod, name):
     1e-6 of the FP64 oracle (heat-flux error recorded, bounded at 1e-4)."""
     p = CASES[name]()
     s = nbte_mod.Solver(p)
-    info = s.solve(scheme="synthetic", precision="fp32", tol=1e-10, max_iter=20000)
+    # FP32 distributions put a rounding floor of ~1e-7 under the relative
+    # increment, so the stopping tolerance sits just above it
+    info = s.solve(scheme="synthetic", precision="fp32", tol=2e-7, max_iter=20000)
     assert info["status"] == 0
     r = oracle_run(name, scheme="synthetic", tol=1e-14, max_iter=20000)
-    assert rel_T(s.temperature(0), r["T"], p.T_ref) < 1e-6
-    assert rel_q(s.heat_flux(), r["q"]) < 1e-4
+    eT = rel_T(s.temperature(0), r["T"], p.T_ref)
+    eq = rel_q(s.heat_flux(), r["q"])
+    print(f"{name}: FP32 iterations {info['iterations']} residual {info['residual']:.2e} T err {eT:.2e} q err {eq:.2e}")
+    assert eT < 1e-6
+    assert eq < 1e-4
     s.close()
 
 
