@@ -131,7 +131,11 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  * precision: 0 FP64 throughout; 1 FP32 sweep (distributions and transport
  *            coefficients FP32; moments, temperature, residual, correction
  *            and energy balance FP64).
- * tol:       stop when |T^{n+1}-T^n|_inf / |T^{n+1}-T_ref|_inf < tol.
+ * tol:       stop when |T^{n+1}-T^n|_inf / |T^{n+1}-T_ref|_inf < tol.  With
+ *            the FP32 sweep the increment bottoms out at the rounding floor
+ *            (about 1e-8..1e-7); the solve also stops, with NBTE_OK, once the
+ *            increment is below 1e-5 and has not fallen by 10% over 200
+ *            iterations (info.residual then reports that floor).
  * max_iter:  iteration cap (> 0).  n_iter > 0 instead runs exactly n_iter
  *            iterations with no convergence test.
  * T_init:    initial temperature field [n_cells] (K) or NULL (= T_ref).
@@ -139,10 +143,14 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  *            values) instead of T_init.
  * band_group: bands per work item (0 = planner's choice); threads_per_cell:
  *            threads sharing one cell's bands (0 = planner's choice, power
- *            of two <= 32); both tune the sweep kernel.
+ *            of two <= 8); cta_threads: threads per sweep CTA (0 = planner's
+ *            choice, multiple of 32 in [32, 512]); all three tune the sweep
+ *            kernel's launch shape and leave results unchanged.
  * cg_tol, cg_max_iter: relative residual and cap of the conjugate-gradient
- *            solve of the synthetic correction (0 = defaults 1e-10, 5000); the
+ *            solve of the synthetic correction (0 = defaults 1e-3, 5000); the
  *            correction only changes the rate of convergence, not the limit.
+ *            Each solve starts from the previous correction scaled by its
+ *            Galerkin factor.
  * use_graph: 1 = replay each iteration from a captured CUDA graph.
  * skip_outputs: 1 = do not compute the energy temperature, heat flux and wall
  *            heat of the last sweep (kind-0 and kind-2 temperatures remain
@@ -168,6 +176,7 @@ typedef struct {
   int32_t use_graph;
   int32_t skip_outputs;
   int32_t profile;
+  int32_t cta_threads;
 } nbte_solve_opts;
 
 /* Filled on return from nbte_solve_steady (also on NOT_CONVERGED):
@@ -219,8 +228,10 @@ int nbte_get_wall_heat(const nbte_solver* solver, int32_t tag, double* out);
  * stats[0] total levels over all directions, [1] max levels of one
  * direction, [2] max ring slots of one direction, [3] lagged faces,
  * [4] work items, [5] bands per item, [6] threads per cell, [7] device bytes
- * held by the solver.                                                      */
-int nbte_plan_stats(nbte_solver* solver, const nbte_solve_opts* opts, int64_t stats[8]);
+ * held by the solver, [8] inflow entries per cell record, [9] exported
+ * (direction, cell) values, [10] imported wall/lag values, [11] threads per
+ * sweep CTA.                                                               */
+int nbte_plan_stats(nbte_solver* solver, const nbte_solve_opts* opts, int64_t stats[12]);
 
 /* Message of the last failing call on this thread (library-owned string). */
 const char* nbte_last_error(void);

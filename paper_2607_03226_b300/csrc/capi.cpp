@@ -116,13 +116,14 @@ struct nbte_solver {
   DBuf wf_ptr, wf_val, wf_coef, dir_w, dir_s;
   // ---- band layout (depends on bands, precision and tuning)
   std::string layout_key;
-  int prec = 0, G = 1, bpt = 1, lanes = 1, n_groups = 1, Bp = 1, n_items = 0, threads = 64;
+  int prec = 0, G = 1, bpt = 1, lanes = 1, n_groups = 1, Bp = 1, n_items = 0, threads = 64, lp_off = 0;
   size_t smem = 0;
   double W = 0, beta = 0, Ctot = 0;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
   DBuf cg_r, cg_z, cg_p, cg_Ap, cg_partial, cg_bar, cg_err, cg_it, cg_res;
-  int cg_grid = 0;
+  DBuf cg_x, cg_rc, cg_yc, cg_perm, cg_agg, cg_agg_cell, cg_blk_cell, cg_blk_agg, cg_Ainv;
+  int cg_grid = 0, cg_Nc = 0, cg_Nc4 = 0;
   // ---- laplacian (synthetic)
   int64_t lap_built = -1;
   DBuf L_rp, L_col, L_val, L_dinv;
@@ -169,7 +170,9 @@ size_t device_bytes(const nbte_solver* S) {
                        &S->band_CoW, &S->band_v64, &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part,
                        &S->T, &S->Tprev, &S->Tkin, &S->Delta, &S->rhs, &S->delta, &S->Qd, &S->Vd, &S->dsum,
                        &S->accE, &S->accQ, &S->res, &S->heat, &S->cg_r, &S->cg_z, &S->cg_p, &S->cg_Ap,
-                       &S->cg_partial, &S->cg_bar, &S->cg_err, &S->cg_it, &S->cg_res, &S->L_rp, &S->L_col,
+                       &S->cg_partial, &S->cg_bar, &S->cg_err, &S->cg_it, &S->cg_res, &S->cg_x, &S->cg_rc,
+                       &S->cg_yc, &S->cg_perm, &S->cg_agg, &S->cg_agg_cell, &S->cg_blk_cell, &S->cg_blk_agg,
+                       &S->cg_Ainv, &S->L_rp, &S->L_col,
                        &S->L_val, &S->L_dinv};
   size_t t = 0;
   for (auto* b : all) t += b->bytes;
@@ -275,7 +278,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device);
   if (smem_optin <= 0) smem_optin = 48 * 1024;
-  const int Gmax = (int)((size_t)smem_optin / ((size_t)(S->max_slots + 1) * sz));
+  const int64_t ring_budget = (int64_t)smem_optin - 16 - (int64_t)(S->max_levels + 1) * 4;
+  const int Gmax = ring_budget > 0 ? (int)((size_t)ring_budget / ((size_t)(S->max_slots + 1) * sz)) : 0;
   if (Gmax < 1)
     return fail(NBTE_ERR_ARG, "one direction's live cells exceed shared memory (" + std::to_string(S->max_slots) +
                                   " ring slots); use FP32 or a smaller mesh");
@@ -304,9 +308,16 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   const int bpt = G / lanes;
   const int ng = (S->B + G - 1) / G;
   const int Bp = ng * G;
-  const int threads = std::min(512, std::max(32, ((S->max_width * lanes + 31) / 32) * 32));
+  int threads = std::min(512, std::max(32, ((S->max_width * lanes + 31) / 32) * 32));
+  if (o.cta_threads != 0) {
+    if (o.cta_threads < 32 || o.cta_threads > 512 || o.cta_threads % 32 != 0)
+      return fail(NBTE_ERR_ARG, "cta_threads must be a multiple of 32 in [32, 512]");
+    if (o.cta_threads < lanes) return fail(NBTE_ERR_ARG, "cta_threads smaller than threads_per_cell");
+    threads = o.cta_threads;
+  }
   const std::string key = std::to_string(prec) + "/" + std::to_string(G) + "/" + std::to_string(lanes) + "/" +
-                          std::to_string(S->version_bands) + "/" + std::to_string(S->plan_built);
+                          std::to_string(threads) + "/" + std::to_string(S->version_bands) + "/" +
+                          std::to_string(S->plan_built);
   if (key == S->layout_key) return NBTE_OK;
   DeviceGuard dg(S->device);
   drop_graph(S);
@@ -317,7 +328,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   S->prec = prec; S->G = G; S->lanes = lanes; S->bpt = bpt; S->n_groups = ng; S->Bp = Bp;
   S->n_items = S->D * ng;
   S->threads = threads;
-  S->smem = (size_t)(S->max_slots + 1) * G * sz;
+  S->lp_off = (int)((((size_t)(S->max_slots + 1) * G * sz) + 15) / 16 * 16);
+  S->smem = (size_t)S->lp_off + (size_t)(S->max_levels + 1) * 4;
   const int64_t N = S->mesh->m.n_cells;
   // band constants, padded bands are inert (C = 0, v = 0, 1/tau = 1)
   S->W = 0;
@@ -405,20 +417,92 @@ int ensure_laplacian(nbte_solver* S) {
   const double k1 = 0.25 * mean_abs * cv;
   Laplacian L;
   build_laplacian(m, S->bcs, kb, k1, L);
-  std::vector<double> dinv(L.diag.size());
-  for (size_t c = 0; c < dinv.size(); ++c) dinv[c] = 1.0 / L.diag[c];
-  DeviceGuard g(S->device);
-  NBTE_CK(upload(S->L_rp, L.row_ptr));
-  NBTE_CK(upload(S->L_col, L.col));
-  NBTE_CK(upload(S->L_val, L.val));
-  NBTE_CK(upload(S->L_dinv, dinv));
   const int64_t N = m.n_cells;
+  // ---- coarse space: geometric aggregates, rows reordered so each
+  // aggregate's cells are contiguous, blocks owning whole aggregates
+  std::vector<int32_t> agg;
+  int target = N <= 4096 ? (int)std::max<int64_t>(1, N / 16)
+                          : (int)std::min<int64_t>(N > 400000 ? 1536 : 1024, N / 32);
+  int Nc = build_aggregates(m, target, agg);
+  while (Nc > kMaxCoarse) {   // partly filled boxes can push the count over the target
+    target = target * 3 / 4;
+    Nc = build_aggregates(m, target, agg);
+  }
+  std::vector<int32_t> perm(N), iperm(N);
+  for (int64_t c = 0; c < N; ++c) perm[c] = (int32_t)c;
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return agg[x] < agg[y]; });
+  for (int64_t c = 0; c < N; ++c) iperm[perm[c]] = (int32_t)c;
+  std::vector<int32_t> agg_p(N), agg_cell(Nc + 1, 0);
+  for (int64_t c = 0; c < N; ++c) {
+    agg_p[c] = agg[perm[c]];
+    agg_cell[agg_p[c] + 1]++;
+  }
+  for (int k = 0; k < Nc; ++k) agg_cell[k + 1] += agg_cell[k];
+  std::vector<int32_t> rp(N + 1, 0), col;
+  std::vector<double> val, dinv(N);
+  col.reserve(L.col.size());
+  val.reserve(L.val.size());
+  std::vector<double> Ac((size_t)Nc * Nc, 0.0);
+  for (int64_t r = 0; r < N; ++r) {
+    const int32_t c = perm[r];
+    for (int32_t k = L.row_ptr[c]; k < L.row_ptr[c + 1]; ++k) {
+      col.push_back(iperm[L.col[k]]);
+      val.push_back(L.val[k]);
+      Ac[(size_t)agg[c] * Nc + agg[L.col[k]]] += L.val[k];
+    }
+    rp[r + 1] = (int32_t)col.size();
+    dinv[r] = 1.0 / L.diag[c];
+  }
+  if (!dense_spd_inverse(Ac, Nc))
+    return fail(NBTE_ERR_ARG, "synthetic correction: coarse operator is not positive definite");
+  int nsm = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device);
+  // one block per SM: the CG is latency-bound, so every SM's warps are used
+  // to shorten each block's dependent-load chains (a grid barrier costs
+  // about the same for 8 or 148 blocks)
+  const int grid = std::max(1, std::min(nsm, Nc));
+  std::vector<int32_t> blk_cell(grid + 1, 0), blk_agg(grid + 1, 0);
+  {
+    int b = 0;
+    for (int k = 0; k < Nc && b < grid; ++k) {
+      // close block b once it reaches its share of cells, keeping one
+      // aggregate for each block still to come
+      const int64_t share = (int64_t)(b + 1) * N / grid;
+      if (agg_cell[k + 1] >= share || Nc - (k + 1) <= grid - (b + 1)) {
+        blk_agg[b + 1] = k + 1;
+        ++b;
+      }
+    }
+    blk_agg[grid] = Nc;
+    for (int k = 0; k <= grid; ++k) blk_cell[k] = agg_cell[blk_agg[k]];
+  }
+  DeviceGuard g(S->device);
+  NBTE_CK(upload(S->L_rp, rp));
+  NBTE_CK(upload(S->L_col, col));
+  NBTE_CK(upload(S->L_val, val));
+  NBTE_CK(upload(S->L_dinv, dinv));
+  NBTE_CK(upload(S->cg_perm, perm));
+  NBTE_CK(upload(S->cg_agg, agg_p));
+  NBTE_CK(upload(S->cg_agg_cell, agg_cell));
+  NBTE_CK(upload(S->cg_blk_cell, blk_cell));
+  NBTE_CK(upload(S->cg_blk_agg, blk_agg));
+  const int Nc4 = (Nc + 3) / 4;
+  std::vector<float> Af((size_t)Nc * Nc4 * 4, 0.0f);
+  for (int r = 0; r < Nc; ++r)
+    for (int c = 0; c < Nc; ++c) Af[(size_t)r * Nc4 * 4 + c] = (float)Ac[(size_t)r * Nc + c];
+  NBTE_CK(upload(S->cg_Ainv, Af));
+  S->cg_Nc4 = Nc4;
+  NBTE_CK(S->cg_x.alloc(N * 8));
   NBTE_CK(S->cg_r.alloc(N * 8));
   NBTE_CK(S->cg_z.alloc(N * 8));
   NBTE_CK(S->cg_p.alloc(N * 8));
   NBTE_CK(S->cg_Ap.alloc(N * 8));
-  S->cg_grid = std::max(1, std::min(cg_max_grid(S->device), (int)((N + 255) / 256)));
-  NBTE_CK(S->cg_partial.alloc((size_t)3 * S->cg_grid * 8));
+  NBTE_CK(S->cg_rc.alloc((size_t)Nc * 8));
+  NBTE_CK(S->cg_yc.alloc((size_t)Nc * 8));
+  S->cg_grid = grid;
+  S->cg_Nc = Nc;
+  NBTE_CK(S->cg_partial.alloc((size_t)5 * S->cg_grid * 8));
+  NBTE_CK(cudaMemset(S->cg_x.p, 0, N * 8));   // no previous correction yet
   NBTE_CK(S->cg_bar.alloc(16));
   NBTE_CK(S->cg_err.alloc(16));
   NBTE_CK(S->cg_it.alloc(16));
@@ -437,6 +521,7 @@ SweepArgs<R> sweep_args(nbte_solver* S, const void* srcTQ, int full) {
   a.N = (int)S->mesh->m.n_cells;
   a.Bp = S->Bp; a.G = S->G; a.n_groups = S->n_groups; a.dim = S->mesh->m.dim;
   a.full = full;
+  a.lp_smem_off = S->lp_off;
   a.item_dir = S->item_dir.as<int32_t>();
   a.item_grp = S->item_grp.as<int32_t>();
   a.lvl_off = S->lvl_off.as<int64_t>();
@@ -515,12 +600,23 @@ UpdateArgs<R> update_args(nbte_solver* S, int mode) {
 CGArgs cg_args(nbte_solver* S, double tol, int max_it) {
   CGArgs a{};
   a.N = (int)S->mesh->m.n_cells;
+  a.Nc = S->cg_Nc;
   a.rp = S->L_rp.as<int32_t>();
   a.col = S->L_col.as<int32_t>();
   a.val = S->L_val.as<double>();
   a.dinv = S->L_dinv.as<double>();
+  a.perm = S->cg_perm.as<int32_t>();
+  a.agg = S->cg_agg.as<int32_t>();
+  a.agg_cell = S->cg_agg_cell.as<int32_t>();
+  a.blk_cell = S->cg_blk_cell.as<int32_t>();
+  a.blk_agg = S->cg_blk_agg.as<int32_t>();
+  a.Ainv = S->cg_Ainv.as<float>();
+  a.Nc4 = S->cg_Nc4;
   a.b = S->rhs.as<double>();
-  a.x = S->delta.as<double>();
+  a.x_out = S->delta.as<double>();
+  a.x = S->cg_x.as<double>();
+  a.rc = S->cg_rc.as<double>();
+  a.yc = S->cg_yc.as<double>();
   a.r = S->cg_r.as<double>();
   a.z = S->cg_z.as<double>();
   a.p = S->cg_p.as<double>();
@@ -569,7 +665,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   const Mesh& m = S->mesh->m;
   const int64_t N = m.n_cells;
   cudaStream_t st = S->stream;
-  const double cg_tol = o.cg_tol > 0 ? o.cg_tol : 1e-10;
+  const double cg_tol = o.cg_tol > 0 ? o.cg_tol : 1e-3;
   const int cg_max = o.cg_max_iter > 0 ? o.cg_max_iter : 5000;
   int64_t kernels = 0;
   // ---- initial state
@@ -641,6 +737,9 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   int status = NBTE_OK;
   // with a fixed iteration count the host only looks at the device once
   const bool check_each = !fixed || profile;
+  double best_r = INFINITY;
+  int it_best = 0;
+  bool floor_reached = false;
   auto check = [&]() -> bool {   // returns true to stop
     if (S->h_misc[0] != 0 && scheme != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the CG correction gave up");
@@ -658,7 +757,20 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     }
     r = dmax / std::max(tmax, 1e-300);
     if (tmax == 0.0 && dmax == 0.0) r = 0.0;
-    return !fixed && r < o.tol;
+    if (!fixed && r < o.tol) return true;
+    // FP32 sweep: the relative increment bottoms out at the rounding floor;
+    // stop once it is below 1e-5 and has not dropped by 10% in 200 iterations
+    if (S->prec && !fixed) {
+      if (r < 0.9 * best_r) {
+        best_r = r;
+        it_best = it;
+      }
+      if (best_r < 1e-5 && it - it_best >= 200) {
+        floor_reached = true;
+        return true;
+      }
+    }
+    return false;
   };
   while (it < limit) {
     if (use_graph) NBTE_CK(cudaGraphLaunch(S->graph, st));
@@ -682,7 +794,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   auto t1 = std::chrono::steady_clock::now();
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
-  if (status == NBTE_OK && !fixed && !(r < o.tol)) status = NBTE_ERR_NOT_CONVERGED;
+  if (status == NBTE_OK && !fixed && !(r < o.tol) && !floor_reached) status = NBTE_ERR_NOT_CONVERGED;
   S->have_results = status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED;
   S->have_outputs = false;
   // ---- moments of the last sweep: replay it with the energy/flux moments on
@@ -936,7 +1048,7 @@ static int check_opts(const nbte_solve_opts& o) {
   return NBTE_OK;
 }
 
-int nbte_plan_stats(nbte_solver* S, const nbte_solve_opts* opts, int64_t stats[8]) {
+int nbte_plan_stats(nbte_solver* S, const nbte_solve_opts* opts, int64_t stats[12]) {
   if (!S || !stats) return fail(NBTE_ERR_ARG, "null argument");
   nbte_solve_opts o;
   nbte_default_opts(&o);
@@ -958,6 +1070,10 @@ int nbte_plan_stats(nbte_solver* S, const nbte_solve_opts* opts, int64_t stats[8
   stats[5] = S->G;
   stats[6] = S->lanes;
   stats[7] = (int64_t)device_bytes(S);
+  stats[8] = S->K;
+  stats[9] = S->n_exp;
+  stats[10] = S->n_imp;
+  stats[11] = S->threads;
   return NBTE_OK;
 }
 

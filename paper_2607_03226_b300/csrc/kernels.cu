@@ -102,10 +102,35 @@ __device__ __forceinline__ R lane_sum(R x) {
 // which equals e = (e0/tau + S + v sum_in c_k e_up)/(1/tau + v G).  Written
 // this way a uniform equilibrium is reproduced exactly in any precision and
 // rounding errors scale with the local differences e_up - e0.
+//
+// The collision moment of Eq. (5) is accumulated as sum_l w_i (e - e0)/tau_l;
+// the equilibrium part sums to beta T' exactly and is added back in FP64 by
+// the update kernel, so reduced-precision partials carry only the deviation.
+//
+// Latency: everything a cell needs except its upwind ring values (its record,
+// its (T', Qdot) pair and any wall/lag import values) is loaded one level
+// ahead, so a level's critical path is: barrier, shared-memory reads,
+// arithmetic, shared-memory store.
+namespace {
+template <typename R, int K>
+struct Rec {
+  int cell, slot, ex;
+  R G;
+  int ref[K];
+  R cf[K];
+};
+template <typename R, int K, int BPT>
+struct Pre {
+  R t, q;
+  R imp[K][BPT];
+};
+}  // namespace
+
 template <typename R, int K, int BPT, int LANES>
 __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* ring = reinterpret_cast<R*>(smem_raw);
+  int* lps = reinterpret_cast<int*>(smem_raw + a.lp_smem_off);
   const int item = blockIdx.x;
   const int i = a.item_dir[item];
   const int g = a.item_grp[item];
@@ -113,7 +138,11 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
   const int lane = LANES > 1 ? (int)(threadIdx.x & (LANES - 1)) : 0;
   const int band0 = g * G + lane * BPT;
   const int N = a.N;
-
+  const int L = (int)(a.lvl_off[i + 1] - a.lvl_off[i]) - 1;
+  {
+    const int32_t* lp = a.level_ptr + a.lvl_off[i];
+    for (int t = threadIdx.x; t <= L; t += blockDim.x) lps[t] = lp[t];
+  }
   for (int t = threadIdx.x; t < G; t += blockDim.x) ring[t] = R(0);   // zero slot
 
   const double wi = a.dir_w[i];
@@ -129,8 +158,6 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
   __syncthreads();
 
   const int64_t dbase = (int64_t)i * N;
-  const int32_t* lp = a.level_ptr + a.lvl_off[i];
-  const int L = (int)(a.lvl_off[i + 1] - a.lvl_off[i]) - 1;
   const R* imp_i = a.imp + a.imp_off[i] * a.Bp + band0;
   R* exp_i = a.exp + a.exp_off[i] * a.Bp + band0;
   const int per_pass = blockDim.x / LANES;
@@ -138,59 +165,105 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
   double* part = a.part + (int64_t)item * N;
   const typename Vec2<R>::T* tq = reinterpret_cast<const typename Vec2<R>::T*>(a.srcTQ);
 
-  for (int l = 0; l < L; ++l) {
-    const int p1 = lp[l + 1];
-    for (int p = lp[l] + cidx; p < p1; p += per_pass) {
-      const int64_t q = dbase + p;
-      const int cell = a.pos_cell[q];
-      const int slot = a.pos_slot[q];
-      const int ex = a.pos_exp[q];
-      const R Gc = a.pos_G[q];
-      const typename Vec2<R>::T src = tq[cell];
-      R e0[BPT], up[BPT];
+  auto load_rec = [&](int p, Rec<R, K>& r) {
+    const int64_t q = dbase + p;
+    r.cell = a.pos_cell[q];
+    r.slot = a.pos_slot[q];
+    r.ex = a.pos_exp[q];
+    r.G = a.pos_G[q];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t qk = ((int64_t)i * K + k) * N + p;
+      r.ref[k] = a.pos_ref[qk];
+      r.cf[k] = a.pos_coef[qk];
+    }
+  };
+  auto load_pre = [&](const Rec<R, K>& r, Pre<R, K, BPT>& d) {
+    const typename Vec2<R>::T s = tq[r.cell];
+    d.t = s.x;
+    d.q = s.y;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (r.ref[k] < 0) load_bands<R, BPT>(imp_i + (int64_t)(-1 - r.ref[k]) * a.Bp, d.imp[k]);
+  };
+  auto compute = [&](const Rec<R, K>& r, const Pre<R, K, BPT>& d) {
+    R e0[BPT], up[BPT];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+      e0[b] = cw[b] * d.t;
+      up[b] = R(0);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      R e_up[BPT];
+      if (r.ref[k] >= 0) {
+        load_bands<R, BPT>(ring + r.ref[k] * G + lane * BPT, e_up);
+      } else {
+#pragma unroll
+        for (int b = 0; b < BPT; ++b) e_up[b] = d.imp[k][b];
+      }
+#pragma unroll
+      for (int b = 0; b < BPT; ++b) up[b] += r.cf[k] * (e_up[b] - e0[b]);
+    }
+    R e[BPT];
+    R nl = R(0);
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+      const R phi = (aQ[b] * d.q + vb[b] * up[b]) * recip(itau[b] + vb[b] * r.G);
+      e[b] = e0[b] + phi;
+      nl += wt[b] * phi;
+    }
+    if (r.slot >= 0) store_bands<R, BPT>(ring + r.slot * G + lane * BPT, e);
+    if (r.ex >= 0) store_bands<R, BPT>(exp_i + (int64_t)r.ex * a.Bp, e);
+    nl = lane_sum<LANES>(nl);
+    if (lane == 0) part[r.cell] = (double)nl;
+    if (a.full) {
+      R es = R(0), evs = R(0);
 #pragma unroll
       for (int b = 0; b < BPT; ++b) {
-        e0[b] = cw[b] * src.x;
-        up[b] = R(0);
+        es += e[b];
+        evs += vb[b] * e[b];
       }
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int64_t qk = ((int64_t)i * K + k) * N + p;
-        const int ref = a.pos_ref[qk];
-        const R cf = a.pos_coef[qk];
-        const R* sp = ref >= 0 ? ring + ref * G + lane * BPT : imp_i + (int64_t)(-1 - ref) * a.Bp;
-        R e_up[BPT];
-        load_bands<R, BPT>(sp, e_up);
-#pragma unroll
-        for (int b = 0; b < BPT; ++b) up[b] += cf * (e_up[b] - e0[b]);
-      }
-      R e[BPT];
-      R nl = R(0);
-#pragma unroll
-      for (int b = 0; b < BPT; ++b) {
-        e[b] = e0[b] + (aQ[b] * src.y + vb[b] * up[b]) * recip(itau[b] + vb[b] * Gc);
-        nl += wt[b] * e[b];
-      }
-      if (slot >= 0) store_bands<R, BPT>(ring + slot * G + lane * BPT, e);
-      if (ex >= 0) store_bands<R, BPT>(exp_i + (int64_t)ex * a.Bp, e);
-      nl = lane_sum<LANES>(nl);
-      if (lane == 0) part[cell] = (double)nl;
-      if (a.full) {
-        R es = R(0), evs = R(0);
-#pragma unroll
-        for (int b = 0; b < BPT; ++b) {
-          es += e[b];
-          evs += vb[b] * e[b];
-        }
-        es = lane_sum<LANES>(es);
-        evs = lane_sum<LANES>(evs);
-        if (lane == 0) {
-          atomicAdd(a.accE + cell, wi * (double)es);
-          for (int d = 0; d < a.dim; ++d) atomicAdd(a.accQ + (int64_t)cell * a.dim + d, wi * a.dir_s[i * 3 + d] * (double)evs);
-        }
+      es = lane_sum<LANES>(es);
+      evs = lane_sum<LANES>(evs);
+      if (lane == 0) {
+        atomicAdd(a.accE + r.cell, wi * (double)es);
+        for (int d = 0; d < a.dim; ++d)
+          atomicAdd(a.accQ + (int64_t)r.cell * a.dim + d, wi * a.dir_s[i * 3 + d] * (double)evs);
       }
     }
+  };
+
+  // pipeline: r0/d0 = this level's first-pass cell, r1 = next level's record
+  Rec<R, K> r0, r1;
+  Pre<R, K, BPT> d0;
+  bool v0 = L > 0 && lps[0] + cidx < lps[1];
+  bool v1 = L > 1 && lps[1] + cidx < lps[2];
+  if (v0) {
+    load_rec(lps[0] + cidx, r0);
+    load_pre(r0, d0);
+  }
+  if (v1) load_rec(lps[1] + cidx, r1);
+  for (int l = 0; l < L; ++l) {
+    Pre<R, K, BPT> d1;
+    if (v1) load_pre(r1, d1);                       // level l+1, issued now
+    Rec<R, K> r2;
+    const bool v2 = l + 2 < L && lps[l + 2] + cidx < lps[l + 3];
+    if (v2) load_rec(lps[l + 2] + cidx, r2);        // level l+2, issued now
+    if (v0) compute(r0, d0);
+    for (int p = lps[l] + cidx + per_pass; p < lps[l + 1]; p += per_pass) {   // wide levels
+      Rec<R, K> rw;
+      Pre<R, K, BPT> dw;
+      load_rec(p, rw);
+      load_pre(rw, dw);
+      compute(rw, dw);
+    }
     __syncthreads();
+    r0 = r1;
+    d0 = d1;
+    v0 = v1;
+    r1 = r2;
+    v1 = v2;
   }
 }
 
@@ -357,7 +430,10 @@ __global__ void update_kernel(const UpdateArgs<R> a) {
     if (a.mode == 0 || a.mode == 3) {
       double s = 0.0;
       for (int it = 0; it < a.n_items; ++it) s += a.part[(int64_t)it * a.N + c];
-      TL = s * a.inv_beta;                        // Eq. (5), as a deviation from T_ref
+      // Eq. (5) as a deviation from T_ref: the equilibrium part of every
+      // distribution sums to beta T'_used, T'_used being the (possibly
+      // reduced-precision) temperature the sweep emitted from
+      TL = (double)a.srcTQ_next[2 * c] + s * a.inv_beta;
       a.Tkin[c] = TL;
     } else {
       TL = a.Tkin[c];
@@ -400,36 +476,32 @@ void launch_fill_srcTQ(R* srcTQ, const double* T, const double* Q, int N, cudaSt
 
 // ============================================================================ CG
 namespace {
-constexpr int kCGThreads = 256;
 constexpr unsigned long long kSpinLimit = 1ull << 25;   // ~seconds with nanosleep
 
-// Grid barrier for a cooperative launch (all blocks co-resident).  Every wait
-// is bounded: on timeout the error word is set and every block leaves.
+// Grid barrier for a cooperative launch (all blocks co-resident).  bar[0] is
+// a counter that only grows: a block arriving as number k waits until the
+// counter reaches the next multiple of the block count.  The host zeroes it
+// before each launch.  The wait spins tightly first, then backs off, and is
+// bounded: on timeout the error word is set and every block leaves.
 __device__ bool grid_sync(unsigned* bar, int32_t* err, unsigned nblocks) {
   __shared__ int s_abort;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned g0 = *vgen;
     __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
+    const unsigned old = atomicAdd(bar, 1u);
+    const unsigned target = (old / nblocks + 1) * nblocks;
+    volatile unsigned* vc = bar;
     int abort = 0;
-    if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*vgen == g0) {
-        if (++spins > kSpinLimit) {
-          atomicExch(err, (int32_t)DEV_BARRIER_TIMEOUT);
-          abort = 1;
-          break;
-        }
-        __nanosleep(64);
+    unsigned long long spins = 0;
+    while ((int)(*vc - target) < 0) {
+      if (++spins > kSpinLimit) {
+        atomicExch(err, (int32_t)DEV_BARRIER_TIMEOUT);
+        abort = 1;
+        break;
       }
-      __threadfence();
+      if (spins > 2048) __nanosleep(32);
     }
+    __threadfence();
     if (*(volatile int32_t*)err != 0) abort = 1;
     s_abort = abort;
   }
@@ -437,110 +509,199 @@ __device__ bool grid_sync(unsigned* bar, int32_t* err, unsigned nblocks) {
   return s_abort != 0;
 }
 
+// block-wide sum, result valid in every thread
 __device__ double block_sum(double x) {
   __shared__ double sh[32];
+  __shared__ double tot;
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) sh[w] = x;
   __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
-  return r;  // valid in thread 0
+  if (w == 0) {
+    double y = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    if (l == 0) tot = y;
+  }
+  __syncthreads();
+  return tot;
 }
 
-// sum of the per-block partials, same order in every block (deterministic)
+// sum of the per-block partials written before the last grid barrier: every
+// block reads them with the same lane split and the same shuffle tree, so all
+// blocks get the same (deterministic) value
 __device__ double grid_total(const double* partial, int slot) {
   __shared__ double tot;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += ((volatile const double*)partial)[slot * gridDim.x + b];
-    tot = s;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(partial + slot * gridDim.x + b);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) tot = s;
   }
   __syncthreads();
   const double r = tot;
   __syncthreads();
   return r;
 }
+
+__device__ __forceinline__ double warp_sum(double s) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
 }  // namespace
 
+// Persistent two-level PCG (one launch per synthetic correction).  Three grid
+// barriers per iteration: after p.Ap, after the aggregate restriction, after
+// r.z.  A p is updated as A z + beta A p_old so that the SpMV only needs z,
+// which is complete at the r.z barrier.
 __global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
-  const int n = a.N;
-  const int stride = gridDim.x * blockDim.x;
-  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nb = gridDim.x;
-  double rz_l = 0.0, bb_l = 0.0;
-  for (int c = t0; c < n; c += stride) {
-    const double r = a.b[c];
-    const double z = a.dinv[c] * r;
-    a.x[c] = 0.0;
-    a.r[c] = r;
-    a.z[c] = z;
-    a.p[c] = z;
-    rz_l += r * z;
-    bb_l += r * r;
+  const int c0 = a.blk_cell[blockIdx.x], c1 = a.blk_cell[blockIdx.x + 1];
+  const int a0 = a.blk_agg[blockIdx.x], a1 = a.blk_agg[blockIdx.x + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+
+  // aggregate restriction of r for the block's own aggregates
+  auto restrict_r = [&]() {
+    for (int g = a0 + warp; g < a1; g += nwarp) {
+      double s = 0.0;
+      for (int c = a.agg_cell[g] + lane; c < a.agg_cell[g + 1]; c += 32) s += a.r[c];
+      s = warp_sum(s);
+      if (lane == 0) a.rc[g] = s;
+    }
+  };
+  // coarse correction rows for the block's own aggregates: the restricted
+  // residual is staged in shared memory, the (symmetric, FP32-stored) coarse
+  // inverse is read four entries per load, sums are FP64
+  __shared__ double rc_s[kMaxCoarse];
+  auto coarse_rows = [&]() {
+    const int nc4 = a.Nc4;
+    for (int k = threadIdx.x; k < 4 * nc4; k += blockDim.x) rc_s[k] = k < a.Nc ? __ldcg(a.rc + k) : 0.0;
+    __syncthreads();
+    for (int g = a0 + warp; g < a1; g += nwarp) {
+      const float4* row = reinterpret_cast<const float4*>(a.Ainv + (int64_t)g * nc4 * 4);
+      double s = 0.0;
+#pragma unroll 4
+      for (int k = lane; k < nc4; k += 32) {
+        const float4 v = __ldg(row + k);
+        const double* r = rc_s + 4 * k;
+        s += (double)v.x * r[0] + (double)v.y * r[1] + (double)v.z * r[2] + (double)v.w * r[3];
+      }
+      s = warp_sum(s);
+      if (lane == 0) a.yc[g] = s;
+    }
+  };
+  auto spmv = [&](const double* v, int c) {
+    double y = 0.0;
+    for (int k = a.rp[c]; k < a.rp[c + 1]; ++k) y += a.val[k] * __ldcg(v + a.col[k]);
+    return y;
+  };
+
+  // ---- initial guess: the previous correction scaled by its Galerkin
+  // factor theta = (x_prev . b) / (x_prev . A x_prev) (zero on first use);
+  // successive synthetic corrections share their slowly decaying shape
+  double xb_l = 0.0, xax_l = 0.0, bb_l = 0.0;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const double b = a.b[a.perm[c]];
+    const double xp = a.x[c];
+    const double q = spmv(a.x, c);
+    a.r[c] = b;
+    a.Ap[c] = q;   // A x_prev, scaled below
+    xb_l += xp * b;
+    xax_l += xp * q;
+    bb_l += b * b;
   }
-  double s = block_sum(rz_l);
+  double s = block_sum(xb_l);
+  if (threadIdx.x == 0) a.partial[0 * nb + blockIdx.x] = s;
+  s = block_sum(xax_l);
   if (threadIdx.x == 0) a.partial[1 * nb + blockIdx.x] = s;
   s = block_sum(bb_l);
-  if (threadIdx.x == 0) a.partial[2 * nb + blockIdx.x] = s;
+  if (threadIdx.x == 0) a.partial[3 * nb + blockIdx.x] = s;
   if (grid_sync(a.bar, a.err, nb)) return;
-  double rz = grid_total(a.partial, 1);
-  const double bb = grid_total(a.partial, 2);
+  const double xb = grid_total(a.partial, 0);
+  const double xax = grid_total(a.partial, 1);
+  const double bb = grid_total(a.partial, 3);
+  const double theta = (xax > 0.0 && isfinite(xb / xax)) ? xb / xax : 0.0;
+  double rr0_l = 0.0;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const double r = a.r[c] - theta * a.Ap[c];
+    a.r[c] = r;
+    a.x[c] = theta * a.x[c];
+    rr0_l += r * r;
+  }
+  __syncthreads();
+  restrict_r();
+  s = block_sum(rr0_l);
+  if (threadIdx.x == 0) a.partial[4 * nb + blockIdx.x] = s;   // own slot: 0-3 may still be read
+  if (grid_sync(a.bar, a.err, nb)) return;
+  const double rr0 = grid_total(a.partial, 4);
   int it = 0;
-  double rr = bb;
-  if (bb > 0.0) {
+  double rr = rr0;
+  if (bb > 0.0 && rr0 > a.tol * a.tol * bb) {
+    coarse_rows();
+    __syncthreads();
+    double rz_l = 0.0;
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      const double z = a.dinv[c] * a.r[c] + a.yc[a.agg[c]];
+      a.z[c] = z;
+      a.p[c] = z;
+      rz_l += a.r[c] * z;
+    }
+    s = block_sum(rz_l);
+    if (threadIdx.x == 0) a.partial[2 * nb + blockIdx.x] = s;
+    if (grid_sync(a.bar, a.err, nb)) return;
+    double rz = grid_total(a.partial, 2);
+    double beta = 0.0;
     for (it = 0; it < a.max_it;) {
+      // p = z + beta p ; Ap = A z + beta Ap
       double pap_l = 0.0;
-      for (int c = t0; c < n; c += stride) {
-        double y = 0.0;
-        for (int k = a.rp[c]; k < a.rp[c + 1]; ++k) y += a.val[k] * __ldcg(a.p + a.col[k]);
-        a.Ap[c] = y;
-        pap_l += a.p[c] * y;
+      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const double az = spmv(a.z, c);
+        const double p = it == 0 ? a.z[c] : a.z[c] + beta * a.p[c];
+        const double ap = it == 0 ? az : az + beta * a.Ap[c];
+        a.p[c] = p;
+        a.Ap[c] = ap;
+        pap_l += p * ap;
       }
       s = block_sum(pap_l);
       if (threadIdx.x == 0) a.partial[0 * nb + blockIdx.x] = s;
       if (grid_sync(a.bar, a.err, nb)) return;
       const double alpha = rz / grid_total(a.partial, 0);
-      double rzn_l = 0.0, rr_l = 0.0;
-      for (int c = t0; c < n; c += stride) {
+      double rr_l = 0.0;
+      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         a.x[c] += alpha * a.p[c];
         const double r = a.r[c] - alpha * a.Ap[c];
-        const double z = a.dinv[c] * r;
         a.r[c] = r;
-        a.z[c] = z;
-        rzn_l += r * z;
         rr_l += r * r;
       }
-      s = block_sum(rzn_l);
-      if (threadIdx.x == 0) a.partial[1 * nb + blockIdx.x] = s;
+      __syncthreads();
+      restrict_r();
       s = block_sum(rr_l);
-      if (threadIdx.x == 0) a.partial[2 * nb + blockIdx.x] = s;
+      if (threadIdx.x == 0) a.partial[1 * nb + blockIdx.x] = s;
       if (grid_sync(a.bar, a.err, nb)) return;
-      const double rzn = grid_total(a.partial, 1);
-      rr = grid_total(a.partial, 2);
+      rr = grid_total(a.partial, 1);
       ++it;
       if (!(rr > a.tol * a.tol * bb)) break;
-      const double beta = rzn / rz;
-      rz = rzn;
-      for (int c = t0; c < n; c += stride) a.p[c] = a.z[c] + beta * a.p[c];
+      coarse_rows();
+      __syncthreads();
+      double rz_n = 0.0;
+      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const double z = a.dinv[c] * a.r[c] + a.yc[a.agg[c]];
+        a.z[c] = z;
+        rz_n += a.r[c] * z;
+      }
+      s = block_sum(rz_n);
+      if (threadIdx.x == 0) a.partial[2 * nb + blockIdx.x] = s;
       if (grid_sync(a.bar, a.err, nb)) return;
+      const double rzn = grid_total(a.partial, 2);
+      beta = rzn / rz;
+      rz = rzn;
     }
-  } else {
-    for (int c = t0; c < n; c += stride) a.x[c] = 0.0;
   }
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) a.x_out[a.perm[c]] = a.x[c];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *a.it_out += it;
     *a.res_out = bb > 0.0 ? sqrt(rr / bb) : 0.0;
   }
-}
-
-int cg_max_grid(int device) {
-  int nsm = 0, per_sm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, kCGThreads, 0);
-  return nsm * (per_sm < 1 ? 1 : per_sm);
 }
 
 cudaError_t launch_cg(const CGArgs& a, int grid, cudaStream_t st) {

@@ -14,6 +14,7 @@ template <typename R>
 struct SweepArgs {
   int N, Bp, G, n_groups, dim;
   int full;                      // also accumulate E and q (atomics)
+  int lp_smem_off;               // byte offset of the level pointers after the ring
   const int32_t* item_dir;       // [n_items]
   const int32_t* item_grp;       // [n_items]
   const int64_t* lvl_off;        // [D+1]
@@ -89,19 +90,34 @@ struct UpdateArgs {
 template <typename R>
 void launch_update(const UpdateArgs<R>& a, cudaStream_t st);
 
+// Two-level preconditioned CG on the synthetic-correction Laplacian.  Rows
+// are in aggregate order (cells of one aggregate contiguous); block k owns
+// aggregates [blk_agg[k], blk_agg[k+1]) and their cells
+// [blk_cell[k], blk_cell[k+1]).  M^{-1} r = D^{-1} r + P Ac^{-1} P^T r with P
+// the piecewise-constant aggregate prolongation and Ac^{-1} dense.
 struct CGArgs {
-  int N;
+  int N, Nc;
   const int32_t* rp;
   const int32_t* col;
   const double* val;
   const double* dinv;
-  const double* b;
-  double* x;
+  const int32_t* perm;           // aggregate-order row -> internal cell
+  const int32_t* agg;            // aggregate of each row
+  const int32_t* agg_cell;       // [Nc+1] first row of each aggregate
+  const int32_t* blk_cell;       // [grid+1]
+  const int32_t* blk_agg;        // [grid+1]
+  const float* Ainv;             // [Nc * Nc4*4], rows padded with zeros to Nc4*4
+  int Nc4;                       // ceil(Nc / 4)
+  const double* b;               // right-hand side, internal order
+  double* x_out;                 // solution, internal order
+  double* x;                     // work vectors in aggregate order
   double* r;
   double* z;
   double* p;
   double* Ap;
-  double* partial;               // [3*grid]
+  double* rc;                    // [Nc]
+  double* yc;                    // [Nc]
+  double* partial;               // [5*grid]
   unsigned* bar;                 // [2] count, generation
   int32_t* err;
   double tol;
@@ -111,7 +127,8 @@ struct CGArgs {
 };
 // persistent cooperative PCG; returns cudaError of the launch
 cudaError_t launch_cg(const CGArgs& a, int grid, cudaStream_t st);
-int cg_max_grid(int device);
+constexpr int kCGThreads = 1024;
+constexpr int kMaxCoarse = 2048;   // aggregates of the coarse space (rc staged in shared memory)
 
 template <typename R>
 struct WallHeatArgs {

@@ -100,4 +100,10 @@ struct Laplacian {
 void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bulk, double k1,
                      Laplacian& L);
 
+// geometric aggregates (boxes of the cell-centroid bounding box); returns the
+// number of non-empty aggregates, agg[c] in [0, n)
+int build_aggregates(const Mesh& m, int target, std::vector<int32_t>& agg);
+// dense SPD inverse in place (row-major); false if not positive definite
+bool dense_spd_inverse(std::vector<double>& A, int n);
+
 }  // namespace nbte
