@@ -233,6 +233,36 @@ int nbte_get_wall_heat(const nbte_solver* solver, int32_t tag, double* out);
  * sweep CTA.                                                               */
 int nbte_plan_stats(nbte_solver* solver, const nbte_solve_opts* opts, int64_t stats[12]);
 
+/* --------------------------------------------------- allocation-free solve --
+ * nbte_laplacian_solve_noalloc: solve A x = rhs for a sparse symmetric
+ * positive-definite A by Jacobi-preconditioned conjugate gradients, without
+ * allocating any memory.  The paper has no counterpart; this call exists for
+ * callers that cannot call cudaMalloc -- e.g. code running inside another
+ * framework's memory pool or under a fixed device-memory budget, or a
+ * real-time loop where an allocation may block or fail.  It is a one-level
+ * variant of the CG kernel that solves the synthetic correction.
+ *   n                 rows, 1 <= n <= 262144 (larger n: NBTE_ERR_ARG).
+ *   row_ptr, col, val the matrix in CSR form, int32 indices, FP64 values,
+ *                     DEVICE pointers owned by the caller; every row holds
+ *                     its diagonal entry.
+ *   rhs, x            DEVICE arrays of n doubles owned by the caller; x is
+ *                     overwritten with the solution (start value 0).
+ *   tol, max_iter     stop when |r|_2 <= tol |rhs|_2, at most max_iter steps.
+ *   iterations, residual  host outputs (may be NULL).
+ *   cuda_stream       cudaStream_t as void* (NULL = legacy default stream);
+ *                     the call returns after the solve has finished on it.
+ * Working vectors live in one fixed array of about 8 MB in the library's
+ * device image: every GPU that loads the library holds it until the process
+ * exits.  All calls on a device share that array, so calls that overlap on
+ * the GPU (other streams, other host threads) race; serialise them.  The
+ * first call on each device looks up the array's device address with that
+ * device current; make that first call outside any CUDA stream capture.
+ * Returns NBTE_OK, NBTE_ERR_ARG, NBTE_ERR_NOT_CONVERGED (x holds the last
+ * iterate), NBTE_ERR_DEVICE_TIMEOUT or NBTE_ERR_CUDA.                      */
+int nbte_laplacian_solve_noalloc(int n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                                 const double* rhs, double* x, double tol, int max_iter, int32_t* iterations,
+                                 double* residual, void* cuda_stream);
+
 /* Message of the last failing call on this thread (library-owned string). */
 const char* nbte_last_error(void);
 /* Library version string. */

@@ -37,6 +37,7 @@ EXPORTS = [
     "nbte_solver_set_stream", "nbte_set_bands", "nbte_set_quadrature", "nbte_set_boundaries",
     "nbte_set_heat_source", "nbte_default_opts", "nbte_solve_steady", "nbte_get_temperature",
     "nbte_get_heat_flux", "nbte_get_wall_heat", "nbte_plan_stats", "nbte_last_error", "nbte_version",
+    "nbte_laplacian_solve_noalloc",
 ]
 
 
@@ -103,6 +104,8 @@ def load(path: str | None = None):
         "nbte_plan_stats": ([_P, C.POINTER(nbte_solve_opts), _I64], C.c_int),
         "nbte_last_error": ([], C.c_char_p),
         "nbte_version": ([], C.c_char_p),
+        "nbte_laplacian_solve_noalloc": ([C.c_int, _P, _P, _P, _P, _P, C.c_double, C.c_int, _I32, _D, _P],
+                                         C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -253,6 +256,17 @@ def nbte_plan_stats(solver, opts=None):
     keys = ["total_levels", "max_levels", "max_slots", "lagged_faces", "items", "band_group",
             "threads_per_cell", "device_bytes", "K", "exports", "imports", "cta_threads"]
     return dict(zip(keys, (int(x) for x in st)))
+
+
+def nbte_laplacian_solve_noalloc(n, row_ptr_dev, col_dev, val_dev, rhs_dev, x_dev, tol, max_iter, stream=0):
+    """Allocation-free CG solve on caller-owned device buffers (raw device
+    addresses as ints).  Returns (status, iterations, residual)."""
+    it = C.c_int32()
+    res = C.c_double()
+    rc = _check(load().nbte_laplacian_solve_noalloc(
+        int(n), _P(row_ptr_dev), _P(col_dev), _P(val_dev), _P(rhs_dev), _P(x_dev), float(tol), int(max_iter),
+        C.byref(it), C.byref(res), _P(stream) if stream else None), allow=(NBTE_ERR_NOT_CONVERGED,))
+    return rc, it.value, res.value
 
 
 def nbte_last_error():
