@@ -141,11 +141,17 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  * T_init:    initial temperature field [n_cells] (K) or NULL (= T_ref).
  * warm:      1 = continue from the solver's current state (T and wall
  *            values) instead of T_init.
- * band_group: bands per work item (0 = planner's choice); threads_per_cell:
- *            threads sharing one cell's bands (0 = planner's choice, power
- *            of two <= 8); cta_threads: threads per sweep CTA (0 = planner's
- *            choice, multiple of 32 in [32, 512]); all three tune the sweep
- *            kernel's launch shape and leave results unchanged.
+ * band_group: bands per work item: 1, 2, 4 or 8 with an FP32 sweep, 1, 2
+ *            or 4 in FP64.  cta_threads: threads per sweep CTA, a multiple of
+ *            32 in [64, 544]; one copy warp plus one consumer thread per
+ *            position of a pipelined chunk.  threads_per_cell: 0 or 1 (one
+ *            thread carries all bands of its group for a cell).  With
+ *            band_group = cta_threads = 0 the first solve times every
+ *            feasible layout once (a few sweeps on scratch state) and keeps
+ *            the fastest for this plan, band table and precision.  None of
+ *            them changes results beyond rounding order; an infeasible
+ *            choice (its ring or stages exceed shared memory) is
+ *            NBTE_ERR_ARG.
  * cg_tol, cg_max_iter: relative residual and cap of the conjugate-gradient
  *            solve of the synthetic correction (0 = defaults 1e-3, 5000); the
  *            correction only changes the rate of convergence, not the limit.
@@ -230,7 +236,9 @@ int nbte_get_wall_heat(const nbte_solver* solver, int32_t tag, double* out);
  * [4] work items, [5] bands per item, [6] threads per cell, [7] device bytes
  * held by the solver, [8] inflow entries per cell record, [9] exported
  * (direction, cell) values, [10] imported wall/lag values, [11] threads per
- * sweep CTA.                                                               */
+ * sweep CTA.  With band_group = cta_threads = 0 and bands, quadrature and
+ * boundaries set, this runs the layout autotuner first (see
+ * nbte_solve_opts), so the layout reported is the one a solve will use.     */
 int nbte_plan_stats(nbte_solver* solver, const nbte_solve_opts* opts, int64_t stats[12]);
 
 /* --------------------------------------------------- allocation-free solve --

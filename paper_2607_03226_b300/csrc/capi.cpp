@@ -56,8 +56,9 @@ struct DBuf {
     bytes = 0;
   }
   cudaError_t alloc(size_t n) {
-    release();
     if (n == 0) n = 16;
+    if (p && n == bytes) return cudaSuccess;
+    release();
     cudaError_t e = cudaMalloc(&p, n);
     if (e == cudaSuccess) bytes = n;
     else p = nullptr;
@@ -88,6 +89,14 @@ struct nbte_mesh {
   Mesh m;
 };
 
+// sweep launch shape picked by timing candidates (band group, chunk length)
+struct Tuned {
+  bool valid = false;
+  int G = 0, cap = 0;
+  int64_t key = -1;
+  double ms = 0.0;
+};
+
 struct nbte_solver {
   const nbte_mesh* mesh = nullptr;
   int device = 0;
@@ -110,15 +119,16 @@ struct nbte_solver {
   int64_t n_exp = 0, n_imp = 0, n_dbf = 0, n_wf = 0, lagged = 0, total_levels = 0;
   int max_levels = 0, max_slots = 0, max_width = 0;
   std::vector<int32_t> wf_tag_h;
-  std::vector<double> pos_G_h, pos_coef_h;   // kept for the FP32 copies
-  DBuf lvl_off, level_ptr, pos_cell, pos_slot, pos_exp, pos_ref, pos_G64, pos_coef64, pos_G32, pos_coef32;
+  Plan plan;                                  // host copy: records are packed per precision from it
   DBuf exp_off, imp_off, exp_cell, imp_kind, imp_dbf, imp_src, imp_par, dif_ptr, dif_src, dif_wt;
   DBuf wf_ptr, wf_val, wf_coef, dir_w, dir_s;
   // ---- band layout (depends on bands, precision and tuning)
-  std::string layout_key;
-  int prec = 0, G = 1, bpt = 1, lanes = 1, n_groups = 1, Bp = 1, n_items = 0, threads = 64, lp_off = 0;
+  std::string layout_key, rec_key, chunk_key;
+  int prec = 0, G = 1, Gpad = 4, n_groups = 1, Bp = 1, n_items = 0, threads = 160, n_stages = 4;
+  int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0;
   size_t smem = 0;
   double W = 0, beta = 0, Ctot = 0;
+  DBuf rec, chunks, chunk_off, tqp;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
   DBuf cg_r, cg_z, cg_p, cg_Ap, cg_partial, cg_bar, cg_err, cg_it, cg_res;
@@ -127,6 +137,8 @@ struct nbte_solver {
   // ---- laplacian (synthetic)
   int64_t lap_built = -1;
   DBuf L_rp, L_col, L_val, L_dinv;
+  // ---- autotuned sweep layout per precision
+  Tuned tuned[2];
   // ---- state
   bool have_state = false;
   bool have_results = false;   // T (kind 0, 2) of the last solve
@@ -162,8 +174,7 @@ struct DeviceGuard {
 };
 
 size_t device_bytes(const nbte_solver* S) {
-  const DBuf* all[] = {&S->lvl_off, &S->level_ptr, &S->pos_cell, &S->pos_slot, &S->pos_exp, &S->pos_ref,
-                       &S->pos_G64, &S->pos_coef64, &S->pos_G32, &S->pos_coef32, &S->exp_off, &S->imp_off,
+  const DBuf* all[] = {&S->rec, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
                        &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
                        &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
@@ -205,27 +216,23 @@ int ensure_plan(nbte_solver* S) {
       for (int64_t p = 0; p < N && !any; ++p) any = P.pos_coef[off + p] != 0.0 || P.pos_ref[off + p] != 0;
       if (any) { K = k + 1; break; }
     }
-  std::vector<int32_t> ref((size_t)P.D * K * N);
-  std::vector<double> coef((size_t)P.D * K * N);
-  for (int i = 0; i < P.D; ++i)
-    for (int k = 0; k < K; ++k) {
-      std::copy_n(P.pos_ref.begin() + ((size_t)i * P.K + k) * N, N, ref.begin() + ((size_t)i * K + k) * N);
-      std::copy_n(P.pos_coef.begin() + ((size_t)i * P.K + k) * N, N, coef.begin() + ((size_t)i * K + k) * N);
-    }
-  P.pos_ref.clear(); P.pos_ref.shrink_to_fit();
-  P.pos_coef.clear(); P.pos_coef.shrink_to_fit();
+  if (K < P.K) {
+    std::vector<int32_t> ref((size_t)P.D * K * N);
+    std::vector<double> coef((size_t)P.D * K * N);
+    for (int i = 0; i < P.D; ++i)
+      for (int k = 0; k < K; ++k) {
+        std::copy_n(P.pos_ref.begin() + ((size_t)i * P.K + k) * N, N, ref.begin() + ((size_t)i * K + k) * N);
+        std::copy_n(P.pos_coef.begin() + ((size_t)i * P.K + k) * N, N, coef.begin() + ((size_t)i * K + k) * N);
+      }
+    P.pos_ref.swap(ref);
+    P.pos_coef.swap(coef);
+    P.K = K;
+  }
   DeviceGuard g(S->device);
   drop_graph(S);
-  S->pos_G32.release();
-  S->pos_coef32.release();
-  NBTE_CK(upload(S->lvl_off, P.lvl_off));
-  NBTE_CK(upload(S->level_ptr, P.level_ptr));
-  NBTE_CK(upload(S->pos_cell, P.pos_cell));
-  NBTE_CK(upload(S->pos_slot, P.pos_slot));
-  NBTE_CK(upload(S->pos_exp, P.pos_exp));
-  NBTE_CK(upload(S->pos_ref, ref));
-  NBTE_CK(upload(S->pos_G64, P.pos_G));
-  NBTE_CK(upload(S->pos_coef64, coef));
+  S->rec.release();
+  S->rec_key.clear();
+  S->chunk_key.clear();
   NBTE_CK(upload(S->exp_off, P.exp_off));
   NBTE_CK(upload(S->imp_off, P.imp_off));
   NBTE_CK(upload(S->exp_cell, P.exp_cell));
@@ -241,8 +248,6 @@ int ensure_plan(nbte_solver* S) {
   NBTE_CK(upload(S->wf_coef, P.wf_coef));
   NBTE_CK(upload(S->dir_w, S->w));
   NBTE_CK(upload(S->dir_s, S->s));
-  S->pos_G_h = std::move(P.pos_G);
-  S->pos_coef_h = std::move(coef);
   S->K = K;
   S->D_plan = P.D;
   S->n_exp = P.exp_off.back();
@@ -255,81 +260,181 @@ int ensure_plan(nbte_solver* S) {
   S->max_levels = P.max_levels;
   S->max_slots = P.max_slots;
   S->max_width = P.max_width_all;
+  S->plan = std::move(P);
   S->plan_built = S->version_plan;
   S->layout_key.clear();
   S->have_state = false;
   return NBTE_OK;
 }
 
-int ensure_fp32_coefs(nbte_solver* S) {
-  if (S->pos_G32.p) return NBTE_OK;
-  NBTE_CK(upload(S->pos_G32, to_float(S->pos_G_h)));
-  NBTE_CK(upload(S->pos_coef32, to_float(S->pos_coef_h)));
+// Packed position records of precision R (see layout.h), direction-major.
+template <typename R>
+int ensure_records(nbte_solver* S) {
+  const std::string key = std::to_string(sizeof(R)) + "/" + std::to_string(S->plan_built);
+  if (key == S->rec_key && S->rec.p) return NBTE_OK;
+  const Plan& P = S->plan;
+  const int K = P.K;
+  const RecLayout L = rec_layout((int)sizeof(R), K);
+  const size_t n = (size_t)P.D * P.N;
+  std::vector<unsigned char> buf(n * L.size, 0);
+  for (int i = 0; i < P.D; ++i)
+    for (int64_t p = 0; p < P.N; ++p) {
+      const size_t q = (size_t)i * P.N + p;
+      unsigned char* r = buf.data() + q * L.size;
+      std::memcpy(r, &P.pos_cell[q], 4);
+      std::memcpy(r + 4, &P.pos_slot[q], 4);
+      std::memcpy(r + 8, &P.pos_exp[q], 4);
+      const R G = (R)P.pos_G[q];
+      std::memcpy(r + L.off_G, &G, sizeof(R));
+      for (int k = 0; k < K; ++k) {
+        const size_t qk = ((size_t)i * K + k) * P.N + p;
+        const R c = (R)P.pos_coef[qk];
+        std::memcpy(r + L.off_ref + 4 * k, &P.pos_ref[qk], 4);
+        std::memcpy(r + L.off_coef + sizeof(R) * k, &c, sizeof(R));
+      }
+    }
+  NBTE_CK(upload(S->rec, buf));
+  S->rec_key = key;
+  return NBTE_OK;
+}
+
+// Chunks of at most cap positions inside one level, with each chunk's slice
+// of the direction's imports (imports are numbered in position order).
+int ensure_chunks(nbte_solver* S, int cap) {
+  const std::string key = std::to_string(cap) + "/" + std::to_string(S->plan_built);
+  if (key == S->chunk_key && S->chunks.p) return NBTE_OK;
+  const Plan& P = S->plan;
+  std::vector<Chunk> ch;
+  std::vector<int64_t> off(P.D + 1, 0);
+  for (int i = 0; i < P.D; ++i) {
+    int32_t imp = 0;
+    const int32_t* lp = P.level_ptr.data() + P.lvl_off[i];
+    const int L = (int)(P.lvl_off[i + 1] - P.lvl_off[i]) - 1;
+    for (int l = 0; l < L; ++l)
+      for (int32_t p0 = lp[l]; p0 < lp[l + 1]; p0 += cap) {
+        const int32_t p1 = std::min(lp[l + 1], p0 + cap);
+        int32_t nimp = 0;
+        for (int32_t p = p0; p < p1; ++p)
+          for (int k = 0; k < P.K; ++k) nimp += P.pos_ref[((size_t)i * P.K + k) * P.N + p] < 0;
+        Chunk c;
+        c.pos = p0;
+        c.len = p1 - p0;
+        c.imp = imp;
+        c.nimp_end = nimp | (p1 == lp[l + 1] ? (1 << 30) : 0);
+        ch.push_back(c);
+        imp += nimp;
+      }
+    if (imp != P.imp_off[i + 1] - P.imp_off[i]) return fail(NBTE_ERR_MESH, "internal: import numbering");
+    off[i + 1] = (int64_t)ch.size();
+  }
+  NBTE_CK(upload(S->chunks, ch));
+  NBTE_CK(upload(S->chunk_off, off));
+  S->chunk_key = key;
   return NBTE_OK;
 }
 
 bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+int64_t tune_key(const nbte_solver* S) { return S->plan_built * 1000003 + S->version_bands; }
+
 // ------------------------------------------------------------------ layout
 int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   if (S->B <= 0) return fail(NBTE_ERR_STATE, "nbte_set_bands must be called before solving");
   const int prec = o.precision;
-  const size_t sz = prec ? 4 : 8;
-  int smem_optin = 0;
-  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, S->device);
-  if (smem_optin <= 0) smem_optin = 48 * 1024;
-  const int64_t ring_budget = (int64_t)smem_optin - 16 - (int64_t)(S->max_levels + 1) * 4;
-  const int Gmax = ring_budget > 0 ? (int)((size_t)ring_budget / ((size_t)(S->max_slots + 1) * sz)) : 0;
-  if (Gmax < 1)
-    return fail(NBTE_ERR_ARG, "one direction's live cells exceed shared memory (" + std::to_string(S->max_slots) +
-                                  " ring slots); use FP32 or a smaller mesh");
-  const int maxbpt = prec ? 8 : 4;
-  int G = o.band_group;
+  const int sz = prec ? 4 : 8;
+  const int K = S->K;
+  const RecLayout RL = rec_layout(sz, K);
+  // the autotuner's choice stands in for "planner's choice" (0, 0)
+  int want_G = o.band_group, want_threads = o.cta_threads;
+  const Tuned& tu = S->tuned[prec];
+  if (want_G == 0 && want_threads == 0 && tu.valid && tu.key == tune_key(S)) {
+    want_G = tu.G;
+    want_threads = tu.cap + 32;
+  }
+  // consumer threads of a sweep CTA = positions per chunk
+  int cap = 128;
+  if (want_threads != 0) {
+    if (want_threads < 64 || want_threads > 544 || want_threads % 32 != 0)
+      return fail(NBTE_ERR_ARG, "cta_threads must be a multiple of 32 in [64, 544]");
+    cap = want_threads - 32;
+  }
+  if (o.threads_per_cell > 1) return fail(NBTE_ERR_ARG, "threads_per_cell must be 0 or 1");
+  // shared memory of one CTA: barriers and chunk headers, the value ring, and
+  // the copy stages (records, (T', Qdot) pairs, imports)
+  auto stage_of = [&](int Gv, int& off_tq, int& off_imp) {
+    const int gpad = padded_group(Gv, sz);
+    const int rec = (cap * RL.size + 15) / 16 * 16;
+    const int tq = ((cap + 2) * 2 * sz + 15) / 16 * 16;
+    const int imp = cap * K * gpad * sz;
+    off_tq = rec;
+    off_imp = rec + tq;
+    return rec + tq + imp;
+  };
+  auto ring_of = [&](int Gv) { return (int)(((size_t)(S->max_slots + 1) * Gv * sz + 15) / 16 * 16); };
+  const int head = 32 * 8;   // up to 8 stages: full + empty barriers and chunk headers
+  auto fits = [&](int Gv, int ns) {
+    int a, b;
+    return (int64_t)head + ring_of(Gv) + (int64_t)ns * stage_of(Gv, a, b) <= kSweepSmemMax;
+  };
+  const int maxG = prec ? 8 : 4;
+  int G = want_G;
   if (G > 0) {
-    if (!pow2(G) || G > 32) return fail(NBTE_ERR_ARG, "band_group must be a power of two <= 32");
-    if (G > Gmax) return fail(NBTE_ERR_ARG, "band_group too large for shared memory on this mesh");
+    if (!(G == 1 || G == 2 || G == 4 || G == 8) || G > maxG)
+      return fail(NBTE_ERR_ARG, prec ? "band_group must be 1, 2, 4 or 8" : "band_group must be 1, 2 or 4 in FP64");
+    if (!fits(G, 2)) return fail(NBTE_ERR_ARG, "band_group too large for shared memory on this mesh");
   } else {
-    G = 1;
+    G = 0;
     double best = 1e300;
-    for (int c : {32, 16, 8, 4, 2, 1}) {
-      if (c > Gmax || c > 2 * maxbpt) continue;
+    for (int c : {8, 4, 2, 1}) {
+      if (c > maxG || !fits(c, 2)) continue;
       const int ng = (S->B + c - 1) / c;
       const double waste = (double)(ng * c - S->B) / S->B;
       // prefer wide groups unless they pad more than 12.5%
       const double score = waste <= 0.125 ? -c : 1000.0 * waste - c;
       if (score < best) { best = score; G = c; }
     }
+    if (G == 0)
+      return fail(NBTE_ERR_ARG, "one direction's live cells exceed shared memory (" + std::to_string(S->max_slots) +
+                                    " ring slots); use FP32 or a smaller mesh");
   }
-  int lanes = o.threads_per_cell > 0 ? o.threads_per_cell : 1;
-  if (!pow2(lanes) || lanes > 8) return fail(NBTE_ERR_ARG, "threads_per_cell must be 1, 2, 4 or 8");
-  if (lanes > G) lanes = G;
-  while (G / lanes > maxbpt) lanes *= 2;
-  if (lanes > 8) return fail(NBTE_ERR_ARG, "band_group too large for the thread layout");
-  const int bpt = G / lanes;
+  // stages: 2..8, as many as fit while every work item can be resident at
+  // once (the sweep of one item is a long dependent chain of levels, so a
+  // second wave would double the time); if even 2 stages do not allow that,
+  // use the most that fit
+  int off_tq = 0, off_imp = 0;
+  const int stage = stage_of(G, off_tq, off_imp);
   const int ng = (S->B + G - 1) / G;
-  const int Bp = ng * G;
-  int threads = std::min(512, std::max(32, ((S->max_width * lanes + 31) / 32) * 32));
-  if (o.cta_threads != 0) {
-    if (o.cta_threads < 32 || o.cta_threads > 512 || o.cta_threads % 32 != 0)
-      return fail(NBTE_ERR_ARG, "cta_threads must be a multiple of 32 in [32, 512]");
-    if (o.cta_threads < lanes) return fail(NBTE_ERR_ARG, "cta_threads smaller than threads_per_cell");
-    threads = o.cta_threads;
+  int nsm = 148;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device);
+  const int per_sm = std::max(1, (S->D * ng + nsm - 1) / nsm);
+  const int64_t budget = (int64_t)(228 * 1024) / per_sm - 1024;
+  int ns = 8;
+  while (ns > 2 && (int64_t)head + ring_of(G) + (int64_t)ns * stage > budget) --ns;
+  if ((int64_t)head + ring_of(G) + (int64_t)ns * stage > budget) {
+    ns = 8;
+    while (ns > 2 && !fits(G, ns)) --ns;
   }
-  const std::string key = std::to_string(prec) + "/" + std::to_string(G) + "/" + std::to_string(lanes) + "/" +
-                          std::to_string(threads) + "/" + std::to_string(S->version_bands) + "/" +
-                          std::to_string(S->plan_built);
+  const int Bp = ng * G;
+  const int threads = cap + 32;
+  const std::string key = std::to_string(prec) + "/" + std::to_string(G) + "/" + std::to_string(cap) + "/" +
+                          std::to_string(S->version_bands) + "/" + std::to_string(S->plan_built);
   if (key == S->layout_key) return NBTE_OK;
   DeviceGuard dg(S->device);
   drop_graph(S);
-  if (prec) {
-    int rc = ensure_fp32_coefs(S);
-    if (rc) return rc;
-  }
-  S->prec = prec; S->G = G; S->lanes = lanes; S->bpt = bpt; S->n_groups = ng; S->Bp = Bp;
+  int rc = prec ? ensure_records<float>(S) : ensure_records<double>(S);
+  if (rc) return rc;
+  rc = ensure_chunks(S, cap);
+  if (rc) return rc;
+  S->prec = prec; S->G = G; S->Gpad = padded_group(G, sz); S->n_groups = ng; S->Bp = Bp;
   S->n_items = S->D * ng;
   S->threads = threads;
-  S->lp_off = (int)((((size_t)(S->max_slots + 1) * G * sz) + 15) / 16 * 16);
-  S->smem = (size_t)S->lp_off + (size_t)(S->max_levels + 1) * 4;
+  S->n_stages = ns;
+  S->stage_bytes = stage;
+  S->off_tq = off_tq;
+  S->off_imp = off_imp;
+  S->off_ring = head;
+  S->off_stage = head + ring_of(G);
+  S->smem = (size_t)S->off_stage + (size_t)ns * stage;
   const int64_t N = S->mesh->m.n_cells;
   // band constants, padded bands are inert (C = 0, v = 0, 1/tau = 1)
   S->W = 0;
@@ -363,11 +468,13 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
     for (int g = 0; g < ng; ++g) { idir[i * ng + g] = i; igrp[i * ng + g] = g; }
   NBTE_CK(upload(S->item_dir, idir));
   NBTE_CK(upload(S->item_grp, igrp));
-  NBTE_CK(S->expt.alloc((size_t)S->n_exp * Bp * sz));
-  NBTE_CK(S->impt.alloc((size_t)S->n_imp * Bp * sz));
+  NBTE_CK(S->expt.alloc((size_t)ng * S->n_exp * S->Gpad * sz));
+  NBTE_CK(S->impt.alloc((size_t)ng * S->n_imp * S->Gpad * sz));
+  NBTE_CK(S->tqp.alloc(((size_t)S->D * N + 2) * 2 * sz));
+  NBTE_CK(cudaMemset(S->tqp.p, 0, S->tqp.bytes));
   NBTE_CK(S->srcTQ.alloc((size_t)2 * N * sz));
   NBTE_CK(S->srcTQ_fin.alloc((size_t)2 * N * sz));
-  NBTE_CK(S->part.alloc((size_t)S->n_items * N * 8));
+  NBTE_CK(S->part.alloc((size_t)S->n_items * N * sz));
   NBTE_CK(S->T.alloc(N * 8));
   NBTE_CK(S->Tprev.alloc(N * 8));
   NBTE_CK(S->Tkin.alloc(N * 8));
@@ -379,7 +486,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   NBTE_CK(S->dsum.alloc((size_t)S->n_dbf * Bp * 8));
   NBTE_CK(S->accE.alloc(N * 8));
   NBTE_CK(S->accQ.alloc((size_t)N * S->mesh->m.dim * 8));
-  NBTE_CK(S->res.alloc(16));
+  NBTE_CK(S->res.alloc(32));   // [0,1] residual words, [2] sweep error word (sticky)
+  NBTE_CK(cudaMemset(S->res.p, 0, 32));
   NBTE_CK(S->heat.alloc((size_t)S->n_wf * 8));
   NBTE_CK(cudaMemcpy(S->Vd.p, S->mesh->m.V.data(), N * 8, cudaMemcpyHostToDevice));
   S->version_q = -1;   // force heat-source upload
@@ -516,39 +624,38 @@ int ensure_laplacian(nbte_solver* S) {
 
 // ------------------------------------------------------------------ iteration body
 template <typename R>
-SweepArgs<R> sweep_args(nbte_solver* S, const void* srcTQ, int full) {
+SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   SweepArgs<R> a{};
   a.N = (int)S->mesh->m.n_cells;
-  a.Bp = S->Bp; a.G = S->G; a.n_groups = S->n_groups; a.dim = S->mesh->m.dim;
+  a.dim = S->mesh->m.dim;
   a.full = full;
-  a.lp_smem_off = S->lp_off;
+  a.Gpad = S->Gpad;
+  a.n_stages = S->n_stages;
+  a.stage_bytes = S->stage_bytes;
+  a.off_ring = S->off_ring;
+  a.off_stage = S->off_stage;
+  a.off_tq = S->off_tq;
+  a.off_imp = S->off_imp;
+  a.n_exp = S->n_exp;
+  a.n_imp = S->n_imp;
   a.item_dir = S->item_dir.as<int32_t>();
   a.item_grp = S->item_grp.as<int32_t>();
-  a.lvl_off = S->lvl_off.as<int64_t>();
-  a.level_ptr = S->level_ptr.as<int32_t>();
-  a.pos_cell = S->pos_cell.as<int32_t>();
-  a.pos_slot = S->pos_slot.as<int32_t>();
-  a.pos_exp = S->pos_exp.as<int32_t>();
-  a.pos_ref = S->pos_ref.as<int32_t>();
-  if constexpr (sizeof(R) == 4) {
-    a.pos_G = S->pos_G32.as<R>();
-    a.pos_coef = S->pos_coef32.as<R>();
-  } else {
-    a.pos_G = S->pos_G64.as<R>();
-    a.pos_coef = S->pos_coef64.as<R>();
-  }
+  a.chunk_off = S->chunk_off.as<int64_t>();
+  a.chunks = S->chunks.as<Chunk>();
+  a.rec = S->rec.as<unsigned char>();
+  a.tqp = S->tqp.as<R>();
   a.exp_off = S->exp_off.as<int64_t>();
   a.imp_off = S->imp_off.as<int64_t>();
   a.imp = S->impt.as<R>();
   a.exp = S->expt.as<R>();
-  a.srcTQ = static_cast<const R*>(srcTQ);
+  a.err = reinterpret_cast<int32_t*>(S->res.as<unsigned long long>() + 2);
   a.band_v = S->band_v.as<R>();
   a.band_inv_tau = S->band_itau.as<R>();
   a.band_cw = S->band_aT.as<R>();
   a.band_aQ = S->band_aQ.as<R>();
   a.dir_w = S->dir_w.as<double>();
   a.dir_s = S->dir_s.as<double>();
-  a.part = S->part.as<double>();
+  a.part = S->part.as<R>();
   a.accE = S->accE.as<double>();
   a.accQ = S->accQ.as<double>();
   return a;
@@ -558,6 +665,9 @@ template <typename R>
 WallArgs<R> wall_args(nbte_solver* S) {
   WallArgs<R> a{};
   a.Bp = S->Bp;
+  a.G = S->G;
+  a.Gpad = S->Gpad;
+  a.n_exp = S->n_exp;
   a.n_imp = S->n_imp;
   a.n_dbf = S->n_dbf;
   a.exp = S->expt.as<R>();
@@ -584,7 +694,7 @@ UpdateArgs<R> update_args(nbte_solver* S, int mode) {
   a.mode = mode;
   a.beta = S->beta;
   a.inv_beta = 1.0 / S->beta;
-  a.part = S->part.as<double>();
+  a.part = S->part.as<R>();
   a.Q = S->Qd.as<double>();
   a.V = S->Vd.as<double>();
   a.T = S->T.as<double>();
@@ -639,8 +749,11 @@ cudaError_t enqueue_iteration(nbte_solver* S, int scheme, double cg_tol, int cg_
   launch_walls<R>(wall_args<R>(S), st);
   cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
+  e = launch_gather_tq<R>(S->tqp.as<R>(), S->rec.p, rec_layout((int)sizeof(R), S->K).size, S->srcTQ.as<R>(),
+                          (int64_t)S->D * S->mesh->m.n_cells, st);
+  if (e != cudaSuccess) return e;
   if (ev0) cudaEventRecord(ev0, st);
-  e = launch_sweep<R>(sweep_args<R>(S, S->srcTQ.p, 0), S->K, S->bpt, S->lanes, S->n_items, S->threads, S->smem, st);
+  e = launch_sweep<R>(sweep_args<R>(S, 0), S->K, S->G, S->n_items, S->threads, S->smem, st);
   if (e != cudaSuccess) return e;
   if (ev1) cudaEventRecord(ev1, st);
   e = cudaMemsetAsync(S->res.p, 0, 16, st);
@@ -653,11 +766,117 @@ cudaError_t enqueue_iteration(nbte_solver* S, int scheme, double cg_tol, int cg_
     if (e != cudaSuccess) return e;
     launch_update<R>(update_args<R>(S, scheme == 1 ? 1 : 2), st);
   }
-  e = cudaMemcpyAsync(S->h_res, S->res.p, 16, cudaMemcpyDeviceToHost, st);
+  e = cudaMemcpyAsync(S->h_res, S->res.p, 24, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(S->h_misc, S->cg_err.p ? S->cg_err.p : S->res.p, 4, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+// T' from T_init (or T_ref), wall distributions at equilibrium with it, no
+// synthetic correction carried yet
+template <typename R>
+int init_state(nbte_solver* S, const nbte_solve_opts& o) {
+  const Mesh& m = S->mesh->m;
+  const int64_t N = m.n_cells;
+  cudaStream_t st = S->stream;
+  std::vector<double> T0(N, 0.0);
+  if (o.T_init) {
+    for (int64_t c = 0; c < N; ++c) {
+      const double t = o.T_init[m.perm[c]];
+      if (!std::isfinite(t)) return fail(NBTE_ERR_ARG, "non-finite T_init");
+      T0[c] = t - S->T_ref;
+    }
+  }
+  NBTE_CK(cudaMemcpyAsync(S->T.p, T0.data(), N * 8, cudaMemcpyHostToDevice, st));
+  NBTE_CK(cudaMemsetAsync(S->Delta.p, 0, N * 8, st));
+  NBTE_CK(cudaMemsetAsync(S->Tkin.p, 0, N * 8, st));
+  launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)N, st);
+  launch_init_exports<R>(S->expt.as<R>(), S->exp_cell.as<int32_t>(), S->T.as<double>(), S->band_CoW.as<double>(),
+                         S->Bp, S->G, S->Gpad, S->n_exp, st);
+  NBTE_CK(cudaGetLastError());
+  NBTE_CK(cudaStreamSynchronize(st));
+  return NBTE_OK;
+}
+
+// device time of one sweep of the current layout, on a scratch state
+template <typename R>
+int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
+  int rc = init_state<R>(S, o);
+  if (rc) return rc;
+  cudaStream_t st = S->stream;
+  launch_walls<R>(wall_args<R>(S), st);
+  NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->rec.p, rec_layout((int)sizeof(R), S->K).size, S->srcTQ.as<R>(),
+                              (int64_t)S->D * S->mesh->m.n_cells, st));
+  NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 0), S->K, S->G, S->n_items, S->threads, S->smem, st));
+  cudaEvent_t e0, e1;
+  NBTE_CK(cudaEventCreate(&e0));
+  NBTE_CK(cudaEventCreate(&e1));
+  NBTE_CK(cudaEventRecord(e0, st));
+  for (int k = 0; k < 2; ++k)
+    NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 0), S->K, S->G, S->n_items, S->threads, S->smem, st));
+  NBTE_CK(cudaEventRecord(e1, st));
+  NBTE_CK(cudaEventSynchronize(e1));
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  unsigned long long err = 0;
+  NBTE_CK(cudaMemcpy(&err, S->res.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost));
+  if (err) {
+    cudaMemset(S->res.p, 0, 32);
+    return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
+  }
+  *ms = t / 2;
+  return NBTE_OK;
+}
+
+// Autotuner: with band_group and cta_threads left at 0, time every feasible
+// (band group, chunk length) layout once per (mesh plan, band table,
+// precision) and keep the fastest.
+int autotune(nbte_solver* S, const nbte_solve_opts& o) {
+  if (o.band_group != 0 || o.cta_threads != 0) return NBTE_OK;
+  Tuned& tu = S->tuned[o.precision];
+  if (tu.valid && tu.key == tune_key(S)) return NBTE_OK;
+  tu.valid = false;
+  const int maxG = o.precision ? 8 : 4;
+  std::vector<int> Gs;
+  for (int c : {8, 4, 2, 1}) {
+    if (c > maxG) continue;
+    const int ng = (S->B + c - 1) / c;
+    if (c > 1 && (double)(ng * c - S->B) / S->B > 0.25) continue;   // too much padding
+    Gs.push_back(c);
+  }
+  double best = 1e300;
+  int bG = 0, bcap = 0;
+  for (int G : Gs)
+    for (int cap : {64, 128, 256, 512}) {
+      nbte_solve_opts c = o;
+      c.band_group = G;
+      c.cta_threads = cap + 32;
+      c.warm = 0;
+      if (ensure_layout(S, c) != NBTE_OK) continue;   // does not fit this mesh
+      int rc = ensure_q(S);
+      if (rc) return rc;
+      float ms = 0.f;
+      rc = o.precision ? time_sweep<float>(S, c, &ms) : time_sweep<double>(S, c, &ms);
+      if (rc) return rc;
+      if (ms < best) {
+        best = ms;
+        bG = G;
+        bcap = cap;
+      }
+    }
+  if (bG == 0) return fail(NBTE_ERR_ARG, "no sweep layout fits shared memory for this mesh");
+  tu.valid = true;
+  tu.G = bG;
+  tu.cap = bcap;
+  tu.key = tune_key(S);
+  tu.ms = best;
+  S->layout_key.clear();
+  S->have_state = false;
+  set_error("");
+  return NBTE_OK;
 }
 
 template <typename R>
@@ -671,22 +890,8 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   // ---- initial state
   if (!(o.warm && S->have_state)) {
     kernels += 2;
-    std::vector<double> T0(N, 0.0);
-    if (o.T_init) {
-      for (int64_t c = 0; c < N; ++c) {
-        const double t = o.T_init[m.perm[c]];
-        if (!std::isfinite(t)) return fail(NBTE_ERR_ARG, "non-finite T_init");
-        T0[c] = t - S->T_ref;
-      }
-    }
-    NBTE_CK(cudaMemcpyAsync(S->T.p, T0.data(), N * 8, cudaMemcpyHostToDevice, st));
-    NBTE_CK(cudaMemsetAsync(S->Delta.p, 0, N * 8, st));
-    NBTE_CK(cudaMemsetAsync(S->Tkin.p, 0, N * 8, st));
-    launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)N, st);
-    launch_init_exports<R>(S->expt.as<R>(), S->exp_cell.as<int32_t>(), S->T.as<double>(),
-                           S->band_CoW.as<double>(), S->Bp, S->n_exp, st);
-    NBTE_CK(cudaGetLastError());
-    NBTE_CK(cudaStreamSynchronize(st));
+    int rc = init_state<R>(S, o);
+    if (rc) return rc;
     S->have_state = true;
   } else {
     kernels += 1;
@@ -723,7 +928,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   // ---- iterate
   const bool profile = o.profile != 0;
   if (profile) use_graph = false;   // events bracket each sweep launch
-  const int64_t kernels_per_iter = (S->n_dbf > 0) + (S->n_imp > 0) + 1 + (scheme == 0 ? 1 : 3);
+  const int64_t kernels_per_iter = (S->n_dbf > 0) + (S->n_imp > 0) + 2 + (scheme == 0 ? 1 : 3);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (profile) {
     NBTE_CK(cudaEventCreate(&ev0));
@@ -741,6 +946,11 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   int it_best = 0;
   bool floor_reached = false;
   auto check = [&]() -> bool {   // returns true to stop
+    if (S->h_res[2] != 0) {
+      status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
+      cudaMemset(S->res.p, 0, 32);
+      return true;
+    }
     if (S->h_misc[0] != 0 && scheme != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the CG correction gave up");
       cudaMemset(S->cg_err.p, 0, 16);
@@ -799,14 +1009,19 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   S->have_outputs = false;
   // ---- moments of the last sweep: replay it with the energy/flux moments on
   if ((status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED) && !o.skip_outputs) {
-    kernels += 3;
+    kernels += 4;
     NBTE_CK(cudaMemsetAsync(S->accE.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
     launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
-    NBTE_CK(launch_sweep<R>(sweep_args<R>(S, S->srcTQ_fin.p, 1), S->K, S->bpt, S->lanes, S->n_items, S->threads,
-                            S->smem, st));
+    NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->rec.p, rec_layout((int)sizeof(R), S->K).size,
+                                S->srcTQ_fin.as<R>(), (int64_t)S->D * N, st));
+    NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 1), S->K, S->G, S->n_items, S->threads, S->smem, st));
     WallHeatArgs<R> wh{};
     wh.Bp = S->Bp;
+    wh.G = S->G;
+    wh.Gpad = S->Gpad;
+    wh.n_exp = S->n_exp;
+    wh.n_imp = S->n_imp;
     wh.n_wf = S->n_wf;
     wh.wf_ptr = S->wf_ptr.as<int64_t>();
     wh.wf_val = S->wf_val.as<int64_t>();
@@ -916,7 +1131,7 @@ static int ensure_device(nbte_solver* S) {
     DeviceGuard g(S->device);
     NBTE_CK(cudaStreamCreateWithFlags(&S->own_stream, cudaStreamNonBlocking));
     if (!S->stream) S->stream = S->own_stream;
-    NBTE_CK(cudaMallocHost(&S->h_res, 16));
+    NBTE_CK(cudaMallocHost(&S->h_res, 32));
     NBTE_CK(cudaMallocHost(&S->h_misc, 16));
     S->h_misc[0] = 0;
   }
@@ -1060,6 +1275,10 @@ int nbte_plan_stats(nbte_solver* S, const nbte_solve_opts* opts, int64_t stats[1
   DeviceGuard g(S->device);
   rc = ensure_plan(S);
   if (rc) return rc;
+  if (S->B > 0 && S->D > 0 && S->bcs_set) {
+    rc = autotune(S, o);
+    if (rc) return rc;
+  }
   rc = ensure_layout(S, o);
   if (rc) return rc;
   stats[0] = S->total_levels;
@@ -1068,7 +1287,7 @@ int nbte_plan_stats(nbte_solver* S, const nbte_solve_opts* opts, int64_t stats[1
   stats[3] = S->lagged;
   stats[4] = S->n_items;
   stats[5] = S->G;
-  stats[6] = S->lanes;
+  stats[6] = 1;   // threads per cell
   stats[7] = (int64_t)device_bytes(S);
   stats[8] = S->K;
   stats[9] = S->n_exp;
@@ -1092,6 +1311,8 @@ int nbte_solve_steady(nbte_solver* S, const nbte_solve_opts* opts, nbte_solve_in
   DeviceGuard g(S->device);
   try {
     rc = ensure_plan(S);
+    if (rc) return rc;
+    rc = autotune(S, o);
     if (rc) return rc;
     rc = ensure_layout(S, o);
     if (rc) return rc;

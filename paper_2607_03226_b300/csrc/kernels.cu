@@ -1,12 +1,5 @@
-// Device kernels of libnanobte (sm_103a).
+// Device kernels of libnanobte (sm_103a), except the sweep (sweep.cu):
 //
-//  sweep_kernel  - the per-(direction, band group) transport solve of Eq. (4)
-//                  as a level-scheduled sweep over the direction's upwind
-//                  graph (the triangular solve of the cached factorisation of
-//                  Eq. (13)), bands innermost in registers, upwind values in a
-//                  shared-memory ring, fused with the collision moment of
-//                  Eq. (5) (and, on request, the energy/flux moments of
-//                  Eq. (7)).
 //  walls         - thermalizing / diffuse / specular / partial wall values and
 //                  lagged cycle faces for the next sweep.
 //  update        - moment reduction over work items, lattice temperature
@@ -25,320 +18,30 @@
 
 namespace nbte {
 
-namespace {
-
-template <typename R>
-struct Vec2;
-template <>
-struct Vec2<float> { using T = float2; };
-template <>
-struct Vec2<double> { using T = double2; };
-
-// BPT consecutive values of one cell's band group
-template <typename R, int BPT>
-__device__ __forceinline__ void load_bands(const R* p, R (&v)[BPT]) {
-  if constexpr (sizeof(R) == 4 && BPT % 4 == 0) {
-#pragma unroll
-    for (int b = 0; b < BPT; b += 4) {
-      const float4 t = *reinterpret_cast<const float4*>(p + b);
-      v[b] = t.x; v[b + 1] = t.y; v[b + 2] = t.z; v[b + 3] = t.w;
-    }
-  } else if constexpr (BPT % 2 == 0) {
-#pragma unroll
-    for (int b = 0; b < BPT; b += 2) {
-      const typename Vec2<R>::T t = *reinterpret_cast<const typename Vec2<R>::T*>(p + b);
-      v[b] = t.x; v[b + 1] = t.y;
-    }
-  } else {
-#pragma unroll
-    for (int b = 0; b < BPT; ++b) v[b] = p[b];
-  }
-}
-
-template <typename R, int BPT>
-__device__ __forceinline__ void store_bands(R* p, const R (&v)[BPT]) {
-  if constexpr (sizeof(R) == 4 && BPT % 4 == 0) {
-#pragma unroll
-    for (int b = 0; b < BPT; b += 4) *reinterpret_cast<float4*>(p + b) = make_float4(v[b], v[b + 1], v[b + 2], v[b + 3]);
-  } else if constexpr (BPT % 2 == 0) {
-#pragma unroll
-    for (int b = 0; b < BPT; b += 2) {
-      typename Vec2<R>::T t;
-      t.x = v[b]; t.y = v[b + 1];
-      *reinterpret_cast<typename Vec2<R>::T*>(p + b) = t;
-    }
-  } else {
-#pragma unroll
-    for (int b = 0; b < BPT; ++b) p[b] = v[b];
-  }
-}
-
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-
-template <int LANES, typename R>
-__device__ __forceinline__ R lane_sum(R x) {
-  if constexpr (LANES > 1) {
-    const unsigned lid = threadIdx.x & 31u;
-    const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << (lid & ~(unsigned)(LANES - 1)));
-#pragma unroll
-    for (int o = LANES / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o);
-  }
-  return x;
-}
-
-}  // namespace
-
-// ============================================================================ sweep
-// One CTA owns one work item (direction i, band group g) and walks the levels
-// of direction i in order; a __syncthreads() between levels makes level l's
-// values visible to level l+1.  Thread t serves lane (t % LANES) of cells
-// (t / LANES), (t / LANES) + blockDim/LANES, ... of each level; lane j holds
-// bands [g*G + j*BPT, g*G + (j+1)*BPT) in registers.  Per cell and band the
-// upwind balance of Eq. (4) is solved for the deviation from the cell's own
-// equilibrium e0 = C T'/W (Eq. (11)):
-//   e = e0 + (Qdot C/(C_tot W) + v sum_in c_k (e_up,k - e0)) / (1/tau + v G),
-//   c_k = |s.An_k|/V,  G = sum_in c_k  (= sum_out (s.An)/V for a closed cell),
-// which equals e = (e0/tau + S + v sum_in c_k e_up)/(1/tau + v G).  Written
-// this way a uniform equilibrium is reproduced exactly in any precision and
-// rounding errors scale with the local differences e_up - e0.
-//
-// The collision moment of Eq. (5) is accumulated as sum_l w_i (e - e0)/tau_l;
-// the equilibrium part sums to beta T' exactly and is added back in FP64 by
-// the update kernel, so reduced-precision partials carry only the deviation.
-//
-// Latency: everything a cell needs except its upwind ring values (its record,
-// its (T', Qdot) pair and any wall/lag import values) is loaded one level
-// ahead, so a level's critical path is: barrier, shared-memory reads,
-// arithmetic, shared-memory store.
-namespace {
-template <typename R, int K>
-struct Rec {
-  int cell, slot, ex;
-  R G;
-  int ref[K];
-  R cf[K];
-};
-template <typename R, int K, int BPT>
-struct Pre {
-  R t, q;
-  R imp[K][BPT];
-};
-}  // namespace
-
-template <typename R, int K, int BPT, int LANES>
-__global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<R> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* ring = reinterpret_cast<R*>(smem_raw);
-  int* lps = reinterpret_cast<int*>(smem_raw + a.lp_smem_off);
-  const int item = blockIdx.x;
-  const int i = a.item_dir[item];
-  const int g = a.item_grp[item];
-  const int G = BPT * LANES;
-  const int lane = LANES > 1 ? (int)(threadIdx.x & (LANES - 1)) : 0;
-  const int band0 = g * G + lane * BPT;
-  const int N = a.N;
-  const int L = (int)(a.lvl_off[i + 1] - a.lvl_off[i]) - 1;
-  {
-    const int32_t* lp = a.level_ptr + a.lvl_off[i];
-    for (int t = threadIdx.x; t <= L; t += blockDim.x) lps[t] = lp[t];
-  }
-  for (int t = threadIdx.x; t < G; t += blockDim.x) ring[t] = R(0);   // zero slot
-
-  const double wi = a.dir_w[i];
-  R vb[BPT], itau[BPT], cw[BPT], aQ[BPT], wt[BPT];
-#pragma unroll
-  for (int b = 0; b < BPT; ++b) {
-    vb[b] = a.band_v[band0 + b];
-    itau[b] = a.band_inv_tau[band0 + b];
-    cw[b] = a.band_cw[band0 + b];
-    aQ[b] = a.band_aQ[band0 + b];
-    wt[b] = (R)(wi * (double)itau[b]);
-  }
-  __syncthreads();
-
-  const int64_t dbase = (int64_t)i * N;
-  const R* imp_i = a.imp + a.imp_off[i] * a.Bp + band0;
-  R* exp_i = a.exp + a.exp_off[i] * a.Bp + band0;
-  const int per_pass = blockDim.x / LANES;
-  const int cidx = threadIdx.x / LANES;
-  double* part = a.part + (int64_t)item * N;
-  const typename Vec2<R>::T* tq = reinterpret_cast<const typename Vec2<R>::T*>(a.srcTQ);
-
-  auto load_rec = [&](int p, Rec<R, K>& r) {
-    const int64_t q = dbase + p;
-    r.cell = a.pos_cell[q];
-    r.slot = a.pos_slot[q];
-    r.ex = a.pos_exp[q];
-    r.G = a.pos_G[q];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int64_t qk = ((int64_t)i * K + k) * N + p;
-      r.ref[k] = a.pos_ref[qk];
-      r.cf[k] = a.pos_coef[qk];
-    }
-  };
-  auto load_pre = [&](const Rec<R, K>& r, Pre<R, K, BPT>& d) {
-    const typename Vec2<R>::T s = tq[r.cell];
-    d.t = s.x;
-    d.q = s.y;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (r.ref[k] < 0) load_bands<R, BPT>(imp_i + (int64_t)(-1 - r.ref[k]) * a.Bp, d.imp[k]);
-  };
-  auto compute = [&](const Rec<R, K>& r, const Pre<R, K, BPT>& d) {
-    R e0[BPT], up[BPT];
-#pragma unroll
-    for (int b = 0; b < BPT; ++b) {
-      e0[b] = cw[b] * d.t;
-      up[b] = R(0);
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      R e_up[BPT];
-      if (r.ref[k] >= 0) {
-        load_bands<R, BPT>(ring + r.ref[k] * G + lane * BPT, e_up);
-      } else {
-#pragma unroll
-        for (int b = 0; b < BPT; ++b) e_up[b] = d.imp[k][b];
-      }
-#pragma unroll
-      for (int b = 0; b < BPT; ++b) up[b] += r.cf[k] * (e_up[b] - e0[b]);
-    }
-    R e[BPT];
-    R nl = R(0);
-#pragma unroll
-    for (int b = 0; b < BPT; ++b) {
-      const R phi = (aQ[b] * d.q + vb[b] * up[b]) * recip(itau[b] + vb[b] * r.G);
-      e[b] = e0[b] + phi;
-      nl += wt[b] * phi;
-    }
-    if (r.slot >= 0) store_bands<R, BPT>(ring + r.slot * G + lane * BPT, e);
-    if (r.ex >= 0) store_bands<R, BPT>(exp_i + (int64_t)r.ex * a.Bp, e);
-    nl = lane_sum<LANES>(nl);
-    if (lane == 0) part[r.cell] = (double)nl;
-    if (a.full) {
-      R es = R(0), evs = R(0);
-#pragma unroll
-      for (int b = 0; b < BPT; ++b) {
-        es += e[b];
-        evs += vb[b] * e[b];
-      }
-      es = lane_sum<LANES>(es);
-      evs = lane_sum<LANES>(evs);
-      if (lane == 0) {
-        atomicAdd(a.accE + r.cell, wi * (double)es);
-        for (int d = 0; d < a.dim; ++d)
-          atomicAdd(a.accQ + (int64_t)r.cell * a.dim + d, wi * a.dir_s[i * 3 + d] * (double)evs);
-      }
-    }
-  };
-
-  // pipeline: r0/d0 = this level's first-pass cell, r1 = next level's record
-  Rec<R, K> r0, r1;
-  Pre<R, K, BPT> d0;
-  bool v0 = L > 0 && lps[0] + cidx < lps[1];
-  bool v1 = L > 1 && lps[1] + cidx < lps[2];
-  if (v0) {
-    load_rec(lps[0] + cidx, r0);
-    load_pre(r0, d0);
-  }
-  if (v1) load_rec(lps[1] + cidx, r1);
-  for (int l = 0; l < L; ++l) {
-    Pre<R, K, BPT> d1;
-    if (v1) load_pre(r1, d1);                       // level l+1, issued now
-    Rec<R, K> r2;
-    const bool v2 = l + 2 < L && lps[l + 2] + cidx < lps[l + 3];
-    if (v2) load_rec(lps[l + 2] + cidx, r2);        // level l+2, issued now
-    if (v0) compute(r0, d0);
-    for (int p = lps[l] + cidx + per_pass; p < lps[l + 1]; p += per_pass) {   // wide levels
-      Rec<R, K> rw;
-      Pre<R, K, BPT> dw;
-      load_rec(p, rw);
-      load_pre(rw, dw);
-      compute(rw, dw);
-    }
-    __syncthreads();
-    r0 = r1;
-    d0 = d1;
-    v0 = v1;
-    r1 = r2;
-    v1 = v2;
-  }
-}
-
-template <typename R, int K, int BPT>
-static cudaError_t launch_sweep_l(const SweepArgs<R>& a, int lanes, int n_items, int threads, size_t smem,
-                                  cudaStream_t st) {
-  switch (lanes) {
-#define NBTE_L(Lv)                                                                                    \
-  case Lv: {                                                                                          \
-    auto kern = sweep_kernel<R, K, BPT, Lv>;                                                          \
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    if (e != cudaSuccess) return e;                                                                   \
-    kern<<<n_items, threads, smem, st>>>(a);                                                          \
-    return cudaGetLastError();                                                                        \
-  }
-    NBTE_L(1) NBTE_L(2) NBTE_L(4) NBTE_L(8)
-#undef NBTE_L
-    default: return cudaErrorInvalidConfiguration;
-  }
-}
-
-template <typename R, int K>
-static cudaError_t launch_sweep_b(const SweepArgs<R>& a, int bpt, int lanes, int n_items, int threads, size_t smem,
-                                  cudaStream_t st) {
-  switch (bpt) {
-    case 1: return launch_sweep_l<R, K, 1>(a, lanes, n_items, threads, smem, st);
-    case 2: return launch_sweep_l<R, K, 2>(a, lanes, n_items, threads, smem, st);
-    case 4: return launch_sweep_l<R, K, 4>(a, lanes, n_items, threads, smem, st);
-    case 8:
-      if constexpr (sizeof(R) == 4) return launch_sweep_l<R, K, 8>(a, lanes, n_items, threads, smem, st);
-      return cudaErrorInvalidConfiguration;
-    default: return cudaErrorInvalidConfiguration;
-  }
-}
-
-// Launches the variant for (K inflow entries, BPT bands per thread, lanes);
-// an unsupported combination returns cudaErrorInvalidConfiguration without
-// launching anything.
-template <typename R>
-cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int bpt, int lanes, int n_items, int threads, size_t smem,
-                         cudaStream_t st) {
-  switch (K) {
-    case 1: return launch_sweep_b<R, 1>(a, bpt, lanes, n_items, threads, smem, st);
-    case 2: return launch_sweep_b<R, 2>(a, bpt, lanes, n_items, threads, smem, st);
-    case 3: return launch_sweep_b<R, 3>(a, bpt, lanes, n_items, threads, smem, st);
-    case 4: return launch_sweep_b<R, 4>(a, bpt, lanes, n_items, threads, smem, st);
-    case 5: return launch_sweep_b<R, 5>(a, bpt, lanes, n_items, threads, smem, st);
-    default: return cudaErrorInvalidConfiguration;
-  }
-}
-
 // ============================================================================ walls
 template <typename R>
 __global__ void init_exports_kernel(R* exp, const int32_t* exp_cell, const double* Tdev, const double* CoW, int Bp,
-                                    int64_t n_exp) {
+                                    int G, int Gpad, int64_t n_exp) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n_exp * Bp) return;
   const int64_t x = t / Bp;
   const int b = (int)(t - x * Bp);
-  exp[t] = (R)(CoW[b] * Tdev[exp_cell[x]]);
+  exp[io_index(x, b, n_exp, G, Gpad)] = (R)(CoW[b] * Tdev[exp_cell[x]]);
 }
 
 template <typename R>
-void launch_init_exports(R* exp, const int32_t* exp_cell, const double* Tdev, const double* CoW, int Bp, int64_t n_exp,
-                         cudaStream_t st) {
+void launch_init_exports(R* exp, const int32_t* exp_cell, const double* Tdev, const double* CoW, int Bp, int G,
+                         int Gpad, int64_t n_exp, cudaStream_t st) {
   const int64_t n = n_exp * Bp;
   if (n == 0) return;
-  init_exports_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(exp, exp_cell, Tdev, CoW, Bp, n_exp);
+  init_exports_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(exp, exp_cell, Tdev, CoW, Bp, G, Gpad, n_exp);
 }
 
 // exported value of entry x, band b, with the synthetic correction's
 // equilibrium part added (zero for the sequential scheme)
 template <typename R>
 __device__ __forceinline__ double exported(const WallArgs<R>& a, int64_t x, int b) {
-  return (double)a.exp[x * a.Bp + b] + a.CoW[b] * a.Delta[a.exp_cell[x]];
+  return (double)a.exp[io_index(x, b, a.n_exp, a.G, a.Gpad)] + a.CoW[b] * a.Delta[a.exp_cell[x]];
 }
 
 // diffuse re-emission: one value per (diffuse face, band)
@@ -379,7 +82,7 @@ __global__ void imports_kernel(const WallArgs<R> a) {
       v = exported(a, a.imp_src[x], b);
       break;
   }
-  a.imp[t] = (R)v;
+  a.imp[io_index(x, b, a.n_imp, a.G, a.Gpad)] = (R)v;
 }
 
 template <typename R>
@@ -726,9 +429,12 @@ __global__ void wall_heat_kernel(const WallHeatArgs<R> a) {
   double h = 0.0;
   for (int64_t k = a.wf_ptr[f]; k < a.wf_ptr[f + 1]; ++k) {
     const int64_t v = a.wf_val[k];
-    const R* src = v >= 0 ? a.exp + v * a.Bp : a.imp + (-1 - v) * a.Bp;
     double s = 0.0;
-    for (int b = 0; b < a.Bp; ++b) s += a.band_v[b] * (double)src[b];
+    for (int b = 0; b < a.Bp; ++b) {
+      const R val = v >= 0 ? a.exp[io_index(v, b, a.n_exp, a.G, a.Gpad)]
+                           : a.imp[io_index(-1 - v, b, a.n_imp, a.G, a.Gpad)];
+      s += a.band_v[b] * (double)val;
+    }
     h += a.wf_coef[k] * s;
   }
   a.heat[f] = h;
@@ -742,9 +448,8 @@ void launch_wall_heat(const WallHeatArgs<R>& a, cudaStream_t st) {
 
 // ---------------------------------------------------------------- instantiations
 #define NBTE_INST(R)                                                                                      \
-  template cudaError_t launch_sweep<R>(const SweepArgs<R>&, int, int, int, int, int, size_t, cudaStream_t); \
-  template void launch_init_exports<R>(R*, const int32_t*, const double*, const double*, int, int64_t,    \
-                                       cudaStream_t);                                                     \
+  template void launch_init_exports<R>(R*, const int32_t*, const double*, const double*, int, int, int,   \
+                                       int64_t, cudaStream_t);                                            \
   template void launch_walls<R>(const WallArgs<R>&, cudaStream_t);                                        \
   template void launch_update<R>(const UpdateArgs<R>&, cudaStream_t);                                     \
   template void launch_wall_heat<R>(const WallHeatArgs<R>&, cudaStream_t);                                \

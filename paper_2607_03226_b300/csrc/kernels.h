@@ -5,54 +5,61 @@
 
 #include <cstdint>
 
+#include "layout.h"
+
 namespace nbte {
 
 // device error word values (written by bounded waits, read by the host)
 enum DevError : int32_t { DEV_OK = 0, DEV_BARRIER_TIMEOUT = 1, DEV_QUEUE_TIMEOUT = 2 };
 
+// shared-memory budget of one sweep CTA (the rest of the SM's 228 KB stays
+// free for a second CTA when the ring is small)
+constexpr int kSweepSmemMax = 227 * 1024;
+
 template <typename R>
 struct SweepArgs {
-  int N, Bp, G, n_groups, dim;
+  int N, dim;
   int full;                      // also accumulate E and q (atomics)
-  int lp_smem_off;               // byte offset of the level pointers after the ring
+  int Gpad;                      // padded row length of the import/export tables
+  int n_stages;                  // shared-memory stages of the copy pipeline
+  int stage_bytes, off_ring, off_stage, off_tq, off_imp;   // shared-memory layout
+  int64_t n_exp, n_imp;
   const int32_t* item_dir;       // [n_items]
   const int32_t* item_grp;       // [n_items]
-  const int64_t* lvl_off;        // [D+1]
-  const int32_t* level_ptr;
-  const int32_t* pos_cell;       // [D*N]
-  const int32_t* pos_slot;
-  const int32_t* pos_exp;
-  const R* pos_G;
-  const int32_t* pos_ref;        // [D*K*N]
-  const R* pos_coef;
+  const int64_t* chunk_off;      // [D+1]
+  const Chunk* chunks;
+  const unsigned char* rec;      // packed position records [D*N]
+  const R* tqp;                  // [2*(D*N+2)] (T', Qdot) per position
   const int64_t* exp_off;        // [D+1]
   const int64_t* imp_off;
-  const R* imp;                  // [n_imp*Bp]
-  R* exp;                        // [n_exp*Bp]
-  const R* srcTQ;                // [2*N] (T', Qdot) per cell
+  const R* imp;                  // band-group-major import rows
+  R* exp;                        // band-group-major export rows
   const R* band_v;               // [Bp]
   const R* band_inv_tau;
   const R* band_cw;              // C / W
   const R* band_aQ;              // C / (C_tot W)
   const double* dir_w;           // [D]
   const double* dir_s;           // [D*3]
-  double* part;                  // [n_items*N] collision-moment partials
+  R* part;                       // [n_items*N] collision-moment partials (of e - e0)
   double* accE;                  // [N]   (full)
   double* accQ;                  // [N*dim] (full)
+  int32_t* err;                  // device error word
 };
 
 template <typename R>
-cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int bpt, int lanes, int n_items, int threads,
-                  size_t smem, cudaStream_t st);
+cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem,
+                         cudaStream_t st);
+template <typename R>
+cudaError_t launch_gather_tq(R* tqp, const void* rec, int rec_bytes, const R* srcTQ, int64_t n, cudaStream_t st);
 
 template <typename R>
-void launch_init_exports(R* exp, const int32_t* exp_cell, const double* Tdev, const double* CoW, int Bp,
-                         int64_t n_exp, cudaStream_t st);
+void launch_init_exports(R* exp, const int32_t* exp_cell, const double* Tdev, const double* CoW, int Bp, int G,
+                         int Gpad, int64_t n_exp, cudaStream_t st);
 
 template <typename R>
 struct WallArgs {
-  int Bp;
-  int64_t n_imp, n_dbf;
+  int Bp, G, Gpad;
+  int64_t n_exp, n_imp, n_dbf;
   const R* exp;
   R* imp;
   const int32_t* exp_cell;
@@ -76,7 +83,7 @@ struct UpdateArgs {
   int N, n_items;
   int mode;                      // 0 sequential, 1 synthetic (DSA), 2 synthetic (literal), 3 rhs only
   double inv_beta, beta;
-  const double* part;
+  const R* part;
   const double* Q;
   const double* V;
   double* T;                     // T' iterate (in/out)
@@ -132,7 +139,8 @@ constexpr int kMaxCoarse = 2048;   // aggregates of the coarse space (rc staged 
 
 template <typename R>
 struct WallHeatArgs {
-  int Bp;
+  int Bp, G, Gpad;
+  int64_t n_exp, n_imp;
   int64_t n_wf;
   const int64_t* wf_ptr;
   const int64_t* wf_val;

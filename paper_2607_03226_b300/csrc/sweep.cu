@@ -1,0 +1,364 @@
+// The transport sweep (sm_103a): per (direction, band group) work item, the
+// first-order upwind solve of Eq. (4) in the topological (level) order of the
+// direction's upwind graph -- the triangular substitution of the factorised
+// system of Eq. (13) -- fused with the collision moment of Eq. (5) and, on
+// request, the energy and flux moments of Eq. (7).
+//
+// Warp-specialised pipeline, one CTA per work item:
+//  * warp 0 (one elected lane) is the producer.  It walks the direction's
+//    chunks (up to CAP consecutive positions of one level) and, several chunks
+//    ahead of the consumers, bulk-copies (cp.async.bulk, completion counted on
+//    an mbarrier) each chunk's packed position records, its pre-gathered
+//    (T', Qdot) pairs and its slice of wall/lag import values into a ring of
+//    shared-memory stages;
+//  * the other warps are consumers: they wait on a stage's "full" barrier,
+//    compute one position per thread from shared memory and the value ring,
+//    release the stage on its "empty" barrier, and meet on a named barrier
+//    only at the end of a level (so the next level sees the ring writes).
+// A level's critical path is therefore shared-memory work only.  Every wait
+// is bounded: on timeout the error word is set, the producer waits (bounded)
+// for the copies it issued, and the CTA leaves.
+//
+// Per cell and band the balance is solved for the deviation from the cell's
+// own equilibrium e0 = C T'/W (Eq. (11)):
+//   e = e0 + (Qdot C/(C_tot W) + v sum_in c_k (e_up,k - e0)) / (1/tau + v G),
+//   c_k = |s.An_k|/V,  G = sum_in c_k  (= sum_out (s.An)/V for a closed cell).
+// The collision-moment partial is sum_l w_i (e - e0)/tau_l; the equilibrium
+// part sums to beta T' exactly and is added back in FP64 by the update kernel.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+#include "layout.h"
+
+namespace nbte {
+
+namespace {
+
+constexpr unsigned long long kWaitLimit = 1ull << 26;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (unsigned long long k = 0; k < kWaitLimit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void consumer_barrier(int count) {
+  asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+
+template <typename R>
+struct Vec2;
+template <>
+struct Vec2<float> { using T = float2; };
+template <>
+struct Vec2<double> { using T = double2; };
+
+template <typename R, int BPT>
+__device__ __forceinline__ void load_vals(const R* p, R (&v)[BPT]) {
+  if constexpr (sizeof(R) == 4 && BPT % 4 == 0) {
+#pragma unroll
+    for (int b = 0; b < BPT; b += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p + b);
+      v[b] = t.x; v[b + 1] = t.y; v[b + 2] = t.z; v[b + 3] = t.w;
+    }
+  } else if constexpr (BPT % 2 == 0) {
+#pragma unroll
+    for (int b = 0; b < BPT; b += 2) {
+      const typename Vec2<R>::T t = *reinterpret_cast<const typename Vec2<R>::T*>(p + b);
+      v[b] = t.x; v[b + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) v[b] = p[b];
+  }
+}
+
+template <typename R, int BPT>
+__device__ __forceinline__ void store_vals(R* p, const R (&v)[BPT]) {
+  if constexpr (sizeof(R) == 4 && BPT % 4 == 0) {
+#pragma unroll
+    for (int b = 0; b < BPT; b += 4) *reinterpret_cast<float4*>(p + b) = make_float4(v[b], v[b + 1], v[b + 2], v[b + 3]);
+  } else if constexpr (BPT % 2 == 0) {
+#pragma unroll
+    for (int b = 0; b < BPT; b += 2) {
+      typename Vec2<R>::T t;
+      t.x = v[b]; t.y = v[b + 1];
+      *reinterpret_cast<typename Vec2<R>::T*>(p + b) = t;
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) p[b] = v[b];
+  }
+}
+
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+}  // namespace
+
+template <typename R, int K, int G>
+__global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int NS = a.n_stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + NS;
+  Chunk* meta = reinterpret_cast<Chunk*>(smem + 16 * NS);
+  R* ring = reinterpret_cast<R*>(smem + a.off_ring);
+  unsigned char* stages = smem + a.off_stage;
+  const RecLayout RL = rec_layout((int)sizeof(R), K);
+
+  const int item = blockIdx.x;
+  const int i = a.item_dir[item];
+  const int g = a.item_grp[item];
+  const int ncons = blockDim.x - 32;
+  const int64_t ch0 = a.chunk_off[i];
+  const int nch = (int)(a.chunk_off[i + 1] - ch0);
+  const int64_t dbase = (int64_t)i * a.N;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, ncons / 32);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (threadIdx.x < 32) {
+    // ------------------------------------------------------------ producer
+    // the warp fetches chunk descriptors 32 at a time, one batch ahead; lane
+    // 0 waits for free stages and issues the copies
+    const int lane = threadIdx.x;
+    auto fetch = [&](int base) {
+      int4 v = make_int4(0, 0, 0, 0);
+      if (base + lane < nch) v = *reinterpret_cast<const int4*>(a.chunks + ch0 + base + lane);
+      return v;
+    };
+    int4 cur = fetch(0), nxt = fetch(32);
+    int issued = 0;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+      if (c > 0 && (c & 31) == 0) {
+        cur = nxt;
+        nxt = fetch(c + 32);
+      }
+      Chunk m;
+      m.pos = __shfl_sync(0xffffffffu, cur.x, c & 31);
+      m.len = __shfl_sync(0xffffffffu, cur.y, c & 31);
+      m.imp = __shfl_sync(0xffffffffu, cur.z, c & 31);
+      m.nimp_end = __shfl_sync(0xffffffffu, cur.w, c & 31);
+      if (lane == 0) {
+        const int s = c % NS;
+        if (c >= NS && !mbar_wait(empty + s, ((c / NS) - 1) & 1)) {
+          atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
+          ok = false;
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      if (lane == 0) {
+        const int s = c % NS;
+        meta[s] = m;
+        unsigned char* st = stages + (size_t)s * a.stage_bytes;
+        const unsigned rec_bytes = (unsigned)(m.len * RL.size);
+        // (T', Qdot) pairs: copy a 16-byte aligned superset
+        const int64_t q0 = dbase + m.pos;
+        const int per16 = 16 / (int)(2 * sizeof(R));   // pairs per 16 bytes (2 for FP32, 1 for FP64)
+        const int64_t qa = q0 / per16 * per16;
+        const int64_t qe = (q0 + m.len + per16 - 1) / per16 * per16;
+        const unsigned tq_bytes = (unsigned)((qe - qa) * 2 * sizeof(R));
+        const int nimp = m.nimp_end & 0x3fffffff;
+        const unsigned imp_bytes = (unsigned)nimp * (unsigned)(a.Gpad * sizeof(R));
+        mbar_arrive_expect_tx(full + s, rec_bytes + tq_bytes + imp_bytes);
+        bulk_copy(st, a.rec + (size_t)q0 * RL.size, rec_bytes, full + s);
+        bulk_copy(st + a.off_tq, a.tqp + (size_t)qa * 2, tq_bytes, full + s);
+        if (nimp > 0)
+          bulk_copy(st + a.off_imp, a.imp + ((size_t)g * a.n_imp + a.imp_off[i] + m.imp) * a.Gpad, imp_bytes,
+                    full + s);
+      }
+      ++issued;
+    }
+    // every copy issued must land before the CTA leaves
+    if (lane == 0)
+      for (int c = issued - NS > 0 ? issued - NS : 0; c < issued; ++c) mbar_wait(full + (c % NS), (c / NS) & 1);
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers
+  const int ct = threadIdx.x - 32;
+  for (int t = ct; t < G; t += ncons) ring[t] = R(0);   // zero slot
+  const double wi = a.dir_w[i];
+  const int band0 = g * G;
+  R vb[G], itau[G], cw[G], aQ[G], wt[G];
+#pragma unroll
+  for (int b = 0; b < G; ++b) {
+    vb[b] = a.band_v[band0 + b];
+    itau[b] = a.band_inv_tau[band0 + b];
+    cw[b] = a.band_cw[band0 + b];
+    aQ[b] = a.band_aQ[band0 + b];
+    wt[b] = (R)(wi * (double)itau[b]);
+  }
+  R* part = a.part + (int64_t)item * a.N;
+  R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * a.Gpad;
+  consumer_barrier(ncons);
+
+  for (int c = 0; c < nch; ++c) {
+    const int s = c % NS;
+    if (!mbar_wait(full + s, (c / NS) & 1)) {
+      atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
+      break;
+    }
+    const Chunk m = meta[s];
+    const unsigned char* st = stages + (size_t)s * a.stage_bytes;
+    const int per16 = 16 / (int)(2 * sizeof(R));
+    const int tq_shift = (int)((dbase + m.pos) % per16);
+    const R* tqs = reinterpret_cast<const R*>(st + a.off_tq) + 2 * tq_shift;
+    const R* imps = reinterpret_cast<const R*>(st + a.off_imp);
+    for (int j = ct; j < m.len; j += ncons) {
+      const unsigned char* rb = st + (size_t)j * RL.size;
+      const int cell = *reinterpret_cast<const int*>(rb);
+      const int slot = *reinterpret_cast<const int*>(rb + 4);
+      const int ex = *reinterpret_cast<const int*>(rb + 8);
+      const R Gc = *reinterpret_cast<const R*>(rb + RL.off_G);
+      const R T = tqs[2 * j];
+      const R Q = tqs[2 * j + 1];
+      R e0[G], up[G];
+#pragma unroll
+      for (int b = 0; b < G; ++b) {
+        e0[b] = cw[b] * T;
+        up[b] = R(0);
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int ref = reinterpret_cast<const int*>(rb + RL.off_ref)[k];
+        const R cf = reinterpret_cast<const R*>(rb + RL.off_coef)[k];
+        const R* src = ref >= 0 ? ring + ref * G : imps + (size_t)((-1 - ref) - m.imp) * a.Gpad;
+        R eu[G];
+        load_vals<R, G>(src, eu);
+#pragma unroll
+        for (int b = 0; b < G; ++b) up[b] += cf * (eu[b] - e0[b]);
+      }
+      R e[G];
+      R nl = R(0);
+#pragma unroll
+      for (int b = 0; b < G; ++b) {
+        const R phi = (aQ[b] * Q + vb[b] * up[b]) * recip(itau[b] + vb[b] * Gc);
+        e[b] = e0[b] + phi;
+        nl += wt[b] * phi;
+      }
+      if (slot >= 0) store_vals<R, G>(ring + slot * G, e);
+      if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * a.Gpad, e);
+      part[cell] = nl;
+      if (a.full) {
+        R es = R(0), evs = R(0);
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+          es += e[b];
+          evs += vb[b] * e[b];
+        }
+        atomicAdd(a.accE + cell, wi * (double)es);
+        for (int d = 0; d < a.dim; ++d)
+          atomicAdd(a.accQ + (int64_t)cell * a.dim + d, wi * a.dir_s[i * 3 + d] * (double)evs);
+      }
+    }
+    __syncwarp();
+    if ((ct & 31) == 0) mbar_arrive(empty + s);
+    if (m.nimp_end & (1 << 30)) consumer_barrier(ncons);
+  }
+}
+
+template <typename R, int K>
+static cudaError_t launch_k(const SweepArgs<R>& a, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
+  switch (G) {
+#define NBTE_G(Gv)                                                                                      \
+  case Gv: {                                                                                            \
+    auto kern = sweep_kernel<R, K, Gv>;                                                                 \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (e != cudaSuccess) return e;                                                                     \
+    kern<<<n_items, threads, smem, st>>>(a);                                                            \
+    return cudaGetLastError();                                                                          \
+  }
+    NBTE_G(1) NBTE_G(2) NBTE_G(4)
+#undef NBTE_G
+    case 8:
+      if constexpr (sizeof(R) == 4) {
+        auto kern = sweep_kernel<R, K, 8>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<n_items, threads, smem, st>>>(a);
+        return cudaGetLastError();
+      }
+      return cudaErrorInvalidConfiguration;
+    default:
+      return cudaErrorInvalidConfiguration;
+  }
+}
+
+template <typename R>
+cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
+  switch (K) {
+    case 1: return launch_k<R, 1>(a, G, n_items, threads, smem, st);
+    case 2: return launch_k<R, 2>(a, G, n_items, threads, smem, st);
+    case 3: return launch_k<R, 3>(a, G, n_items, threads, smem, st);
+    case 4: return launch_k<R, 4>(a, G, n_items, threads, smem, st);
+    case 5: return launch_k<R, 5>(a, G, n_items, threads, smem, st);
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
+
+// (T', Qdot) of every position's cell, in each direction's level order, so
+// the sweep's producer can bulk-copy them with the position records
+template <typename R>
+__global__ void gather_tq_kernel(R* tqp, const int32_t* rec_cells, int rec_stride_words, const R* srcTQ, int64_t n) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int cell = rec_cells[q * rec_stride_words];
+  tqp[2 * q] = srcTQ[2 * cell];
+  tqp[2 * q + 1] = srcTQ[2 * cell + 1];
+}
+
+template <typename R>
+cudaError_t launch_gather_tq(R* tqp, const void* rec, int rec_bytes, const R* srcTQ, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  gather_tq_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tqp, static_cast<const int32_t*>(rec),
+                                                                  rec_bytes / 4, srcTQ, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_gather_tq<float>(float*, const void*, int, const float*, int64_t, cudaStream_t);
+template cudaError_t launch_gather_tq<double>(double*, const void*, int, const double*, int64_t, cudaStream_t);
+
+}  // namespace nbte

@@ -119,11 +119,12 @@ def test_square_full_size_golden(nbte_mod):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [dict(band_group=1), dict(band_group=2, threads_per_cell=2),
-                                     dict(use_graph=True), dict(band_group=4, threads_per_cell=4, use_graph=True)])
+@pytest.mark.parametrize("variant", [dict(band_group=1), dict(band_group=2, cta_threads=96),
+                                     dict(use_graph=True), dict(band_group=4, cta_threads=544, use_graph=True)])
 def test_launch_variants_identical(nbte_mod, variant):
-    """Band grouping, threads per cell and graph replay change only the launch
-    shape: FP64 results are identical to the default to rounding."""
+    """Band grouping, CTA size (chunk length of the copy pipeline) and graph
+    replay change only the launch shape: FP64 results are identical to the
+    default to rounding."""
     p = CASES["fin2d_mixed"]()
     p.C, p.v, p.tau = (np.tile(x, 2)[:4] for x in (p.C, p.v, p.tau))
     s = nbte_mod.Solver(p)
@@ -159,4 +160,50 @@ def test_uniform_temperature_invariant_fp32(nbte_mod):
     info = s.solve(scheme="synthetic", precision="fp32", tol=1e-9, max_iter=5000)
     assert info["status"] == 0
     assert np.abs(s.temperature(0) - 303.0).max() < 3e-6 * 3.0
+    s.close()
+
+
+def _fin2d_golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    return json.load(open(path))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-6)])
+def test_finfet2d_full_size_steps(nbte_mod, precision, tol):
+    """The full-size 2D fin (50,474 triangles, 20 bands, 64 directions), in
+    the launch configuration the benchmark times (autotuned layout, graph
+    replay): T after sequential iterations 1 and 2 from T_ref on 4096 stored
+    oracle sample cells."""
+    g = _fin2d_golden("finfet2d_steps.json")
+    p = W.problems.finfet2d()
+    idx = np.array(g["cells"])
+    s = nbte_mod.Solver(p)
+    for n in (1, 2):
+        info = s.solve(scheme="sequential", precision=precision, n_iter=n, use_graph=True)
+        assert info["iterations"] == n
+        T = s.temperature(0)[idx]
+        err = np.abs(T - np.array(g[f"T_iter{n}"])).max() / g[f"T_iter{n}_max_dev"]
+        print(f"{precision} iteration {n}: rel err {err:.2e}")
+        assert err < tol
+    s.close()
+
+
+def test_finfet2d_full_size_converged(nbte_mod):
+    """The full-size 2D fin converged with the benchmark's scheme (synthetic,
+    FP32 sweep) and in FP64: T and q on the stored oracle sample cells."""
+    g = _fin2d_golden("finfet2d_converged.json")
+    p = W.problems.finfet2d()
+    idx = np.array(g["cells"])
+    Tg, qg = np.array(g["T"]), np.array(g["q"])
+    dev = g["T_max"] - p.T_ref
+    s = nbte_mod.Solver(p)
+    info = s.solve(scheme="synthetic", precision="fp64", tol=1e-12, max_iter=5000)
+    assert info["status"] == 0
+    assert np.abs(s.temperature(0)[idx] - Tg).max() / dev < 1e-8
+    assert np.abs(s.heat_flux()[idx] - qg).max() / np.abs(qg).max() < 1e-7
+    info = s.solve(scheme="synthetic", precision="fp32", tol=1e-9, max_iter=5000)
+    assert info["status"] == 0
+    assert np.abs(s.temperature(0)[idx] - Tg).max() / dev < 2e-6
     s.close()
