@@ -128,15 +128,17 @@ struct nbte_solver {
   int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0;
   size_t smem = 0;
   double W = 0, beta = 0, Ctot = 0;
-  DBuf rec, chunks, chunk_off, tqp;
+  DBuf rec, pos_cell, chunks, chunk_off, tqp;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
-  DBuf cg_r, cg_z, cg_p, cg_Ap, cg_partial, cg_bar, cg_err, cg_it, cg_res;
-  DBuf cg_x, cg_rc, cg_yc, cg_perm, cg_agg, cg_agg_cell, cg_blk_cell, cg_blk_agg, cg_Ainv;
-  int cg_grid = 0, cg_Nc = 0, cg_Nc4 = 0;
+  DBuf cg_r, cg_u, cg_w, cg_p, cg_s, cg_xw, cg_slots, cg_bar, cg_err, cg_it, cg_res;
+  DBuf cg_Ainv64;
+  DBuf cg_x, cg_rw, cg_rcx, cg_scx, cg_perm, cg_agg_rel, cg_agg_cell, cg_blk_cell, cg_blk_agg, cg_Ainv;
+  int cg_grid = 0, cg_threads = kCGThreads, cg_Nc = 0, cg_Nc4 = 0, cg_W = 0;
+  int cg_max_rows = 0, cg_max_na = 0, cg_smem_vec = 0, cg_smem_ell = 0;
   // ---- laplacian (synthetic)
   int64_t lap_built = -1;
-  DBuf L_rp, L_col, L_val, L_dinv;
+  DBuf L_ecol, L_eval, L_diag, L_dinv;
   // ---- autotuned sweep layout per precision
   Tuned tuned[2];
   // ---- state
@@ -174,17 +176,18 @@ struct DeviceGuard {
 };
 
 size_t device_bytes(const nbte_solver* S) {
-  const DBuf* all[] = {&S->rec, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
+  const DBuf* all[] = {&S->rec, &S->pos_cell, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
                        &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
                        &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
                        &S->band_CoW, &S->band_v64, &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part,
                        &S->T, &S->Tprev, &S->Tkin, &S->Delta, &S->rhs, &S->delta, &S->Qd, &S->Vd, &S->dsum,
-                       &S->accE, &S->accQ, &S->res, &S->heat, &S->cg_r, &S->cg_z, &S->cg_p, &S->cg_Ap,
-                       &S->cg_partial, &S->cg_bar, &S->cg_err, &S->cg_it, &S->cg_res, &S->cg_x, &S->cg_rc,
-                       &S->cg_yc, &S->cg_perm, &S->cg_agg, &S->cg_agg_cell, &S->cg_blk_cell, &S->cg_blk_agg,
-                       &S->cg_Ainv, &S->L_rp, &S->L_col,
-                       &S->L_val, &S->L_dinv};
+                       &S->accE, &S->accQ, &S->res, &S->heat, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s,
+                       &S->cg_w, &S->cg_slots, &S->cg_err, &S->cg_it, &S->cg_res, &S->cg_x, &S->cg_rw,
+                       &S->cg_rcx, &S->cg_scx, &S->cg_xw, &S->cg_bar, &S->cg_Ainv64,
+                       &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell, &S->cg_blk_agg,
+                       &S->cg_Ainv, &S->L_ecol, &S->L_eval,
+                       &S->L_diag, &S->L_dinv};
   size_t t = 0;
   for (auto* b : all) t += b->bytes;
   return t;
@@ -294,6 +297,7 @@ int ensure_records(nbte_solver* S) {
       }
     }
   NBTE_CK(upload(S->rec, buf));
+  NBTE_CK(upload(S->pos_cell, P.pos_cell));
   S->rec_key = key;
   return NBTE_OK;
 }
@@ -506,7 +510,7 @@ int ensure_q(nbte_solver* S) {
 
 int ensure_laplacian(nbte_solver* S) {
   const int64_t want = S->version_bands * 1000003 + S->version_plan;
-  if (S->lap_built == want && S->L_rp.p) return NBTE_OK;
+  if (S->lap_built == want && S->L_diag.p) return NBTE_OK;
   const Mesh& m = S->mesh->m;
   // kappa_bulk = sum C v^2 tau * (1/dim) sum_i w_i |s_i|^2 / W  (in-domain s)
   double ang = 0, mean_abs = 0, W = 0;
@@ -546,19 +550,24 @@ int ensure_laplacian(nbte_solver* S) {
     agg_cell[agg_p[c] + 1]++;
   }
   for (int k = 0; k < Nc; ++k) agg_cell[k + 1] += agg_cell[k];
-  std::vector<int32_t> rp(N + 1, 0), col;
-  std::vector<double> val, dinv(N);
-  col.reserve(L.col.size());
-  val.reserve(L.val.size());
+  // ELL off-diagonals [k][row] (padding: own row, value 0) and the diagonal,
+  // rows in aggregate order; Galerkin coarse operator Ac = P^T A P
+  const int Wl = m.nfc;
+  std::vector<int32_t> ecol((size_t)Wl * N);
+  std::vector<double> eval((size_t)Wl * N, 0.0), diag(N), dinv(N);
   std::vector<double> Ac((size_t)Nc * Nc, 0.0);
   for (int64_t r = 0; r < N; ++r) {
     const int32_t c = perm[r];
-    for (int32_t k = L.row_ptr[c]; k < L.row_ptr[c + 1]; ++k) {
-      col.push_back(iperm[L.col[k]]);
-      val.push_back(L.val[k]);
-      Ac[(size_t)agg[c] * Nc + agg[L.col[k]]] += L.val[k];
+    int k = 0;
+    for (int32_t j = L.row_ptr[c]; j < L.row_ptr[c + 1]; ++j) {
+      Ac[(size_t)agg[c] * Nc + agg[L.col[j]]] += L.val[j];
+      if (L.col[j] == c) continue;
+      ecol[(size_t)k * N + r] = iperm[L.col[j]];
+      eval[(size_t)k * N + r] = L.val[j];
+      ++k;
     }
-    rp[r + 1] = (int32_t)col.size();
+    for (; k < Wl; ++k) ecol[(size_t)k * N + r] = (int32_t)r;
+    diag[r] = L.diag[c];
     dinv[r] = 1.0 / L.diag[c];
   }
   if (!dense_spd_inverse(Ac, Nc))
@@ -566,9 +575,8 @@ int ensure_laplacian(nbte_solver* S) {
   int nsm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device);
   // one block per SM: the CG is latency-bound, so every SM's warps are used
-  // to shorten each block's dependent-load chains (a grid barrier costs
-  // about the same for 8 or 148 blocks)
-  const int grid = std::max(1, std::min(nsm, Nc));
+  // to shorten each block's dependent-load chains
+  const int grid = std::max(1, std::min(std::min(nsm, 256), Nc));
   std::vector<int32_t> blk_cell(grid + 1, 0), blk_agg(grid + 1, 0);
   {
     int b = 0;
@@ -584,37 +592,68 @@ int ensure_laplacian(nbte_solver* S) {
     blk_agg[grid] = Nc;
     for (int k = 0; k <= grid; ++k) blk_cell[k] = agg_cell[blk_agg[k]];
   }
+  std::vector<int32_t> agg_rel(N);
+  int max_rows = 1, max_na = 1;
+  for (int k = 0; k < grid; ++k) {
+    max_rows = std::max(max_rows, blk_cell[k + 1] - blk_cell[k]);
+    max_na = std::max(max_na, blk_agg[k + 1] - blk_agg[k]);
+    for (int32_t r = blk_cell[k]; r < blk_cell[k + 1]; ++r) agg_rel[r] = agg_p[r] - blk_agg[k];
+  }
+  const int Nc4 = (Nc + 3) / 4;
+  // threads per block: enough for one pass over the largest block's rows
+  const int threads = std::min(kCGThreads, std::max(128, (max_rows + 31) / 32 * 32));
+  // shared memory: own-row vectors first, then the ELL rows, as far as they
+  // fit (sized for the FP64 coarse variant, the larger one)
+  const size_t budget = (size_t)kSweepSmemMax - 2048;
+  auto need = [&](int v, int e) { return cg_smem_layout(Nc4, max_rows, max_na, Wl, threads, v, e, 8).total; };
+  int vec = need(1, 0) <= budget;
+  int ell = vec && need(1, 1) <= budget;
+  if (need(0, 0) > budget) return fail(NBTE_ERR_ARG, "synthetic correction: too many aggregates per block");
   DeviceGuard g(S->device);
-  NBTE_CK(upload(S->L_rp, rp));
-  NBTE_CK(upload(S->L_col, col));
-  NBTE_CK(upload(S->L_val, val));
+  NBTE_CK(upload(S->L_ecol, ecol));
+  NBTE_CK(upload(S->L_eval, eval));
+  NBTE_CK(upload(S->L_diag, diag));
   NBTE_CK(upload(S->L_dinv, dinv));
   NBTE_CK(upload(S->cg_perm, perm));
-  NBTE_CK(upload(S->cg_agg, agg_p));
+  NBTE_CK(upload(S->cg_agg_rel, agg_rel));
   NBTE_CK(upload(S->cg_agg_cell, agg_cell));
   NBTE_CK(upload(S->cg_blk_cell, blk_cell));
   NBTE_CK(upload(S->cg_blk_agg, blk_agg));
-  const int Nc4 = (Nc + 3) / 4;
   std::vector<float> Af((size_t)Nc * Nc4 * 4, 0.0f);
   for (int r = 0; r < Nc; ++r)
     for (int c = 0; c < Nc; ++c) Af[(size_t)r * Nc4 * 4 + c] = (float)Ac[(size_t)r * Nc + c];
   NBTE_CK(upload(S->cg_Ainv, Af));
+  std::vector<double> Ad((size_t)Nc * Nc4 * 4, 0.0);
+  for (int r = 0; r < Nc; ++r)
+    for (int c = 0; c < Nc; ++c) Ad[(size_t)r * Nc4 * 4 + c] = Ac[(size_t)r * Nc + c];
+  NBTE_CK(upload(S->cg_Ainv64, Ad));
   S->cg_Nc4 = Nc4;
+  S->cg_W = Wl;
+  S->cg_max_rows = max_rows;
+  S->cg_max_na = max_na;
+  S->cg_smem_vec = vec;
+  S->cg_smem_ell = ell;
   NBTE_CK(S->cg_x.alloc(N * 8));
-  NBTE_CK(S->cg_r.alloc(N * 8));
-  NBTE_CK(S->cg_z.alloc(N * 8));
-  NBTE_CK(S->cg_p.alloc(N * 8));
-  NBTE_CK(S->cg_Ap.alloc(N * 8));
-  NBTE_CK(S->cg_rc.alloc((size_t)Nc * 8));
-  NBTE_CK(S->cg_yc.alloc((size_t)Nc * 8));
+  NBTE_CK(S->cg_u.alloc(N * 8));
+  const size_t work = vec ? 16 : (size_t)N * 8;   // global work vectors only when not in shared memory
+  NBTE_CK(S->cg_xw.alloc(work));
+  NBTE_CK(S->cg_r.alloc(work));
+  NBTE_CK(S->cg_p.alloc(work));
+  NBTE_CK(S->cg_s.alloc(work));
+  NBTE_CK(S->cg_w.alloc(work));
+  NBTE_CK(S->cg_rw.alloc((size_t)Nc * 8));
+  NBTE_CK(S->cg_rcx.alloc((size_t)Nc * 8));
+  NBTE_CK(S->cg_scx.alloc((size_t)Nc * 8));
   S->cg_grid = grid;
   S->cg_Nc = Nc;
-  NBTE_CK(S->cg_partial.alloc((size_t)5 * S->cg_grid * 8));
+  S->cg_threads = threads;
   NBTE_CK(cudaMemset(S->cg_x.p, 0, N * 8));   // no previous correction yet
+  NBTE_CK(S->cg_slots.alloc((size_t)grid * sizeof(CGSlot)));
   NBTE_CK(S->cg_bar.alloc(16));
   NBTE_CK(S->cg_err.alloc(16));
   NBTE_CK(S->cg_it.alloc(16));
   NBTE_CK(S->cg_res.alloc(16));
+  NBTE_CK(cudaMemset(S->cg_slots.p, 0, S->cg_slots.bytes));
   NBTE_CK(cudaMemset(S->cg_bar.p, 0, 16));
   NBTE_CK(cudaMemset(S->cg_err.p, 0, 16));
   S->lap_built = want;
@@ -711,28 +750,37 @@ CGArgs cg_args(nbte_solver* S, double tol, int max_it) {
   CGArgs a{};
   a.N = (int)S->mesh->m.n_cells;
   a.Nc = S->cg_Nc;
-  a.rp = S->L_rp.as<int32_t>();
-  a.col = S->L_col.as<int32_t>();
-  a.val = S->L_val.as<double>();
+  a.W = S->cg_W;
+  a.ell_col = S->L_ecol.as<int32_t>();
+  a.ell_val = S->L_eval.as<double>();
+  a.diag = S->L_diag.as<double>();
   a.dinv = S->L_dinv.as<double>();
   a.perm = S->cg_perm.as<int32_t>();
-  a.agg = S->cg_agg.as<int32_t>();
+  a.agg_rel = S->cg_agg_rel.as<int32_t>();
   a.agg_cell = S->cg_agg_cell.as<int32_t>();
   a.blk_cell = S->cg_blk_cell.as<int32_t>();
   a.blk_agg = S->cg_blk_agg.as<int32_t>();
-  a.Ainv = S->cg_Ainv.as<float>();
+  a.Ainv32 = S->cg_Ainv.as<float>();
+  a.Ainv64 = S->cg_Ainv64.as<double>();
   a.Nc4 = S->cg_Nc4;
+  a.max_rows = S->cg_max_rows;
+  a.max_na = S->cg_max_na;
+  a.smem_vec = S->cg_smem_vec;
+  a.smem_ell = S->cg_smem_ell;
   a.b = S->rhs.as<double>();
   a.x_out = S->delta.as<double>();
   a.x = S->cg_x.as<double>();
-  a.rc = S->cg_rc.as<double>();
-  a.yc = S->cg_yc.as<double>();
+  a.u = S->cg_u.as<double>();
+  a.x_work = S->cg_xw.as<double>();
   a.r = S->cg_r.as<double>();
-  a.z = S->cg_z.as<double>();
   a.p = S->cg_p.as<double>();
-  a.Ap = S->cg_Ap.as<double>();
-  a.partial = S->cg_partial.as<double>();
-  a.bar = S->cg_bar.as<unsigned>();
+  a.s = S->cg_s.as<double>();
+  a.w = S->cg_w.as<double>();
+  a.rw = S->cg_rw.p;
+  a.rcx = S->cg_rcx.p;
+  a.scx = S->cg_scx.p;
+  a.slots = S->cg_slots.as<CGSlot>();
+  a.bar = S->cg_bar.as<unsigned long long>();
   a.err = S->cg_err.as<int32_t>();
   a.tol = tol;
   a.max_it = max_it;
@@ -749,7 +797,7 @@ cudaError_t enqueue_iteration(nbte_solver* S, int scheme, double cg_tol, int cg_
   launch_walls<R>(wall_args<R>(S), st);
   cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  e = launch_gather_tq<R>(S->tqp.as<R>(), S->rec.p, rec_layout((int)sizeof(R), S->K).size, S->srcTQ.as<R>(),
+  e = launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
                           (int64_t)S->D * S->mesh->m.n_cells, st);
   if (e != cudaSuccess) return e;
   if (ev0) cudaEventRecord(ev0, st);
@@ -762,7 +810,13 @@ cudaError_t enqueue_iteration(nbte_solver* S, int scheme, double cg_tol, int cg_
     launch_update<R>(update_args<R>(S, 0), st);
   } else {
     launch_update<R>(update_args<R>(S, 3), st);
-    e = launch_cg(cg_args(S, cg_tol, cg_max), S->cg_grid, st);
+    // an FP32 coarse preconditioner suffices unless the correction is wanted
+    // to near FP64 rounding
+    const bool c32 = cg_tol >= 1e-7;
+    const size_t smem = cg_smem_layout(S->cg_Nc4, S->cg_max_rows, S->cg_max_na, S->cg_W, S->cg_threads,
+                                       S->cg_smem_vec, S->cg_smem_ell, c32 ? 4 : 8)
+                            .total;
+    e = launch_cg(cg_args(S, cg_tol, cg_max), c32, S->cg_grid, S->cg_threads, smem, st);
     if (e != cudaSuccess) return e;
     launch_update<R>(update_args<R>(S, scheme == 1 ? 1 : 2), st);
   }
@@ -806,7 +860,7 @@ int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
   if (rc) return rc;
   cudaStream_t st = S->stream;
   launch_walls<R>(wall_args<R>(S), st);
-  NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->rec.p, rec_layout((int)sizeof(R), S->K).size, S->srcTQ.as<R>(),
+  NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
                               (int64_t)S->D * S->mesh->m.n_cells, st));
   NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 0), S->K, S->G, S->n_items, S->threads, S->smem, st));
   cudaEvent_t e0, e1;
@@ -954,6 +1008,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     if (S->h_misc[0] != 0 && scheme != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the CG correction gave up");
       cudaMemset(S->cg_err.p, 0, 16);
+      cudaMemset(S->cg_slots.p, 0, S->cg_slots.bytes);
       cudaMemset(S->cg_bar.p, 0, 16);
       return true;
     }
@@ -1013,8 +1068,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     NBTE_CK(cudaMemsetAsync(S->accE.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
     launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
-    NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->rec.p, rec_layout((int)sizeof(R), S->K).size,
-                                S->srcTQ_fin.as<R>(), (int64_t)S->D * N, st));
+    NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ_fin.as<R>(), (int64_t)S->D * N, st));
     NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 1), S->K, S->G, S->n_items, S->threads, S->smem, st));
     WallHeatArgs<R> wh{};
     wh.Bp = S->Bp;

@@ -98,41 +98,86 @@ void launch_walls(const WallArgs<R>& a, cudaStream_t st) {
 }
 
 // ============================================================================ update
-__device__ __forceinline__ void block_max2(double& x, double& y, unsigned long long* res) {
-  __shared__ double sx[32], sy[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-    y = fmax(y, __shfl_xor_sync(0xffffffffu, y, o));
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { sx[w] = x; sy[w] = y; }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    x = l < nw ? sx[l] : 0.0;
-    y = l < nw ? sy[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-      y = fmax(y, __shfl_xor_sync(0xffffffffu, y, o));
-    }
-    if (l == 0) {
-      // non-negative doubles order like their bit patterns; NaN sorts above +inf
-      atomicMax(res, (unsigned long long)__double_as_longlong(x));
-      atomicMax(res + 1, (unsigned long long)__double_as_longlong(y));
-    }
-  }
+// One block per 32 cells.  The collision-moment partials of the n_items work
+// items are summed by 8 item slices per cell and combined in shared memory in
+// a fixed order; one warp then applies the update.  FP32 partials are summed
+// with compensation (Kahan) in FP32, which keeps the sum to FP32 rounding of
+// the total while spending no FP64 instruction per partial; FP64 partials are
+// summed in FP64.
+constexpr int kUpdCells = 32, kUpdSlices = 8;
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
 }
 
 template <typename R>
-__global__ void update_kernel(const UpdateArgs<R> a) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kUpdCells * kUpdSlices) update_kernel(const UpdateArgs<R> a) {
+  const int c = blockIdx.x * kUpdCells + threadIdx.x;
+  const bool reduce = a.mode == 0 || a.mode == 3;
+  double s = 0.0;
+  if (reduce) {
+    const int64_t N = a.N;
+    if constexpr (sizeof(R) == 4) {
+      __shared__ float red_s[kUpdSlices][kUpdCells], red_c[kUpdSlices][kUpdCells];
+      float ks = 0.0f, kc = 0.0f;
+      if (c < a.N) {
+        const R* p = a.part + c;
+        int it = threadIdx.y;
+        for (; it + 3 * kUpdSlices < a.n_items; it += 4 * kUpdSlices) {
+          const float x0 = __ldcs(p + it * N), x1 = __ldcs(p + (it + kUpdSlices) * N);
+          const float x2 = __ldcs(p + (it + 2 * kUpdSlices) * N), x3 = __ldcs(p + (it + 3 * kUpdSlices) * N);
+          kahan_add(ks, kc, x0);
+          kahan_add(ks, kc, x1);
+          kahan_add(ks, kc, x2);
+          kahan_add(ks, kc, x3);
+        }
+        for (; it < a.n_items; it += kUpdSlices) kahan_add(ks, kc, __ldcs(p + it * N));
+      }
+      red_s[threadIdx.y][threadIdx.x] = ks;
+      red_c[threadIdx.y][threadIdx.x] = kc;
+      __syncthreads();
+      if (threadIdx.y != 0) return;
+      float ts = 0.0f, tc = 0.0f;
+#pragma unroll
+      for (int y = 0; y < kUpdSlices; ++y) {
+        kahan_add(ts, tc, red_s[y][threadIdx.x]);
+        kahan_add(ts, tc, -red_c[y][threadIdx.x]);
+      }
+      s = (double)ts - (double)tc;
+    } else {
+      __shared__ double red[kUpdSlices][kUpdCells];
+      if (c < a.N) {
+        const R* p = a.part + c;
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+        int it = threadIdx.y;
+        for (; it + 3 * kUpdSlices < a.n_items; it += 4 * kUpdSlices) {
+          acc0 += __ldcs(p + it * N);
+          acc1 += __ldcs(p + (it + kUpdSlices) * N);
+          acc2 += __ldcs(p + (it + 2 * kUpdSlices) * N);
+          acc3 += __ldcs(p + (it + 3 * kUpdSlices) * N);
+        }
+        for (; it < a.n_items; it += kUpdSlices) acc0 += __ldcs(p + it * N);
+        s = (acc0 + acc1) + (acc2 + acc3);
+      }
+      red[threadIdx.y][threadIdx.x] = s;
+      __syncthreads();
+      if (threadIdx.y != 0) return;
+      s = 0.0;
+#pragma unroll
+      for (int y = 0; y < kUpdSlices; ++y) s += red[y][threadIdx.x];
+    }
+  } else if (threadIdx.y != 0) {
+    return;
+  }
+  // one warp per block from here on
   double dmax = 0.0, tmax = 0.0;
   if (c < a.N) {
     const double Told = a.T[c];
     double TL = 0.0;
-    if (a.mode == 0 || a.mode == 3) {
-      double s = 0.0;
-      for (int it = 0; it < a.n_items; ++it) s += a.part[(int64_t)it * a.N + c];
+    if (reduce) {
       // Eq. (5) as a deviation from T_ref: the equilibrium part of every
       // distribution sums to beta T'_used, T'_used being the (possibly
       // reduced-precision) temperature the sweep emitted from
@@ -156,12 +201,23 @@ __global__ void update_kernel(const UpdateArgs<R> a) {
       a.srcTQ_next[2 * c + 1] = (R)a.Q[c];
     }
   }
-  if (a.mode != 3) block_max2(dmax, tmax, a.res);
+  if (a.mode != 3) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    }
+    if (threadIdx.x == 0) {
+      // non-negative doubles order like their bit patterns; NaN sorts above +inf
+      atomicMax(a.res, (unsigned long long)__double_as_longlong(dmax));
+      atomicMax(a.res + 1, (unsigned long long)__double_as_longlong(tmax));
+    }
+  }
 }
 
 template <typename R>
 void launch_update(const UpdateArgs<R>& a, cudaStream_t st) {
-  update_kernel<R><<<(a.N + 255) / 256, 256, 0, st>>>(a);
+  const bool reduce = a.mode == 0 || a.mode == 3;
+  update_kernel<R><<<(a.N + kUpdCells - 1) / kUpdCells, dim3(kUpdCells, reduce ? kUpdSlices : 1), 0, st>>>(a);
 }
 
 template <typename R>
@@ -178,247 +234,392 @@ void launch_fill_srcTQ(R* srcTQ, const double* T, const double* Q, int N, cudaSt
 }
 
 // ============================================================================ CG
+// FP64 arithmetic is scarce on this part (a warp-wide FP64 instruction holds
+// its scheduler's FP64 pipe for tens of cycles), so the kernel below spends
+// FP64 instructions only where the correction's accuracy needs them: the
+// vectors, the matrix product and the inner products.  Scalars are formed by
+// one thread, block sums go through shared memory to one warp per value, and
+// with a loose tolerance the coarse preconditioner runs in FP32.
 namespace {
-constexpr unsigned long long kSpinLimit = 1ull << 25;   // ~seconds with nanosleep
+constexpr unsigned long long kSpinLimit = 1ull << 24;   // polls of the barrier word before giving up (seconds)
 
-// Grid barrier for a cooperative launch (all blocks co-resident).  bar[0] is
-// a counter that only grows: a block arriving as number k waits until the
-// counter reaches the next multiple of the block count.  The host zeroes it
-// before each launch.  The wait spins tightly first, then backs off, and is
-// bounded: on timeout the error word is set and every block leaves.
-__device__ bool grid_sync(unsigned* bar, int32_t* err, unsigned nblocks) {
+__device__ __forceinline__ double warp_sum(double s) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+__device__ __forceinline__ float warp_sumf(float s) {
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Grid barrier fused with a reduction of NV (<= 3) values.  Thread values go
+// to red_s[j][tid]; warp j sums column j and writes the block's sum into its
+// slot (buffer gen & 1); thread 0 arrives on a 64-bit counter that only grows
+// (a block arriving as number k waits for the next multiple of the block
+// count); after the barrier warp j loads every block's sum j at once and adds
+// them in one fixed order, so all blocks get the same totals.  The wait is
+// bounded: on timeout, or when another block reported one, the error word is
+// set and the function returns true.  Thread 0 replaces inv[0..n_inv) by
+// their reciprocals while it waits (work off the critical path).
+template <int NV>
+__device__ bool grid_reduce(const double* v, double* tot, double* red_s, CGSlot* slots, unsigned long long* bar,
+                            unsigned gen, int32_t* err, double* inv = nullptr, int n_inv = 0) {
+  static_assert(NV >= 0 && NV <= 3, "a slot carries up to three sums");
+  __shared__ double s_tot[3];
   __shared__ int s_abort;
+  const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned nb = gridDim.x;
+  const int buf = gen & 1;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) red_s[j * T + tid] = v[j];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned old = atomicAdd(bar, 1u);
-    const unsigned target = (old / nblocks + 1) * nblocks;
-    volatile unsigned* vc = bar;
+  if (warp < NV) {
+    double y = 0.0;
+    for (int i = lane; i < T; i += 32) y += red_s[warp * T + i];
+    y = warp_sum(y);
+    if (lane == 0) slots[blockIdx.x].v[buf][warp] = y;
+  }
+  __syncthreads();   // orders every thread's global writes (and the slot sums) before the fence below
+  if (tid == 0) {
     int abort = 0;
+    __threadfence();
+    const unsigned long long old = atomicAdd(bar, 1ull);
+    const unsigned long long target = (old / nb + 1) * nb;
+    for (int k = 0; k < n_inv; ++k) inv[k] = 1.0 / inv[k];
+    volatile unsigned long long* vb = bar;
     unsigned long long spins = 0;
-    while ((int)(*vc - target) < 0) {
+    while (*vb < target) {
       if (++spins > kSpinLimit) {
         atomicExch(err, (int32_t)DEV_BARRIER_TIMEOUT);
         abort = 1;
         break;
       }
-      if (spins > 2048) __nanosleep(32);
+      if (spins > 4096) __nanosleep(64);
     }
     __threadfence();
     if (*(volatile int32_t*)err != 0) abort = 1;
     s_abort = abort;
   }
   __syncthreads();
+  if (warp < NV) {
+    // every block's sum at once (grid <= 256), added in one fixed order
+    double t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[k] = (unsigned)(k * 32 + lane) < nb ? __ldcg(&slots[k * 32 + lane].v[buf][warp]) : 0.0;
+    double y = t[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k)
+      if ((unsigned)(k * 32) < nb) y += t[k];
+    y = warp_sum(y);
+    if (lane == 0) s_tot[warp] = y;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) tot[j] = s_tot[j];
   return s_abort != 0;
 }
 
-// block-wide sum, result valid in every thread
-__device__ double block_sum(double x) {
-  __shared__ double sh[32];
-  __shared__ double tot;
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    double y = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-    if (l == 0) tot = y;
-  }
-  __syncthreads();
-  return tot;
-}
-
-// sum of the per-block partials written before the last grid barrier: every
-// block reads them with the same lane split and the same shuffle tree, so all
-// blocks get the same (deterministic) value
-__device__ double grid_total(const double* partial, int slot) {
-  __shared__ double tot;
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) s += __ldcg(partial + slot * gridDim.x + b);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) tot = s;
-  }
-  __syncthreads();
-  const double r = tot;
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ double warp_sum(double s) {
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
+template <bool C32>
+struct CoarseT { using T = double; };
+template <>
+struct CoarseT<true> { using T = float; };
 }  // namespace
 
-// Persistent two-level PCG (one launch per synthetic correction).  Three grid
-// barriers per iteration: after p.Ap, after the aggregate restriction, after
-// r.z.  A p is updated as A z + beta A p_old so that the SpMV only needs z,
-// which is complete at the r.z barrier.
+// Persistent two-level PCG (one launch per synthetic correction), in the
+// Chronopoulos-Gear arrangement: with u = M^{-1} r and w = A u, the two inner
+// products (r,u) and (w,u) come from one reduction, and s = A p follows the
+// recurrence s = w + beta s.  Two grid barriers per iteration:
+//   X  after w = A u, carrying (r,u), (w,u), (r,r);
+//   Z  after u = M^{-1} r, so the next product A u sees every row of u.
+// The coarse part of M needs every aggregate's sum of r.  Each block keeps all
+// of them in shared memory and advances them with the same linear recurrence
+// as r itself (P^T r <- P^T r - alpha (P^T w + beta P^T s)), starting each
+// step from the exact sums the owning blocks computed one step earlier, so no
+// third barrier is needed and rounding does not accumulate.
+//
+// A block's own rows of x, r, p, s, w, u, D^{-1} (and, when they fit, its
+// ELL matrix rows) live in shared memory; only u is mirrored to global memory
+// for the neighbours' products.  Row l of the block is cell c0 + l.  C32: the
+// coarse sums, the coarse inverse product and the correction it yields are
+// FP32 (a preconditioner only has to be fixed and SPD to rounding; the
+// iteration's vectors and inner products stay FP64).
+template <bool C32>
 __global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
-  const unsigned nb = gridDim.x;
-  const int c0 = a.blk_cell[blockIdx.x], c1 = a.blk_cell[blockIdx.x + 1];
-  const int a0 = a.blk_agg[blockIdx.x], a1 = a.blk_agg[blockIdx.x + 1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-
-  // aggregate restriction of r for the block's own aggregates
-  auto restrict_r = [&]() {
-    for (int g = a0 + warp; g < a1; g += nwarp) {
-      double s = 0.0;
-      for (int c = a.agg_cell[g] + lane; c < a.agg_cell[g + 1]; c += 32) s += a.r[c];
-      s = warp_sum(s);
-      if (lane == 0) a.rc[g] = s;
+  using CT = typename CoarseT<C32>::T;
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  const int c0 = a.blk_cell[blockIdx.x], nr = a.blk_cell[blockIdx.x + 1] - c0;
+  const int a0 = a.blk_agg[blockIdx.x], na = a.blk_agg[blockIdx.x + 1] - a0;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = T >> 5;
+  const int Nc = a.Nc, nc4 = a.Nc4, W = a.W;
+  __shared__ double s_scal[4];
+  CgSmem L = cg_smem_layout(nc4, a.max_rows, a.max_na, W, T, a.smem_vec, a.smem_ell, (int)sizeof(CT));
+  double* red_s = reinterpret_cast<double*>(cg_smem + L.red);
+  CT* rc_s = reinterpret_cast<CT*>(cg_smem + L.rc);   // aggregate sums of r, every aggregate
+  CT* sc_s = reinterpret_cast<CT*>(cg_smem + L.sc);   // aggregate sums of s
+  CT* yc_s = reinterpret_cast<CT*>(cg_smem + L.yc);   // coarse correction, own aggregates
+  CT* fr_s = reinterpret_cast<CT*>(cg_smem + L.fr);   // own rows of the vector being restricted
+  int32_t* ab_s = reinterpret_cast<int32_t*>(cg_smem + L.ab);   // own aggregates' first rows
+  for (int g = tid; g <= na; g += T) ab_s[g] = a.agg_cell[a0 + g] - c0;
+  double *x, *r, *p, *s, *w, *u, *dv;
+  const int32_t* ag;   // aggregate of each own row, relative to a0
+  if (a.smem_vec) {
+    x = reinterpret_cast<double*>(cg_smem + L.vec);
+    r = x + a.max_rows;
+    p = r + a.max_rows;
+    s = p + a.max_rows;
+    w = s + a.max_rows;
+    u = w + a.max_rows;
+    dv = u + a.max_rows;
+    int32_t* ag_s = reinterpret_cast<int32_t*>(dv + a.max_rows);
+    for (int l = tid; l < nr; l += T) {
+      x[l] = a.x[c0 + l];
+      dv[l] = a.dinv[c0 + l];
+      ag_s[l] = a.agg_rel[c0 + l];
     }
-  };
-  // coarse correction rows for the block's own aggregates: the restricted
-  // residual is staged in shared memory, the (symmetric, FP32-stored) coarse
-  // inverse is read four entries per load, sums are FP64
-  __shared__ double rc_s[kMaxCoarse];
-  auto coarse_rows = [&]() {
-    const int nc4 = a.Nc4;
-    for (int k = threadIdx.x; k < 4 * nc4; k += blockDim.x) rc_s[k] = k < a.Nc ? __ldcg(a.rc + k) : 0.0;
-    __syncthreads();
-    for (int g = a0 + warp; g < a1; g += nwarp) {
-      const float4* row = reinterpret_cast<const float4*>(a.Ainv + (int64_t)g * nc4 * 4);
-      double s = 0.0;
-#pragma unroll 4
-      for (int k = lane; k < nc4; k += 32) {
-        const float4 v = __ldg(row + k);
-        const double* r = rc_s + 4 * k;
-        s += (double)v.x * r[0] + (double)v.y * r[1] + (double)v.z * r[2] + (double)v.w * r[3];
+    ag = ag_s;
+  } else {
+    x = a.x_work + c0;
+    r = a.r + c0;
+    p = a.p + c0;
+    s = a.s + c0;
+    w = a.w + c0;
+    u = a.u + c0;
+    dv = const_cast<double*>(a.dinv) + c0;
+    ag = a.agg_rel + c0;
+    for (int l = tid; l < nr; l += T) x[l] = a.x[c0 + l];
+  }
+  // ELL off-diagonals [k][row] and the diagonal
+  const double* ev;
+  const int32_t* ec;
+  const double* dg;
+  int es;
+  if (a.smem_ell) {
+    double* v_s = reinterpret_cast<double*>(cg_smem + L.ell);
+    double* d_s = v_s + (size_t)W * a.max_rows;
+    int32_t* c_s = reinterpret_cast<int32_t*>(d_s + a.max_rows);
+    for (int l = tid; l < nr; l += T) {
+      d_s[l] = a.diag[c0 + l];
+      for (int k = 0; k < W; ++k) {
+        v_s[k * a.max_rows + l] = a.ell_val[(int64_t)k * a.N + c0 + l];
+        c_s[k * a.max_rows + l] = a.ell_col[(int64_t)k * a.N + c0 + l];
       }
-      s = warp_sum(s);
-      if (lane == 0) a.yc[g] = s;
+    }
+    ev = v_s;
+    ec = c_s;
+    dg = d_s;
+    es = a.max_rows;
+  } else {
+    ev = a.ell_val + c0;
+    ec = a.ell_col + c0;
+    dg = a.diag + c0;
+    es = a.N;
+  }
+  for (int k = Nc + tid; k < 4 * nc4; k += T) rc_s[k] = CT(0);   // row padding of the coarse inverse
+  const CT* Ainv = reinterpret_cast<const CT*>(C32 ? static_cast<const void*>(a.Ainv32) : static_cast<const void*>(a.Ainv64));
+  CT* rcx = static_cast<CT*>(a.rcx);
+  CT* scx = static_cast<CT*>(a.scx);
+  CT* rw = static_cast<CT*>(a.rw);
+  unsigned gen = 0;
+  __syncthreads();
+
+  // (A v)_row for row l; v is a global vector in aggregate order.  The
+  // neighbour loads are issued together, the products form one FMA chain.
+  auto spmv = [&](const double* vg, int l) {
+    double t[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < W) t[k] = __ldcg(vg + ec[k * es + l]);
+    double y = dg[l] * __ldcg(vg + c0 + l);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < W) y = fma(ev[k * es + l], t[k], y);
+    return y;
+  };
+  // aggregate sums of fr_s (own rows) over the own aggregates, one warp per
+  // aggregate, written to out[global aggregate]
+  auto restrict_own = [&](CT* out) {
+    for (int g = warp; g < na; g += nwarp) {
+      CT t = CT(0);
+      for (int l = ab_s[g] + lane; l < ab_s[g + 1]; l += 32) t += fr_s[l];
+      if constexpr (C32) t = warp_sumf(t);
+      else t = warp_sum(t);
+      if (lane == 0) out[a0 + g] = t;
     }
   };
-  auto spmv = [&](const double* v, int c) {
-    double y = 0.0;
-    for (int k = a.rp[c]; k < a.rp[c + 1]; ++k) y += a.val[k] * __ldcg(v + a.col[k]);
-    return y;
+  // u = D^{-1} r + P Ac^{-1} rc on own rows: the coarse rows of the own
+  // aggregates (the symmetric inverse read four entries per load), then the
+  // fine rows; u is mirrored to global memory
+  auto precondition = [&]() {
+    for (int g = warp; g < na; g += nwarp) {
+      const CT* row = Ainv + (int64_t)(a0 + g) * nc4 * 4;
+      CT t = CT(0);
+#pragma unroll 8
+      for (int k = lane; k < nc4; k += 32) {
+        const CT* rr = rc_s + 4 * k;
+        if constexpr (C32) {
+          const float4 f = __ldg(reinterpret_cast<const float4*>(row) + k);
+          t = fmaf(f.x, rr[0], t);
+          t = fmaf(f.y, rr[1], t);
+          t = fmaf(f.z, rr[2], t);
+          t = fmaf(f.w, rr[3], t);
+        } else {
+          const double2 f0 = __ldg(reinterpret_cast<const double2*>(row) + 2 * k);
+          const double2 f1 = __ldg(reinterpret_cast<const double2*>(row) + 2 * k + 1);
+          t = fma(f0.x, rr[0], t);
+          t = fma(f0.y, rr[1], t);
+          t = fma(f1.x, rr[2], t);
+          t = fma(f1.y, rr[3], t);
+        }
+      }
+      if constexpr (C32) t = warp_sumf(t);
+      else t = warp_sum(t);
+      if (lane == 0) yc_s[g] = t;
+    }
+    __syncthreads();
+    for (int l = tid; l < nr; l += T) {
+      const double v = fma(dv[l], r[l], (double)yc_s[ag[l]]);
+      u[l] = v;
+      if (a.smem_vec) a.u[c0 + l] = v;
+    }
   };
 
   // ---- initial guess: the previous correction scaled by its Galerkin
   // factor theta = (x_prev . b) / (x_prev . A x_prev) (zero on first use);
   // successive synthetic corrections share their slowly decaying shape
-  double xb_l = 0.0, xax_l = 0.0, bb_l = 0.0;
-  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-    const double b = a.b[a.perm[c]];
-    const double xp = a.x[c];
-    const double q = spmv(a.x, c);
-    a.r[c] = b;
-    a.Ap[c] = q;   // A x_prev, scaled below
-    xb_l += xp * b;
-    xax_l += xp * q;
-    bb_l += b * b;
+  double v3[3] = {0.0, 0.0, 0.0}, t3[3];
+  for (int l = tid; l < nr; l += T) {
+    const double b = a.b[a.perm[c0 + l]];
+    const double qx = spmv(a.x, l);
+    r[l] = b;
+    s[l] = qx;   // A x_prev, scaled below
+    v3[0] = fma(x[l], b, v3[0]);
+    v3[1] = fma(x[l], qx, v3[1]);
+    v3[2] = fma(b, b, v3[2]);
   }
-  double s = block_sum(xb_l);
-  if (threadIdx.x == 0) a.partial[0 * nb + blockIdx.x] = s;
-  s = block_sum(xax_l);
-  if (threadIdx.x == 0) a.partial[1 * nb + blockIdx.x] = s;
-  s = block_sum(bb_l);
-  if (threadIdx.x == 0) a.partial[3 * nb + blockIdx.x] = s;
-  if (grid_sync(a.bar, a.err, nb)) return;
-  const double xb = grid_total(a.partial, 0);
-  const double xax = grid_total(a.partial, 1);
-  const double bb = grid_total(a.partial, 3);
-  const double theta = (xax > 0.0 && isfinite(xb / xax)) ? xb / xax : 0.0;
-  double rr0_l = 0.0;
-  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-    const double r = a.r[c] - theta * a.Ap[c];
-    a.r[c] = r;
-    a.x[c] = theta * a.x[c];
-    rr0_l += r * r;
+  if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err)) return;
+  if (tid == 0) {
+    const double th = t3[1] > 0.0 ? t3[0] / t3[1] : 0.0;
+    s_scal[0] = isfinite(th) ? th : 0.0;
   }
   __syncthreads();
-  restrict_r();
-  s = block_sum(rr0_l);
-  if (threadIdx.x == 0) a.partial[4 * nb + blockIdx.x] = s;   // own slot: 0-3 may still be read
-  if (grid_sync(a.bar, a.err, nb)) return;
-  const double rr0 = grid_total(a.partial, 4);
+  const double bb = t3[2];
+  const double theta = s_scal[0];
+  double v1[1] = {0.0}, t1[1];
+  for (int l = tid; l < nr; l += T) {
+    const double rv = fma(-theta, s[l], r[l]);
+    r[l] = rv;
+    fr_s[l] = (CT)rv;
+    x[l] = theta * x[l];
+    v1[0] = fma(rv, rv, v1[0]);
+  }
+  __syncthreads();
+  restrict_own(rcx);
+  if (grid_reduce<1>(v1, t1, red_s, a.slots, a.bar, gen++, a.err)) return;
+  double rho = t1[0];
+  const double stop = a.tol * a.tol * bb;
   int it = 0;
-  double rr = rr0;
-  if (bb > 0.0 && rr0 > a.tol * a.tol * bb) {
-    coarse_rows();
+  if (bb > 0.0 && rho > stop) {
+    for (int k = tid; k < Nc; k += T) rc_s[k] = __ldcg(rcx + k);
     __syncthreads();
-    double rz_l = 0.0;
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-      const double z = a.dinv[c] * a.r[c] + a.yc[a.agg[c]];
-      a.z[c] = z;
-      a.p[c] = z;
-      rz_l += a.r[c] * z;
-    }
-    s = block_sum(rz_l);
-    if (threadIdx.x == 0) a.partial[2 * nb + blockIdx.x] = s;
-    if (grid_sync(a.bar, a.err, nb)) return;
-    double rz = grid_total(a.partial, 2);
-    double beta = 0.0;
-    for (it = 0; it < a.max_it;) {
-      // p = z + beta p ; Ap = A z + beta Ap
-      double pap_l = 0.0;
-      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        const double az = spmv(a.z, c);
-        const double p = it == 0 ? a.z[c] : a.z[c] + beta * a.p[c];
-        const double ap = it == 0 ? az : az + beta * a.Ap[c];
-        a.p[c] = p;
-        a.Ap[c] = ap;
-        pap_l += p * ap;
+    precondition();
+    if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err)) return;
+    // s_scal[2], s_scal[3]: 1/gamma and 1/alpha of the previous step (thread 0)
+    while (true) {
+      // -- w = A u, (r,u), (w,u), (r,r), aggregate sums of w
+      if (it > 0) {
+        for (int k = tid; k < Nc; k += T) {
+          rc_s[k] = __ldcg(rcx + k);
+          sc_s[k] = __ldcg(scx + k);
+        }
       }
-      s = block_sum(pap_l);
-      if (threadIdx.x == 0) a.partial[0 * nb + blockIdx.x] = s;
-      if (grid_sync(a.bar, a.err, nb)) return;
-      const double alpha = rz / grid_total(a.partial, 0);
-      double rr_l = 0.0;
-      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        a.x[c] += alpha * a.p[c];
-        const double r = a.r[c] - alpha * a.Ap[c];
-        a.r[c] = r;
-        rr_l += r * r;
+      v3[0] = v3[1] = v3[2] = 0.0;
+      for (int l = tid; l < nr; l += T) {
+        const double wv = spmv(a.u, l);
+        w[l] = wv;
+        fr_s[l] = (CT)wv;
+        const double rv = r[l], uv = u[l];
+        v3[0] = fma(rv, uv, v3[0]);
+        v3[1] = fma(wv, uv, v3[1]);
+        v3[2] = fma(rv, rv, v3[2]);
       }
       __syncthreads();
-      restrict_r();
-      s = block_sum(rr_l);
-      if (threadIdx.x == 0) a.partial[1 * nb + blockIdx.x] = s;
-      if (grid_sync(a.bar, a.err, nb)) return;
-      rr = grid_total(a.partial, 1);
+      restrict_own(rw);
+      if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err)) return;
+      const double gamma = t3[0], delta = t3[1];
+      rho = t3[2];
+      if (!(rho > stop) || it >= a.max_it) break;
+      if (tid == 0) {
+        const double beta = it == 0 ? 0.0 : gamma * s_scal[2];
+        s_scal[0] = beta;
+        s_scal[1] = gamma / (it == 0 ? delta : delta - beta * gamma * s_scal[3]);
+      }
+      __syncthreads();
+      const double beta = s_scal[0], alpha = s_scal[1];
+      // -- p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s
+      for (int l = tid; l < nr; l += T) {
+        const double pv = it == 0 ? u[l] : fma(beta, p[l], u[l]);
+        const double sv = it == 0 ? w[l] : fma(beta, s[l], w[l]);
+        p[l] = pv;
+        s[l] = sv;
+        x[l] = fma(alpha, pv, x[l]);
+        r[l] = fma(-alpha, sv, r[l]);
+      }
+      // the same recurrence on the aggregate sums, in every block
+      const CT cb = (CT)beta, ca = (CT)alpha;
+      for (int k = tid; k < Nc; k += T) {
+        const CT rwk = __ldcg(rw + k);
+        const CT sc = it == 0 ? rwk : rwk + cb * sc_s[k];
+        sc_s[k] = sc;
+        rc_s[k] -= ca * sc;
+      }
+      __syncthreads();
+      // exact aggregate sums of r and s for the next step
+      for (int l = tid; l < nr; l += T) fr_s[l] = (CT)r[l];
+      __syncthreads();
+      restrict_own(rcx);
+      __syncthreads();
+      for (int l = tid; l < nr; l += T) fr_s[l] = (CT)s[l];
+      __syncthreads();
+      restrict_own(scx);
+      precondition();
+      if (tid == 0) {
+        s_scal[2] = gamma;   // inverted by thread 0 inside the barrier below
+        s_scal[3] = alpha;
+      }
       ++it;
-      if (!(rr > a.tol * a.tol * bb)) break;
-      coarse_rows();
-      __syncthreads();
-      double rz_n = 0.0;
-      for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        const double z = a.dinv[c] * a.r[c] + a.yc[a.agg[c]];
-        a.z[c] = z;
-        rz_n += a.r[c] * z;
-      }
-      s = block_sum(rz_n);
-      if (threadIdx.x == 0) a.partial[2 * nb + blockIdx.x] = s;
-      if (grid_sync(a.bar, a.err, nb)) return;
-      const double rzn = grid_total(a.partial, 2);
-      beta = rzn / rz;
-      rz = rzn;
+      if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err, s_scal + 2, 2)) return;
     }
   }
-  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) a.x_out[a.perm[c]] = a.x[c];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  // every read of the previous correction happened before the first barrier
+  for (int l = tid; l < nr; l += T) {
+    a.x_out[a.perm[c0 + l]] = x[l];
+    a.x[c0 + l] = x[l];
+  }
+  if (blockIdx.x == 0 && tid == 0) {
     *a.it_out += it;
-    *a.res_out = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    *a.res_out = bb > 0.0 ? sqrt(rho / bb) : 0.0;
   }
 }
 
-cudaError_t launch_cg(const CGArgs& a, int grid, cudaStream_t st) {
+cudaError_t launch_cg(const CGArgs& a, bool coarse32, int grid, int threads, size_t smem, cudaStream_t st) {
+  if (grid < 1 || grid > 256 || threads < 128 || threads > kCGThreads || threads % 32 != 0)
+    return cudaErrorInvalidConfiguration;
+  if (a.Nc > kMaxCoarse || a.W > 8) return cudaErrorInvalidValue;
+  auto kern = coarse32 ? cg_kernel<true> : cg_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kCGThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cg_kernel, a);
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 // ============================================================================ wall heat

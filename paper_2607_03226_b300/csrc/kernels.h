@@ -50,7 +50,7 @@ template <typename R>
 cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem,
                          cudaStream_t st);
 template <typename R>
-cudaError_t launch_gather_tq(R* tqp, const void* rec, int rec_bytes, const R* srcTQ, int64_t n, cudaStream_t st);
+cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st);
 
 template <typename R>
 void launch_init_exports(R* exp, const int32_t* exp_cell, const double* Tdev, const double* CoW, int Bp, int G,
@@ -102,40 +102,85 @@ void launch_update(const UpdateArgs<R>& a, cudaStream_t st);
 // aggregates [blk_agg[k], blk_agg[k+1]) and their cells
 // [blk_cell[k], blk_cell[k+1]).  M^{-1} r = D^{-1} r + P Ac^{-1} P^T r with P
 // the piecewise-constant aggregate prolongation and Ac^{-1} dense.
+
+// One block's published partial sums, one 64-byte line per block,
+// double-buffered by barrier parity: a block can only write the sums of
+// barrier k+2 after every block has arrived at barrier k+1, i.e. has finished
+// reading the sums of barrier k.
+struct alignas(64) CGSlot {
+  double v[2][3];
+  double pad[2];
+};
+
 struct CGArgs {
-  int N, Nc;
-  const int32_t* rp;
-  const int32_t* col;
-  const double* val;
-  const double* dinv;
+  int N, Nc, W;                  // rows, aggregates, ELL width (off-diagonals per row, <= 8)
+  const int32_t* ell_col;        // [W][N] off-diagonal columns (padding: own row)
+  const double* ell_val;         // [W][N] off-diagonal values (padding: 0)
+  const double* diag;            // [N]
+  const double* dinv;            // [N]
   const int32_t* perm;           // aggregate-order row -> internal cell
-  const int32_t* agg;            // aggregate of each row
+  const int32_t* agg_rel;        // aggregate of each row minus its block's first aggregate
   const int32_t* agg_cell;       // [Nc+1] first row of each aggregate
   const int32_t* blk_cell;       // [grid+1]
   const int32_t* blk_agg;        // [grid+1]
-  const float* Ainv;             // [Nc * Nc4*4], rows padded with zeros to Nc4*4
+  const float* Ainv32;           // [Nc * Nc4*4] coarse inverse, rows padded with zeros to Nc4*4
+  const double* Ainv64;          // the same in FP64
   int Nc4;                       // ceil(Nc / 4)
+  int max_rows, max_na;          // largest block's rows / aggregates
+  int smem_vec, smem_ell;        // own-row vectors / ELL rows held in shared memory
   const double* b;               // right-hand side, internal order
   double* x_out;                 // solution, internal order
-  double* x;                     // work vectors in aggregate order
+  double* x;                     // [N] previous correction in, new correction out (aggregate order)
+  double* u;                     // [N] M^{-1} r (read by the neighbours' products)
+  double* x_work;                // [N] work vectors when not in shared memory
   double* r;
-  double* z;
   double* p;
-  double* Ap;
-  double* rc;                    // [Nc]
-  double* yc;                    // [Nc]
-  double* partial;               // [5*grid]
-  unsigned* bar;                 // [2] count, generation
+  double* s;
+  double* w;
+  void* rw;                      // [Nc] aggregate sums of w (coarse precision)
+  void* rcx;                     // [Nc] aggregate sums of r
+  void* scx;                     // [Nc] aggregate sums of s
+  CGSlot* slots;                 // [grid]
+  unsigned long long* bar;       // barrier counter (only grows)
   int32_t* err;
   double tol;
   int max_it;
   int32_t* it_out;
   double* res_out;
 };
-// persistent cooperative PCG; returns cudaError of the launch
-cudaError_t launch_cg(const CGArgs& a, int grid, cudaStream_t st);
-constexpr int kCGThreads = 1024;
-constexpr int kMaxCoarse = 2048;   // aggregates of the coarse space (rc staged in shared memory)
+// persistent cooperative PCG; coarse32 selects the FP32 coarse preconditioner
+cudaError_t launch_cg(const CGArgs& a, bool coarse32, int grid, int threads, size_t smem, cudaStream_t st);
+
+// dynamic shared memory of the CG kernel (byte offsets, 16-byte aligned)
+struct CgSmem {
+  size_t red, rc, sc, yc, fr, ab, vec, ell, total;
+};
+NBTE_HD constexpr size_t cg_align16(size_t x) { return (x + 15) / 16 * 16; }
+NBTE_HD inline CgSmem cg_smem_layout(int nc4, int max_rows, int max_na, int W, int threads, int vec, int ell,
+                                     int coarse_bytes) {
+  CgSmem L{};
+  size_t o = 0;
+  L.red = o;
+  o = cg_align16(o + (size_t)3 * threads * 8);
+  L.rc = o;
+  o = cg_align16(o + (size_t)4 * nc4 * coarse_bytes);
+  L.sc = o;
+  o = cg_align16(o + (size_t)4 * nc4 * coarse_bytes);
+  L.yc = o;
+  o = cg_align16(o + (size_t)max_na * coarse_bytes);
+  L.fr = o;
+  o = cg_align16(o + (size_t)max_rows * coarse_bytes);
+  L.ab = o;
+  o = cg_align16(o + (size_t)(max_na + 1) * 4);
+  L.vec = o;
+  if (vec) o = cg_align16(o + (size_t)7 * max_rows * 8 + (size_t)max_rows * 4);
+  L.ell = o;
+  if (ell) o = cg_align16(o + (size_t)W * max_rows * 8 + (size_t)max_rows * 8 + (size_t)W * max_rows * 4);
+  L.total = o;
+  return L;
+}
+constexpr int kCGThreads = 512;
+constexpr int kMaxCoarse = 2048;   // aggregates of the coarse space (staged in shared memory)
 
 template <typename R>
 struct WallHeatArgs {

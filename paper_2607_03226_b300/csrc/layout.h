@@ -21,20 +21,22 @@ NBTE_HD inline size_t io_index(int64_t x, int b, int64_t n, int G, int Gpad) {
   return ((size_t)g * (size_t)n + (size_t)x) * (size_t)Gpad + (size_t)(b - g * G);
 }
 
-NBTE_HD inline int padded_group(int G, int elem_bytes) {
+NBTE_HD constexpr int padded_group(int G, int elem_bytes) {
   const int per16 = 16 / elem_bytes;
   return ((G + per16 - 1) / per16) * per16;
 }
 
 // Packed position record (one per direction and position, level order):
 //   int32 cell, int32 slot, int32 export, [pad], R G, int32 ref[K], [pad], R coef[K]
-// padded to a multiple of 16 bytes.
+// padded to an ODD multiple of 16 bytes: a warp reads records of consecutive
+// positions with 16-byte shared-memory loads, eight threads per wavefront,
+// and an odd stride (in 16-byte units) puts those eight in distinct banks.
 struct RecLayout {
   int size, off_G, off_ref, off_coef;
 };
 
-NBTE_HD inline RecLayout rec_layout(int elem_bytes, int K) {
-  RecLayout L;
+NBTE_HD constexpr RecLayout rec_layout(int elem_bytes, int K) {
+  RecLayout L{0, 0, 0, 0};
   int off = 12;
   off = (off + elem_bytes - 1) / elem_bytes * elem_bytes;
   L.off_G = off;
@@ -44,7 +46,9 @@ NBTE_HD inline RecLayout rec_layout(int elem_bytes, int K) {
   off = (off + elem_bytes - 1) / elem_bytes * elem_bytes;
   L.off_coef = off;
   off += elem_bytes * K;
-  L.size = (off + 15) / 16 * 16;
+  int n16 = (off + 15) / 16;
+  if (n16 % 2 == 0) ++n16;
+  L.size = 16 * n16;
   return L;
 }
 

@@ -122,8 +122,43 @@ __device__ __forceinline__ void store_vals(R* p, const R (&v)[BPT]) {
   }
 }
 
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// FP32: the hardware approximate reciprocal (relative error below 2^-22,
+// under the FP32 sweep's own rounding); FP64: a correctly rounded division
+__device__ __forceinline__ float recip(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// word idx (4-byte units) of a record held in registers; idx is a
+// compile-time constant after unrolling, so this folds to a register move
+template <int NQ>
+__device__ __forceinline__ uint32_t rec_word(const uint4 (&w)[NQ], int idx) {
+  const uint4 v = w[idx >> 2];
+  switch (idx & 3) {
+    case 0: return v.x;
+    case 1: return v.y;
+    case 2: return v.z;
+    default: return v.w;
+  }
+}
+template <typename R>
+struct RecField;
+template <>
+struct RecField<float> {
+  template <int NQ>
+  __device__ __forceinline__ static float get(const uint4 (&w)[NQ], int byte_off) {
+    return __uint_as_float(rec_word(w, byte_off / 4));
+  }
+};
+template <>
+struct RecField<double> {
+  template <int NQ>
+  __device__ __forceinline__ static double get(const uint4 (&w)[NQ], int byte_off) {
+    return __hiloint2double((int)rec_word(w, byte_off / 4 + 1), (int)rec_word(w, byte_off / 4));
+  }
+};
 
 }  // namespace
 
@@ -136,7 +171,9 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
   Chunk* meta = reinterpret_cast<Chunk*>(smem + 16 * NS);
   R* ring = reinterpret_cast<R*>(smem + a.off_ring);
   unsigned char* stages = smem + a.off_stage;
-  const RecLayout RL = rec_layout((int)sizeof(R), K);
+  constexpr RecLayout RL = rec_layout((int)sizeof(R), K);
+  constexpr int NQ = RL.size / 16;
+  constexpr int GP = padded_group(G, (int)sizeof(R));   // row length of the import/export tables
 
   const int item = blockIdx.x;
   const int i = a.item_dir[item];
@@ -230,7 +267,7 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
     wt[b] = (R)(wi * (double)itau[b]);
   }
   R* part = a.part + (int64_t)item * a.N;
-  R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * a.Gpad;
+  R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * GP;
   consumer_barrier(ncons);
 
   for (int c = 0; c < nch; ++c) {
@@ -243,16 +280,21 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
     const unsigned char* st = stages + (size_t)s * a.stage_bytes;
     const int per16 = 16 / (int)(2 * sizeof(R));
     const int tq_shift = (int)((dbase + m.pos) % per16);
-    const R* tqs = reinterpret_cast<const R*>(st + a.off_tq) + 2 * tq_shift;
+    using R2 = typename Vec2<R>::T;
+    const R2* tqs = reinterpret_cast<const R2*>(st + a.off_tq) + tq_shift;
     const R* imps = reinterpret_cast<const R*>(st + a.off_imp);
+    const int imp0 = m.imp;
     for (int j = ct; j < m.len; j += ncons) {
-      const unsigned char* rb = st + (size_t)j * RL.size;
-      const int cell = *reinterpret_cast<const int*>(rb);
-      const int slot = *reinterpret_cast<const int*>(rb + 4);
-      const int ex = *reinterpret_cast<const int*>(rb + 8);
-      const R Gc = *reinterpret_cast<const R*>(rb + RL.off_G);
-      const R T = tqs[2 * j];
-      const R Q = tqs[2 * j + 1];
+      uint4 w[NQ];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) w[q] = reinterpret_cast<const uint4*>(st)[j * NQ + q];
+      const int cell = (int)rec_word(w, 0);
+      const int slot = (int)rec_word(w, 1);
+      const int ex = (int)rec_word(w, 2);
+      const R Gc = RecField<R>::get(w, RL.off_G);
+      const R2 tq = tqs[j];
+      const R T = tq.x;
+      const R Q = tq.y;
       R e0[G], up[G];
 #pragma unroll
       for (int b = 0; b < G; ++b) {
@@ -261,9 +303,9 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
       }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const int ref = reinterpret_cast<const int*>(rb + RL.off_ref)[k];
-        const R cf = reinterpret_cast<const R*>(rb + RL.off_coef)[k];
-        const R* src = ref >= 0 ? ring + ref * G : imps + (size_t)((-1 - ref) - m.imp) * a.Gpad;
+        const int ref = (int)rec_word(w, RL.off_ref / 4 + k);
+        const R cf = RecField<R>::get(w, RL.off_coef + k * (int)sizeof(R));
+        const R* src = ref >= 0 ? ring + ref * G : imps + ((-1 - ref) - imp0) * GP;
         R eu[G];
         load_vals<R, G>(src, eu);
 #pragma unroll
@@ -278,7 +320,7 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
         nl += wt[b] * phi;
       }
       if (slot >= 0) store_vals<R, G>(ring + slot * G, e);
-      if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * a.Gpad, e);
+      if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * GP, e);
       part[cell] = nl;
       if (a.full) {
         R es = R(0), evs = R(0);
@@ -340,25 +382,23 @@ cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int t
 // (T', Qdot) of every position's cell, in each direction's level order, so
 // the sweep's producer can bulk-copy them with the position records
 template <typename R>
-__global__ void gather_tq_kernel(R* tqp, const int32_t* rec_cells, int rec_stride_words, const R* srcTQ, int64_t n) {
+__global__ void gather_tq_kernel(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n) {
+  using R2 = typename Vec2<R>::T;
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= n) return;
-  const int cell = rec_cells[q * rec_stride_words];
-  tqp[2 * q] = srcTQ[2 * cell];
-  tqp[2 * q + 1] = srcTQ[2 * cell + 1];
+  reinterpret_cast<R2*>(tqp)[q] = __ldg(reinterpret_cast<const R2*>(srcTQ) + __ldcs(pos_cell + q));
 }
 
 template <typename R>
-cudaError_t launch_gather_tq(R* tqp, const void* rec, int rec_bytes, const R* srcTQ, int64_t n, cudaStream_t st) {
+cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  gather_tq_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tqp, static_cast<const int32_t*>(rec),
-                                                                  rec_bytes / 4, srcTQ, n);
+  gather_tq_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tqp, pos_cell, srcTQ, n);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, int, int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, int, int, size_t, cudaStream_t);
-template cudaError_t launch_gather_tq<float>(float*, const void*, int, const float*, int64_t, cudaStream_t);
-template cudaError_t launch_gather_tq<double>(double*, const void*, int, const double*, int64_t, cudaStream_t);
+template cudaError_t launch_gather_tq<float>(float*, const int32_t*, const float*, int64_t, cudaStream_t);
+template cudaError_t launch_gather_tq<double>(double*, const int32_t*, const double*, int64_t, cudaStream_t);
 
 }  // namespace nbte
