@@ -113,6 +113,33 @@ def sweep_algorithmic_bytes(st, n_cells, n_dirs, prec_bytes, Bp):
             + (st["exports"] + st["imports"]) * Bp * prec_bytes)
 
 
+def _sweep_traffic(G, threads):
+    """DRAM bytes per sweep launch from the committed ncu summary, if that
+    capture was taken with the current sweep sources and this launch layout
+    (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_finfet2d_fp32.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("|", "#", " ")):
+            k, _, v = line.partition(":")
+            fields[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "layout.h", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2607_03226_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if fields.get("sweep_source_digest") != h.hexdigest()[:16]:
+        return None
+    if fields.get("layout") != f"band_group={G} cta_threads={threads}":
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -199,7 +226,9 @@ def run_gpu(args):
         "gpu_launches": int(info["kernel_launches"]),
         "cg_iterations_per_step": info["cg_iterations"] / max(1, args.steps),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": (_sweep_traffic(G, stats["cta_threads"])
+                                 if args.precision == "fp32" else None),
                      "kernel": "sweep_kernel", "sweep_ms": sweep_ms,
                      "algorithmic_bytes_per_launch": bytes_launch},
         "clocks": clocks,

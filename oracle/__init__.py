@@ -24,10 +24,13 @@ appearance in Sec. II "Methods"):
 * Walls (thermalizing / diffuse / specular / partially specular) with the
   reflected values taken from the previous iteration.
 
-Readings of points the paper leaves open (first-order upwind, lagged wall
-coupling, the DSA form of the synthetic update, the convergence measure, the
-TPFA Laplacian) are listed with their justification in the repository's design
-notes; each function below names the one it uses.
+Points the paper leaves open are read as follows, and each function below
+names the reading it uses: first-order step upwind; wall values lagged one
+outer iteration; the synthetic update in its DSA form (the diffusion term at
+the kinetic temperature, Eqs. (8)-(10)), with the correction's equilibrium
+part added to the lagged wall values; a TPFA cell Laplacian with the upwind
+scheme's numerical diffusivity added to kappa; convergence measured as
+max|dT'| / max|T'|.
 
 Parity status: the transport/moment/wall arithmetic is pinned by the tests in
 ``tests/test_oracle_pins.py`` (closed forms, invariants, brute-force dense
