@@ -150,8 +150,12 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  *            feasible layout once (a few sweeps on scratch state) and keeps
  *            the fastest for this plan, band table and precision.  None of
  *            them changes results beyond rounding order; an infeasible
- *            choice (its ring or stages exceed shared memory) is
- *            NBTE_ERR_ARG.
+ *            choice (two copy stages exceed shared memory) is NBTE_ERR_ARG.
+ * ring:      where the sweep keeps the outgoing values of a direction's live
+ *            cells: 0 = shared memory when it fits, else global memory;
+ *            1 = shared memory (NBTE_ERR_ARG if it does not fit); 2 = global
+ *            memory (one region per work item, L2-resident while it runs).
+ *            Results are identical either way.
  * cg_tol, cg_max_iter: relative residual and cap of the conjugate-gradient
  *            solve of the synthetic correction (0 = defaults 1e-3, 5000); the
  *            correction only changes the rate of convergence, not the limit.
@@ -183,6 +187,7 @@ typedef struct {
   int32_t skip_outputs;
   int32_t profile;
   int32_t cta_threads;
+  int32_t ring;
 } nbte_solve_opts;
 
 /* Filled on return from nbte_solve_steady (also on NOT_CONVERGED):
@@ -233,7 +238,8 @@ int nbte_get_wall_heat(const nbte_solver* solver, int32_t tag, double* out);
 /* Planner statistics of the current quadrature/mesh (for tuning and tests):
  * stats[0] total levels over all directions, [1] max levels of one
  * direction, [2] max ring slots of one direction, [3] lagged faces,
- * [4] work items, [5] bands per item, [6] threads per cell, [7] device bytes
+ * [4] work items, [5] bands per item, [6] value ring (1 shared memory,
+ * 2 global memory), [7] device bytes
  * held by the solver, [8] inflow entries per cell record, [9] exported
  * (direction, cell) values, [10] imported wall/lag values, [11] threads per
  * sweep CTA.  With band_group = cta_threads = 0 and bands, quadrature and

@@ -128,7 +128,8 @@ struct nbte_solver {
   int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0;
   size_t smem = 0;
   double W = 0, beta = 0, Ctot = 0;
-  DBuf rec, pos_cell, chunks, chunk_off, tqp;
+  DBuf rec, pos_cell, chunks, chunk_off, tqp, gring;
+  int64_t gring_stride = 0;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
   DBuf cg_r, cg_u, cg_w, cg_p, cg_s, cg_xw, cg_slots, cg_bar, cg_err, cg_it, cg_res;
@@ -176,7 +177,7 @@ struct DeviceGuard {
 };
 
 size_t device_bytes(const nbte_solver* S) {
-  const DBuf* all[] = {&S->rec, &S->pos_cell, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
+  const DBuf* all[] = {&S->rec, &S->pos_cell, &S->gring, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
                        &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
                        &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
@@ -351,7 +352,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   // the autotuner's choice stands in for "planner's choice" (0, 0)
   int want_G = o.band_group, want_threads = o.cta_threads;
   const Tuned& tu = S->tuned[prec];
-  if (want_G == 0 && want_threads == 0 && tu.valid && tu.key == tune_key(S)) {
+  if (want_G == 0 && want_threads == 0 && o.ring == 0 && tu.valid && tu.key == tune_key(S)) {
     want_G = tu.G;
     want_threads = tu.cap + 32;
   }
@@ -374,54 +375,62 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
     off_imp = rec + tq;
     return rec + tq + imp;
   };
+  // the value ring: in shared memory when it fits beside two copy stages,
+  // else one global-memory region per CTA
   auto ring_of = [&](int Gv) { return (int)(((size_t)(S->max_slots + 1) * Gv * sz + 15) / 16 * 16); };
   const int head = 32 * 8;   // up to 8 stages: full + empty barriers and chunk headers
-  auto fits = [&](int Gv, int ns) {
+  auto smem_ring = [&](int Gv) {
     int a, b;
-    return (int64_t)head + ring_of(Gv) + (int64_t)ns * stage_of(Gv, a, b) <= kSweepSmemMax;
+    return (int64_t)head + ring_of(Gv) + 2 * (int64_t)stage_of(Gv, a, b) <= kSweepSmemMax;
   };
+  auto ring_smem_bytes = [&](int Gv) { return smem_ring(Gv) ? ring_of(Gv) : 0; };
   const int maxG = prec ? 8 : 4;
   int G = want_G;
   if (G > 0) {
     if (!(G == 1 || G == 2 || G == 4 || G == 8) || G > maxG)
       return fail(NBTE_ERR_ARG, prec ? "band_group must be 1, 2, 4 or 8" : "band_group must be 1, 2 or 4 in FP64");
-    if (!fits(G, 2)) return fail(NBTE_ERR_ARG, "band_group too large for shared memory on this mesh");
   } else {
     G = 0;
     double best = 1e300;
     for (int c : {8, 4, 2, 1}) {
-      if (c > maxG || !fits(c, 2)) continue;
+      if (c > maxG) continue;
       const int ng = (S->B + c - 1) / c;
       const double waste = (double)(ng * c - S->B) / S->B;
-      // prefer wide groups unless they pad more than 12.5%
-      const double score = waste <= 0.125 ? -c : 1000.0 * waste - c;
+      // prefer wide groups with a shared-memory ring, unless they pad more than 12.5%
+      const double score = (waste <= 0.125 ? -c : 1000.0 * waste - c) + (smem_ring(c) ? 0.0 : 100.0);
       if (score < best) { best = score; G = c; }
     }
-    if (G == 0)
-      return fail(NBTE_ERR_ARG, "one direction's live cells exceed shared memory (" + std::to_string(S->max_slots) +
-                                    " ring slots); use FP32 or a smaller mesh");
   }
-  // stages: 2..8, as many as fit while every work item can be resident at
-  // once (the sweep of one item is a long dependent chain of levels, so a
-  // second wave would double the time); if even 2 stages do not allow that,
-  // use the most that fit
+  if (o.ring == 1 && !smem_ring(G))
+    return fail(NBTE_ERR_ARG, "the value ring does not fit in shared memory (" + std::to_string(S->max_slots) +
+                                  " live cells in one direction)");
+  const bool gr = o.ring == 2 || !smem_ring(G);
+  {
+    int a, b;
+    if ((int64_t)head + 2 * (int64_t)stage_of(G, a, b) > kSweepSmemMax)
+      return fail(NBTE_ERR_ARG, "cta_threads too large for shared memory with this band group");
+  }
+  // stages: 2..8.  The sweep of one item is a long dependent chain of
+  // levels, so co-resident CTAs are what hides its latency: aim for every
+  // work item resident at once, else for as many CTAs per SM as still get
+  // three stages each, then give each CTA as many stages as that allows
   int off_tq = 0, off_imp = 0;
   const int stage = stage_of(G, off_tq, off_imp);
   const int ng = (S->B + G - 1) / G;
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device);
-  const int per_sm = std::max(1, (S->D * ng + nsm - 1) / nsm);
-  const int64_t budget = (int64_t)(228 * 1024) / per_sm - 1024;
+  const int64_t ringB = ring_smem_bytes(G);
+  auto total = [&](int ns) { return (int64_t)head + ringB + (int64_t)ns * stage; };
+  auto budget = [&](int t) { return (int64_t)(228 * 1024) / t - 1024; };
+  int per_sm = std::max(1, (S->D * ng + nsm - 1) / nsm);
+  while (per_sm > 1 && total(3) > budget(per_sm)) --per_sm;
   int ns = 8;
-  while (ns > 2 && (int64_t)head + ring_of(G) + (int64_t)ns * stage > budget) --ns;
-  if ((int64_t)head + ring_of(G) + (int64_t)ns * stage > budget) {
-    ns = 8;
-    while (ns > 2 && !fits(G, ns)) --ns;
-  }
+  while (ns > 2 && total(ns) > std::min<int64_t>(budget(per_sm), kSweepSmemMax)) --ns;
   const int Bp = ng * G;
   const int threads = cap + 32;
   const std::string key = std::to_string(prec) + "/" + std::to_string(G) + "/" + std::to_string(cap) + "/" +
-                          std::to_string(S->version_bands) + "/" + std::to_string(S->plan_built);
+                          std::to_string(S->version_bands) + "/" + std::to_string(S->plan_built) + "/" +
+                          std::to_string(ns) + (gr ? "/global" : "/shared");
   if (key == S->layout_key) return NBTE_OK;
   DeviceGuard dg(S->device);
   drop_graph(S);
@@ -437,7 +446,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   S->off_tq = off_tq;
   S->off_imp = off_imp;
   S->off_ring = head;
-  S->off_stage = head + ring_of(G);
+  S->off_stage = head + (int)ringB;
+  S->gring_stride = gr ? ((int64_t)(S->max_slots + 1) * G + 3) / 4 * 4 : 0;
   S->smem = (size_t)S->off_stage + (size_t)ns * stage;
   const int64_t N = S->mesh->m.n_cells;
   // band constants, padded bands are inert (C = 0, v = 0, 1/tau = 1)
@@ -479,6 +489,11 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   NBTE_CK(S->srcTQ.alloc((size_t)2 * N * sz));
   NBTE_CK(S->srcTQ_fin.alloc((size_t)2 * N * sz));
   NBTE_CK(S->part.alloc((size_t)S->n_items * N * sz));
+  if (gr) {
+    NBTE_CK(S->gring.alloc((size_t)S->n_items * S->gring_stride * sz));
+  } else {
+    S->gring.release();
+  }
   NBTE_CK(S->T.alloc(N * 8));
   NBTE_CK(S->Tprev.alloc(N * 8));
   NBTE_CK(S->Tkin.alloc(N * 8));
@@ -695,6 +710,8 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.dir_w = S->dir_w.as<double>();
   a.dir_s = S->dir_s.as<double>();
   a.part = S->part.as<R>();
+  a.gring = S->gring.p ? S->gring.as<R>() : nullptr;
+  a.gring_stride = S->gring_stride;
   a.accE = S->accE.as<double>();
   a.accQ = S->accQ.as<double>();
   return a;
@@ -889,7 +906,7 @@ int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
 // (band group, chunk length) layout once per (mesh plan, band table,
 // precision) and keep the fastest.
 int autotune(nbte_solver* S, const nbte_solve_opts& o) {
-  if (o.band_group != 0 || o.cta_threads != 0) return NBTE_OK;
+  if (o.band_group != 0 || o.cta_threads != 0 || o.ring != 0) return NBTE_OK;
   Tuned& tu = S->tuned[o.precision];
   if (tu.valid && tu.key == tune_key(S)) return NBTE_OK;
   tu.valid = false;
@@ -1314,6 +1331,7 @@ static int check_opts(const nbte_solve_opts& o) {
   if (o.n_iter < 0) return fail(NBTE_ERR_ARG, "n_iter must be >= 0");
   if (o.n_iter == 0 && !(o.tol > 0 && std::isfinite(o.tol))) return fail(NBTE_ERR_ARG, "tol must be positive");
   if (o.n_iter == 0 && o.max_iter <= 0) return fail(NBTE_ERR_ARG, "max_iter must be positive");
+  if (o.ring < 0 || o.ring > 2) return fail(NBTE_ERR_ARG, "ring must be 0, 1 or 2");
   return NBTE_OK;
 }
 
@@ -1341,7 +1359,7 @@ int nbte_plan_stats(nbte_solver* S, const nbte_solve_opts* opts, int64_t stats[1
   stats[3] = S->lagged;
   stats[4] = S->n_items;
   stats[5] = S->G;
-  stats[6] = 1;   // threads per cell
+  stats[6] = S->gring_stride > 0 ? 2 : 1;
   stats[7] = (int64_t)device_bytes(S);
   stats[8] = S->K;
   stats[9] = S->n_exp;

@@ -40,6 +40,8 @@ struct SweepArgs {
   const R* band_aQ;              // C / (C_tot W)
   const double* dir_w;           // [D]
   const double* dir_s;           // [D*3]
+  R* gring;                      // global-memory value rings, or null for the shared-memory ring
+  int64_t gring_stride;          // elements per CTA's global ring
   R* part;                       // [n_items*N] collision-moment partials (of e - e0)
   double* accE;                  // [N]   (full)
   double* accQ;                  // [N*dim] (full)

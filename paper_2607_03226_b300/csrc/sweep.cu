@@ -15,7 +15,11 @@
 //    compute one position per thread from shared memory and the value ring,
 //    release the stage on its "empty" barrier, and meet on a named barrier
 //    only at the end of a level (so the next level sees the ring writes).
-// A level's critical path is therefore shared-memory work only.  Every wait
+// The value ring holds the outgoing values of the direction's live cells
+// (slots assigned by the planner).  It lives in shared memory when it fits
+// (GR = false); otherwise (GR = true, large 3D meshes whose sweep front has
+// tens of thousands of live cells) in a per-CTA global-memory region, where
+// the concurrently running CTAs' live windows stay mostly in L2.  Every wait
 // is bounded: on timeout the error word is set, the producer waits (bounded)
 // for the copies it issued, and the CTA leaves.
 //
@@ -162,14 +166,14 @@ struct RecField<double> {
 
 }  // namespace
 
-template <typename R, int K, int G>
+template <typename R, int K, int G, bool GR>
 __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int NS = a.n_stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + NS;
   Chunk* meta = reinterpret_cast<Chunk*>(smem + 16 * NS);
-  R* ring = reinterpret_cast<R*>(smem + a.off_ring);
+  R* ring = GR ? a.gring + (size_t)blockIdx.x * (size_t)a.gring_stride : reinterpret_cast<R*>(smem + a.off_ring);
   unsigned char* stages = smem + a.off_stage;
   constexpr RecLayout RL = rec_layout((int)sizeof(R), K);
   constexpr int NQ = RL.size / 16;
@@ -340,43 +344,46 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
   }
 }
 
-template <typename R, int K>
+template <typename R, int K, int G, bool GR>
+static cudaError_t launch_one(const SweepArgs<R>& a, int n_items, int threads, size_t smem, cudaStream_t st) {
+  auto kern = sweep_kernel<R, K, G, GR>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_items, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int K, bool GR>
 static cudaError_t launch_k(const SweepArgs<R>& a, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
   switch (G) {
-#define NBTE_G(Gv)                                                                                      \
-  case Gv: {                                                                                            \
-    auto kern = sweep_kernel<R, K, Gv>;                                                                 \
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    if (e != cudaSuccess) return e;                                                                     \
-    kern<<<n_items, threads, smem, st>>>(a);                                                            \
-    return cudaGetLastError();                                                                          \
-  }
-    NBTE_G(1) NBTE_G(2) NBTE_G(4)
-#undef NBTE_G
+    case 1: return launch_one<R, K, 1, GR>(a, n_items, threads, smem, st);
+    case 2: return launch_one<R, K, 2, GR>(a, n_items, threads, smem, st);
+    case 4: return launch_one<R, K, 4, GR>(a, n_items, threads, smem, st);
     case 8:
-      if constexpr (sizeof(R) == 4) {
-        auto kern = sweep_kernel<R, K, 8>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<n_items, threads, smem, st>>>(a);
-        return cudaGetLastError();
-      }
+      if constexpr (sizeof(R) == 4) return launch_one<R, K, 8, GR>(a, n_items, threads, smem, st);
       return cudaErrorInvalidConfiguration;
     default:
       return cudaErrorInvalidConfiguration;
   }
 }
 
-template <typename R>
-cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
+template <typename R, bool GR>
+static cudaError_t launch_gr(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem,
+                             cudaStream_t st) {
   switch (K) {
-    case 1: return launch_k<R, 1>(a, G, n_items, threads, smem, st);
-    case 2: return launch_k<R, 2>(a, G, n_items, threads, smem, st);
-    case 3: return launch_k<R, 3>(a, G, n_items, threads, smem, st);
-    case 4: return launch_k<R, 4>(a, G, n_items, threads, smem, st);
-    case 5: return launch_k<R, 5>(a, G, n_items, threads, smem, st);
+    case 1: return launch_k<R, 1, GR>(a, G, n_items, threads, smem, st);
+    case 2: return launch_k<R, 2, GR>(a, G, n_items, threads, smem, st);
+    case 3: return launch_k<R, 3, GR>(a, G, n_items, threads, smem, st);
+    case 4: return launch_k<R, 4, GR>(a, G, n_items, threads, smem, st);
+    case 5: return launch_k<R, 5, GR>(a, G, n_items, threads, smem, st);
     default: return cudaErrorInvalidConfiguration;
   }
+}
+
+template <typename R>
+cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
+  return a.gring ? launch_gr<R, true>(a, K, G, n_items, threads, smem, st)
+                 : launch_gr<R, false>(a, K, G, n_items, threads, smem, st);
 }
 
 // (T', Qdot) of every position's cell, in each direction's level order, so

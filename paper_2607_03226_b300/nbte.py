@@ -50,7 +50,8 @@ class nbte_solve_opts(C.Structure):
                 ("max_iter", C.c_int32), ("n_iter", C.c_int32), ("T_init", C.POINTER(C.c_double)),
                 ("warm", C.c_int32), ("band_group", C.c_int32), ("threads_per_cell", C.c_int32),
                 ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("use_graph", C.c_int32),
-                ("skip_outputs", C.c_int32), ("profile", C.c_int32), ("cta_threads", C.c_int32)]
+                ("skip_outputs", C.c_int32), ("profile", C.c_int32), ("cta_threads", C.c_int32),
+                ("ring", C.c_int32)]
 
 
 class nbte_solve_info(C.Structure):
@@ -210,7 +211,7 @@ def nbte_default_opts():
 
 def make_opts(scheme="sequential", precision="fp64", tol=1e-10, max_iter=10000, n_iter=0, T_init=None,
               warm=False, band_group=0, threads_per_cell=0, cg_tol=0.0, cg_max_iter=0, use_graph=False,
-              skip_outputs=False, profile=False, cta_threads=0):
+              skip_outputs=False, profile=False, cta_threads=0, ring=0):
     o = nbte_default_opts()
     o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     o.precision = {"fp64": 0, "fp32": 1}[precision] if isinstance(precision, str) else int(precision)
@@ -218,6 +219,7 @@ def make_opts(scheme="sequential", precision="fp64", tol=1e-10, max_iter=10000, 
     o.warm, o.band_group, o.threads_per_cell = int(bool(warm)), int(band_group), int(threads_per_cell)
     o.cg_tol, o.cg_max_iter, o.use_graph = float(cg_tol), int(cg_max_iter), int(bool(use_graph))
     o.skip_outputs, o.profile, o.cta_threads = int(bool(skip_outputs)), int(bool(profile)), int(cta_threads)
+    o.ring = {"auto": 0, "shared": 1, "global": 2}[ring] if isinstance(ring, str) else int(ring)
     keep = None
     if T_init is not None:
         keep, o.T_init = _d(T_init)
@@ -254,7 +256,7 @@ def nbte_plan_stats(solver, opts=None):
     st = np.zeros(12, dtype=np.int64)
     _check(load().nbte_plan_stats(solver, C.byref(opts) if opts is not None else None, st.ctypes.data_as(_I64)))
     keys = ["total_levels", "max_levels", "max_slots", "lagged_faces", "items", "band_group",
-            "threads_per_cell", "device_bytes", "K", "exports", "imports", "cta_threads"]
+            "ring", "device_bytes", "K", "exports", "imports", "cta_threads"]
     return dict(zip(keys, (int(x) for x in st)))
 
 

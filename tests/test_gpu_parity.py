@@ -120,11 +120,12 @@ def test_square_full_size_golden(nbte_mod):
 
 
 @pytest.mark.parametrize("variant", [dict(band_group=1), dict(band_group=2, cta_threads=96),
-                                     dict(use_graph=True), dict(band_group=4, cta_threads=544, use_graph=True)])
+                                     dict(use_graph=True), dict(band_group=4, cta_threads=544, use_graph=True),
+                                     dict(ring="global"), dict(band_group=4, cta_threads=160, ring="global")])
 def test_launch_variants_identical(nbte_mod, variant):
-    """Band grouping, CTA size (chunk length of the copy pipeline) and graph
-    replay change only the launch shape: FP64 results are identical to the
-    default to rounding."""
+    """Band grouping, CTA size (chunk length of the copy pipeline), the value
+    ring's placement (shared or global memory) and graph replay change only
+    the launch shape: FP64 results are identical to the default to rounding."""
     p = CASES["fin2d_mixed"]()
     p.C, p.v, p.tau = (np.tile(x, 2)[:4] for x in (p.C, p.v, p.tau))
     s = nbte_mod.Solver(p)
