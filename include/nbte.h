@@ -234,6 +234,14 @@ int nbte_get_heat_flux(const nbte_solver* solver, double* out);
 /* Net outward heat flow through the walls of one tag after the last sweep
  * (W, or W/m in 2D): sum over its faces of sum_l sum_i w_i v_l (s_i.An) e~. */
 int nbte_get_wall_heat(const nbte_solver* solver, int32_t tag, double* out);
+/* The phonon energy density e'_{band,direction} of the last sweep, Eq. (4):
+ * out[n_cells] (J/m^3 per unit solid angle), as the deviation from the
+ * equilibrium at T_ref (e' = e - C T_ref / W), in the caller's cell order.
+ * Recomputed on the device by re-running the last sweep for the work item
+ * holding (direction, band), whose inputs are still resident; valid until
+ * the next solve or setter call.  NBTE_ERR_STATE without a previous solve,
+ * NBTE_ERR_ARG for an index out of range.                                  */
+int nbte_get_distribution(nbte_solver* solver, int32_t direction, int32_t band, double* out);
 
 /* Planner statistics of the current quadrature/mesh (for tuning and tests):
  * stats[0] total levels over all directions, [1] max levels of one

@@ -118,24 +118,33 @@ class OracleSolver:
             dist = np.sum((mirror[:, None, :] - self.s3[None, :, :]) ** 2, axis=2)
             self.R[rows] = np.argmin(dist, axis=1)[None, :]
 
-        # ---------------- per-direction unit advection operators K_i (Eq. (13))
-        self._K = []
-        self._bin = []
-        Vc = g.V[g.hf_cell]
-        interior = g.hf_nb >= 0
-        for i in range(self.D):
-            a = g.hf_An @ self.s[i]
-            out = a > 0
-            diag = np.bincount(g.hf_cell[out], weights=a[out] / Vc[out], minlength=self.N)
-            m = (a < 0) & interior
-            K = sp.coo_matrix((a[m] / Vc[m], (g.hf_cell[m], g.hf_nb[m])), shape=(self.N, self.N))
-            K = (K + sp.diags(diag)).tocsc()
-            ab = a[self.bhf]
-            bi = np.where(ab < 0)[0]                 # inflow boundary half-faces
-            self._K.append(K)
-            self._bin.append((bi, -ab[bi] / g.V[self.bcell_of_hf[bi]]))
+        # per-direction unit advection operators K_i (Eq. (13)), built on
+        # first use (see _direction)
+        self._dir = {}
         self._lu = {}
         self._lap = None
+
+    def _direction(self, i):
+        """K_i of Eq. (13) for direction i, and its inflow boundary half-faces
+        with their coefficients |s_i . An| / V.  K_i e = sum over outflow faces
+        (s.An/V) e_cell + sum over interior inflow faces (s.An/V) e_neighbour."""
+        got = self._dir.get(i)
+        if got is not None:
+            return got
+        g = self.g
+        Vc = g.V[g.hf_cell]
+        interior = g.hf_nb >= 0
+        a = g.hf_An @ self.s[i]
+        out = a > 0
+        diag = np.bincount(g.hf_cell[out], weights=a[out] / Vc[out], minlength=self.N)
+        m = (a < 0) & interior
+        K = sp.coo_matrix((a[m] / Vc[m], (g.hf_cell[m], g.hf_nb[m])), shape=(self.N, self.N))
+        K = (K + sp.diags(diag)).tocsc()
+        ab = a[self.bhf]
+        bi = np.where(ab < 0)[0]                 # inflow boundary half-faces
+        got = (K, (bi, -ab[bi] / g.V[self.bcell_of_hf[bi]]))
+        self._dir[i] = got
+        return got
 
     # ------------------------------------------------------------------ pieces
     def source(self):
@@ -168,11 +177,42 @@ class OracleSolver:
         e_in[pm] = p * spec[pm] + (1.0 - p) * diff[pm][:, :, None]
         return e_in
 
+    def incoming_band(self, eb_band, l):
+        """The same incoming wall values as :meth:`incoming`, for band l only:
+        ``eb_band`` is the wall-cell distribution of band l, shape (cells, D);
+        returns (boundary half-faces, D).  Lets a single task be checked on a
+        mesh whose full (cells, B, D) wall array would not fit in memory."""
+        e_cell = eb_band[self.bidx]                                # (nb, D)
+        sn = self.b_sn
+        outw = np.where(sn > 0, sn, 0.0) * self.w[None, :]
+        diff = np.sum(e_cell * outw, axis=1) / self.b_denom       # (nb,)
+        spec = np.take_along_axis(e_cell, self.R, axis=1)         # (nb, D)
+        t = self.btype
+        e_in = np.empty((self.bhf.size, self.D))
+        th = t == THERMALIZING
+        e_in[th] = (self.bTw[th] * self.C[l] / self.W)[:, None]
+        df = t == DIFFUSE
+        e_in[df] = diff[df][:, None]
+        e_in[t == SPECULAR] = spec[t == SPECULAR]
+        pm = t == PARTIAL
+        p = self.bp[pm][:, None]
+        e_in[pm] = p * spec[pm] + (1.0 - p) * diff[pm][:, None]
+        return e_in
+
+    def solve_task(self, Tdev, e_in_band, i, l):
+        """e'_{l i} over all cells: the transport solve of one (band,
+        direction) task of Eq. (4) from the temperature deviation ``Tdev`` and
+        band l's incoming wall values (as returned by :meth:`incoming_band`)."""
+        bi, coef = self._direction(i)[1]
+        rhs = self.C[l] * Tdev / (self.W * self.tau[l]) + self.source()[:, l]
+        rhs += self.v[l] * np.bincount(self.bcell_of_hf[bi], weights=coef * e_in_band[bi, i], minlength=self.N)
+        return self._factor(i, l).solve(rhs)
+
     def _factor(self, i, l):
         key = (i, l)
         lu = self._lu.get(key)
         if lu is None:
-            A = (sp.identity(self.N, format="csc") / self.tau[l] + self.v[l] * self._K[i]).tocsc()
+            A = (sp.identity(self.N, format="csc") / self.tau[l] + self.v[l] * self._direction(i)[0]).tocsc()
             lu = spla.splu(A)
             self._lu[key] = lu
         return lu
@@ -192,7 +232,7 @@ class OracleSolver:
         e_all = np.zeros((self.N, self.B, self.D)) if store_e else None
         todo = tasks if tasks is not None else [(i, l) for i in range(self.D) for l in range(self.B)]
         for (i, l) in todo:
-            bi, coef = self._bin[i]
+            bi, coef = self._direction(i)[1]
             rhs = self.C[l] * Tdev / (self.W * self.tau[l]) + S[:, l]
             rhs += self.v[l] * np.bincount(self.bcell_of_hf[bi], weights=coef * e_in[bi, l, i],
                                            minlength=self.N)

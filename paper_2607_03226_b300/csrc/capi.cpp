@@ -128,7 +128,7 @@ struct nbte_solver {
   int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0;
   size_t smem = 0;
   double W = 0, beta = 0, Ctot = 0;
-  DBuf rec, pos_cell, chunks, chunk_off, tqp, gring;
+  DBuf rec, pos_cell, chunks, chunk_off, tqp, gring, e_scratch;
   int64_t gring_stride = 0;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
@@ -177,7 +177,7 @@ struct DeviceGuard {
 };
 
 size_t device_bytes(const nbte_solver* S) {
-  const DBuf* all[] = {&S->rec, &S->pos_cell, &S->gring, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
+  const DBuf* all[] = {&S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
                        &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
                        &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
@@ -1436,6 +1436,48 @@ int nbte_get_heat_flux(const nbte_solver* S, double* out) {
   for (int64_t c = 0; c < N; ++c)
     for (int d = 0; d < m.dim; ++d) out[m.perm[c] * m.dim + d] = tmp[c * m.dim + d];
   return NBTE_OK;
+}
+
+}  // extern "C"
+
+// the last sweep's values of one work item, recomputed: its inputs (the
+// gathered (T', Qdot) pairs and the import rows) are still resident and the
+// sweep is deterministic, so re-running the item reproduces them exactly
+template <typename R>
+static int distribution(nbte_solver* S, int dir, int band, double* out) {
+  const Mesh& m = S->mesh->m;
+  const int64_t N = m.n_cells;
+  const int G = S->G;
+  cudaStream_t st = S->stream;
+  NBTE_CK(S->e_scratch.alloc((size_t)N * G * sizeof(R)));
+  SweepArgs<R> a = sweep_args<R>(S, 0);
+  a.item0 = dir * S->n_groups + band / G;
+  a.e_out = S->e_scratch.as<R>();
+  NBTE_CK(launch_sweep<R>(a, S->K, G, 1, S->threads, S->smem, st));
+  std::vector<R> tmp((size_t)N * G);
+  NBTE_CK(cudaMemcpyAsync(tmp.data(), S->e_scratch.p, tmp.size() * sizeof(R), cudaMemcpyDeviceToHost, st));
+  unsigned long long err = 0;
+  NBTE_CK(cudaMemcpyAsync(&err, S->res.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost, st));
+  NBTE_CK(cudaStreamSynchronize(st));
+  if (err) {
+    cudaMemset(S->res.p, 0, 32);
+    return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
+  }
+  const int b = band % G;
+  for (int64_t c = 0; c < N; ++c) out[m.perm[c]] = (double)tmp[(size_t)c * G + b];
+  return NBTE_OK;
+}
+
+extern "C" {
+
+int nbte_get_distribution(nbte_solver* S, int32_t direction, int32_t band, double* out) {
+  if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
+  if (!S->have_results || S->layout_key.empty())
+    return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
+  if (direction < 0 || direction >= S->D) return fail(NBTE_ERR_ARG, "direction out of range");
+  if (band < 0 || band >= S->B) return fail(NBTE_ERR_ARG, "band out of range");
+  DeviceGuard g(S->device);
+  return S->prec ? distribution<float>(S, direction, band, out) : distribution<double>(S, direction, band, out);
 }
 
 int nbte_get_wall_heat(const nbte_solver* S, int32_t tag, double* out) {

@@ -40,6 +40,8 @@ struct SweepArgs {
   const R* band_aQ;              // C / (C_tot W)
   const double* dir_w;           // [D]
   const double* dir_s;           // [D*3]
+  int item0;                     // first work item of the launch (block b runs item item0 + b)
+  R* e_out;                      // null, or [N*G]: every cell's outgoing values of the item's bands
   R* gring;                      // global-memory value rings, or null for the shared-memory ring
   int64_t gring_stride;          // elements per CTA's global ring
   R* part;                       // [n_items*N] collision-moment partials (of e - e0)

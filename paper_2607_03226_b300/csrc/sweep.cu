@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
   constexpr int NQ = RL.size / 16;
   constexpr int GP = padded_group(G, (int)sizeof(R));   // row length of the import/export tables
 
-  const int item = blockIdx.x;
+  const int item = blockIdx.x + a.item0;
   const int i = a.item_dir[item];
   const int g = a.item_grp[item];
   const int ncons = blockDim.x - 32;
@@ -325,6 +325,7 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
       }
       if (slot >= 0) store_vals<R, G>(ring + slot * G, e);
       if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * GP, e);
+      if (a.e_out) store_vals<R, G>(a.e_out + (size_t)cell * G, e);
       part[cell] = nl;
       if (a.full) {
         R es = R(0), evs = R(0);

@@ -37,7 +37,7 @@ EXPORTS = [
     "nbte_solver_set_stream", "nbte_set_bands", "nbte_set_quadrature", "nbte_set_boundaries",
     "nbte_set_heat_source", "nbte_default_opts", "nbte_solve_steady", "nbte_get_temperature",
     "nbte_get_heat_flux", "nbte_get_wall_heat", "nbte_plan_stats", "nbte_last_error", "nbte_version",
-    "nbte_laplacian_solve_noalloc",
+    "nbte_laplacian_solve_noalloc", "nbte_get_distribution",
 ]
 
 
@@ -102,6 +102,7 @@ def load(path: str | None = None):
         "nbte_get_temperature": ([_P, C.c_int, _D], C.c_int),
         "nbte_get_heat_flux": ([_P, _D], C.c_int),
         "nbte_get_wall_heat": ([_P, C.c_int32, _D], C.c_int),
+        "nbte_get_distribution": ([_P, C.c_int32, C.c_int32, _D], C.c_int),
         "nbte_plan_stats": ([_P, C.POINTER(nbte_solve_opts), _I64], C.c_int),
         "nbte_last_error": ([], C.c_char_p),
         "nbte_version": ([], C.c_char_p),
@@ -246,6 +247,12 @@ def nbte_get_heat_flux(solver, n_cells, dim):
     return out
 
 
+def nbte_get_distribution(solver, direction, band, n_cells):
+    out = np.empty(n_cells, dtype=np.float64)
+    _check(load().nbte_get_distribution(solver, int(direction), int(band), out.ctypes.data_as(_D)))
+    return out
+
+
 def nbte_get_wall_heat(solver, tag):
     v = C.c_double()
     _check(load().nbte_get_wall_heat(solver, int(tag), C.byref(v)))
@@ -313,6 +320,9 @@ class Solver:
 
     def wall_heat(self, tag):
         return nbte_get_wall_heat(self.solver, tag)
+
+    def distribution(self, direction, band):
+        return nbte_get_distribution(self.solver, direction, band, self.n_cells)
 
     def plan_stats(self, **kw):
         return nbte_plan_stats(self.solver, make_opts(**kw))

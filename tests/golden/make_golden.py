@@ -13,6 +13,12 @@ Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_conve
                             1 and 2 from T_ref, on 4096 seeded sample cells.
 * ``finfet2d_converged``  - the same problem converged (sequential, 1e-10),
                             T_L and q on the sample cells.
+* ``cube3d_tasks`` / ``finfet3d_tasks`` - the 64^3 cube and the 1.14M-tet
+                            FinFET at full size: the distribution e'_{l i} of
+                            a few (direction, band) tasks in the first
+                            sequential iteration from T_ref (walls at
+                            equilibrium with T_ref), on 4096 sample cells.
+                            Each task is one sparse solve of Eq. (4).
 """
 from __future__ import annotations
 
@@ -81,6 +87,34 @@ def finfet2d_converged():
         converged=r["converged"], seconds=time.time() - t, sample_seed=SAMPLE_SEED,
         cells=idx.tolist(), T=r["T"][idx].tolist(), q=r["q"][idx].tolist(),
         T_max=float(r["T"].max()), energy_imbalance=r["energy_imbalance"]))
+
+
+def _tasks(name, p, tasks):
+    o = OracleSolver(p)
+    idx = _sample(p.n_cells)
+    T0 = np.zeros(o.N)
+    eb0 = np.zeros((o.bcells.size, o.D))    # wall cells at equilibrium with T_ref
+    out = dict(problem=f"{name}()", scheme="sequential", iteration=1, sample_seed=SAMPLE_SEED,
+               cells=idx.tolist(), tasks=[])
+    for (i, l) in tasks:
+        t = time.time()
+        e = o.solve_task(T0, o.incoming_band(eb0, l), i, l)
+        out["tasks"].append(dict(direction=int(i), band=int(l), e=e[idx].tolist(),
+                                 max_abs=float(np.abs(e).max()), seconds=time.time() - t))
+        print(name, "task", i, l, "done", time.time() - t, flush=True)
+    _write(f"{name}_tasks.json", out)
+
+
+def cube3d_tasks():
+    p = W.problems.cube3d()
+    s = np.asarray(p.s)
+    along = np.argsort(-s[:, 0])            # most nearly +x first (the hot wall is x = 0)
+    _tasks("cube3d", p, [(int(along[0]), 0), (int(along[5]), p.n_bands - 1), (int(along[20]), 21)])
+
+
+def finfet3d_tasks():
+    p = W.problems.finfet3d()
+    _tasks("finfet3d", p, [(0, 0), (p.n_dirs // 2, 21), (p.n_dirs - 1, p.n_bands - 1)])
 
 
 if __name__ == "__main__":

@@ -208,3 +208,24 @@ def test_finfet2d_full_size_converged(nbte_mod):
     assert info["status"] == 0
     assert np.abs(s.temperature(0)[idx] - Tg).max() / dev < 2e-6
     s.close()
+
+
+@pytest.mark.parametrize("name", ["fin2d_mixed", "fin3d_tets", "cube_hex"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-6)])
+def test_distribution_every_task(nbte_mod, name, precision, tol):
+    """e'_{band,direction} of the last sweep (nbte_get_distribution) for every
+    task after three sequential iterations, against the oracle's last sweep
+    (relative to max|e'| over the task)."""
+    p = CASES[name]()
+    s = nbte_mod.Solver(p)
+    s.solve(scheme="sequential", precision=precision, n_iter=3)
+    r = oracle_run(name, scheme="sequential", n_iter=3, store_e=True)
+    worst = 0.0
+    for i in range(p.n_dirs):
+        for l in range(p.n_bands):
+            ref = r["e"][:, l, i]
+            scale = max(np.abs(ref).max(), 1e-300)
+            worst = max(worst, np.abs(s.distribution(i, l) - ref).max() / scale)
+    print(f"{name} {precision}: worst task error {worst:.2e}")
+    assert worst < tol
+    s.close()
