@@ -202,7 +202,9 @@ typedef struct {
  *   sweep_seconds     summed device time of the sweep launches (profile=1);
  *   sweep_launches    sweep launches timed (profile=1);
  *   kernel_launches   kernels this call launched (graph replays counted by
- *                     their kernel nodes).                                  */
+ *                     their kernel nodes);
+ *   status            this solve's own status (the call's return value for
+ *                     nbte_solve_steady; per solver for nbte_solve_batch).  */
 typedef struct {
   int32_t iterations;
   double residual;
@@ -213,6 +215,7 @@ typedef struct {
   double sweep_seconds;
   int64_t sweep_launches;
   int64_t kernel_launches;
+  int32_t status;
 } nbte_solve_info;
 
 /* Default options: sequential, FP64, tol 1e-10, max_iter 10000.           */
@@ -222,6 +225,20 @@ int nbte_default_opts(nbte_solve_opts* opts);
  * Returns NBTE_OK, NBTE_ERR_NOT_CONVERGED (results of the last iteration are
  * kept and readable), NBTE_ERR_DIVERGED or NBTE_ERR_DEVICE_TIMEOUT.       */
 int nbte_solve_steady(nbte_solver* solver, const nbte_solve_opts* opts, nbte_solve_info* info);
+
+/* Solve several independent problems together (Sec. II iteration for each,
+ * one options record for all).  Every iteration runs all still-unconverged
+ * solvers at once: their sweeps share fused launches (one per sweep variant),
+ * their synthetic corrections one cooperative CG launch in which each solver
+ * owns a share of the blocks, on solvers[0]'s stream.  A solver leaves the
+ * batch when it converges, exactly as nbte_solve_steady would stop it, so
+ * each result equals its solve alone (to the CG's rounding: its block share
+ * differs).  infos[k] (may be NULL) gets solver k's record, status included.
+ * Requirements: n in [1, 148] distinct solvers of one device; opts->T_init
+ * NULL; opts->profile 0.  Returns NBTE_OK if every solver converged, else
+ * the first failing solver's status; every solver's results stay readable. */
+int nbte_solve_batch(nbte_solver* const* solvers, int32_t n, const nbte_solve_opts* opts,
+                     nbte_solve_info* infos);
 
 /* Results of the last solve, in the caller's cell order.
  *   kind 0: lattice temperature T_L after the last update (K);

@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <string>
@@ -137,6 +138,8 @@ struct nbte_solver {
   DBuf cg_x, cg_rw, cg_rcx, cg_scx, cg_perm, cg_agg_rel, cg_agg_cell, cg_blk_cell, cg_blk_agg, cg_Ainv;
   int cg_grid = 0, cg_threads = kCGThreads, cg_Nc = 0, cg_Nc4 = 0, cg_W = 0;
   int cg_max_rows = 0, cg_max_na = 0, cg_smem_vec = 0, cg_smem_ell = 0;
+  int64_t cg_part_key = -1;
+  std::vector<int32_t> h_agg_cell, h_agg_p;   // aggregate row ranges / aggregate of each row (aggregate order)
   // ---- laplacian (synthetic)
   int64_t lap_built = -1;
   DBuf L_ecol, L_eval, L_diag, L_dinv;
@@ -587,12 +590,54 @@ int ensure_laplacian(nbte_solver* S) {
   }
   if (!dense_spd_inverse(Ac, Nc))
     return fail(NBTE_ERR_ARG, "synthetic correction: coarse operator is not positive definite");
-  int nsm = 1;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device);
-  // one block per SM: the CG is latency-bound, so every SM's warps are used
-  // to shorten each block's dependent-load chains
-  const int grid = std::max(1, std::min(std::min(nsm, 256), Nc));
+  const int Nc4 = (Nc + 3) / 4;
+  DeviceGuard g(S->device);
+  NBTE_CK(upload(S->L_ecol, ecol));
+  NBTE_CK(upload(S->L_eval, eval));
+  NBTE_CK(upload(S->L_diag, diag));
+  NBTE_CK(upload(S->L_dinv, dinv));
+  NBTE_CK(upload(S->cg_perm, perm));
+  NBTE_CK(upload(S->cg_agg_cell, agg_cell));
+  std::vector<float> Af((size_t)Nc * Nc4 * 4, 0.0f);
+  for (int r = 0; r < Nc; ++r)
+    for (int c = 0; c < Nc; ++c) Af[(size_t)r * Nc4 * 4 + c] = (float)Ac[(size_t)r * Nc + c];
+  NBTE_CK(upload(S->cg_Ainv, Af));
+  std::vector<double> Ad((size_t)Nc * Nc4 * 4, 0.0);
+  for (int r = 0; r < Nc; ++r)
+    for (int c = 0; c < Nc; ++c) Ad[(size_t)r * Nc4 * 4 + c] = Ac[(size_t)r * Nc + c];
+  NBTE_CK(upload(S->cg_Ainv64, Ad));
+  S->cg_Nc4 = Nc4;
+  S->cg_W = Wl;
+  S->cg_Nc = Nc;
+  S->h_agg_cell = agg_cell;
+  S->h_agg_p = agg_p;
+  NBTE_CK(S->cg_x.alloc(N * 8));
+  NBTE_CK(S->cg_u.alloc(N * 8));
+  NBTE_CK(S->cg_rw.alloc((size_t)Nc * 8));
+  NBTE_CK(S->cg_rcx.alloc((size_t)Nc * 8));
+  NBTE_CK(S->cg_scx.alloc((size_t)Nc * 8));
+  NBTE_CK(cudaMemset(S->cg_x.p, 0, N * 8));   // no previous correction yet
+  NBTE_CK(S->cg_bar.alloc(16));
+  NBTE_CK(S->cg_err.alloc(16));
+  NBTE_CK(S->cg_it.alloc(16));
+  NBTE_CK(S->cg_res.alloc(16));
+  NBTE_CK(cudaMemset(S->cg_err.p, 0, 16));
+  S->cg_part_key = -1;
+  S->lap_built = want;
+  drop_graph(S);
+  return NBTE_OK;
+}
+
+// Blocks of the CG launch and what each owns: `grid` blocks, each a run of
+// whole aggregates with about N/grid rows, and at least `threads_min`
+// threads per block (a batched launch shares one block size).  Chooses which
+// per-block arrays fit in shared memory for that block size.
+int cg_partition(nbte_solver* S, int grid, int threads_min) {
+  const int N = (int)S->mesh->m.n_cells;
+  const int Nc = S->cg_Nc;
+  grid = std::max(1, std::min(std::min(grid, 256), Nc));
   std::vector<int32_t> blk_cell(grid + 1, 0), blk_agg(grid + 1, 0);
+  const std::vector<int32_t>& agg_cell = S->h_agg_cell;
   {
     int b = 0;
     for (int k = 0; k < Nc && b < grid; ++k) {
@@ -612,68 +657,56 @@ int ensure_laplacian(nbte_solver* S) {
   for (int k = 0; k < grid; ++k) {
     max_rows = std::max(max_rows, blk_cell[k + 1] - blk_cell[k]);
     max_na = std::max(max_na, blk_agg[k + 1] - blk_agg[k]);
-    for (int32_t r = blk_cell[k]; r < blk_cell[k + 1]; ++r) agg_rel[r] = agg_p[r] - blk_agg[k];
+    for (int32_t r = blk_cell[k]; r < blk_cell[k + 1]; ++r) agg_rel[r] = S->h_agg_p[r] - blk_agg[k];
   }
-  const int Nc4 = (Nc + 3) / 4;
   // threads per block: enough for one pass over the largest block's rows
-  const int threads = std::min(kCGThreads, std::max(128, (max_rows + 31) / 32 * 32));
+  const int threads = std::min(kCGThreads, std::max(std::max(128, threads_min), (max_rows + 31) / 32 * 32));
+  const int64_t key = ((int64_t)grid << 20) + threads;
+  if (key == S->cg_part_key) return NBTE_OK;
   // shared memory: own-row vectors first, then the ELL rows, as far as they
   // fit (sized for the FP64 coarse variant, the larger one)
   const size_t budget = (size_t)kSweepSmemMax - 2048;
-  auto need = [&](int v, int e) { return cg_smem_layout(Nc4, max_rows, max_na, Wl, threads, v, e, 8).total; };
-  int vec = need(1, 0) <= budget;
-  int ell = vec && need(1, 1) <= budget;
+  auto need = [&](int v, int e) {
+    return cg_smem_layout(S->cg_Nc4, max_rows, max_na, S->cg_W, threads, v, e, 8).total;
+  };
+  const int vec = need(1, 0) <= budget;
+  const int ell = vec && need(1, 1) <= budget;
   if (need(0, 0) > budget) return fail(NBTE_ERR_ARG, "synthetic correction: too many aggregates per block");
   DeviceGuard g(S->device);
-  NBTE_CK(upload(S->L_ecol, ecol));
-  NBTE_CK(upload(S->L_eval, eval));
-  NBTE_CK(upload(S->L_diag, diag));
-  NBTE_CK(upload(S->L_dinv, dinv));
-  NBTE_CK(upload(S->cg_perm, perm));
   NBTE_CK(upload(S->cg_agg_rel, agg_rel));
-  NBTE_CK(upload(S->cg_agg_cell, agg_cell));
   NBTE_CK(upload(S->cg_blk_cell, blk_cell));
   NBTE_CK(upload(S->cg_blk_agg, blk_agg));
-  std::vector<float> Af((size_t)Nc * Nc4 * 4, 0.0f);
-  for (int r = 0; r < Nc; ++r)
-    for (int c = 0; c < Nc; ++c) Af[(size_t)r * Nc4 * 4 + c] = (float)Ac[(size_t)r * Nc + c];
-  NBTE_CK(upload(S->cg_Ainv, Af));
-  std::vector<double> Ad((size_t)Nc * Nc4 * 4, 0.0);
-  for (int r = 0; r < Nc; ++r)
-    for (int c = 0; c < Nc; ++c) Ad[(size_t)r * Nc4 * 4 + c] = Ac[(size_t)r * Nc + c];
-  NBTE_CK(upload(S->cg_Ainv64, Ad));
-  S->cg_Nc4 = Nc4;
-  S->cg_W = Wl;
-  S->cg_max_rows = max_rows;
-  S->cg_max_na = max_na;
-  S->cg_smem_vec = vec;
-  S->cg_smem_ell = ell;
-  NBTE_CK(S->cg_x.alloc(N * 8));
-  NBTE_CK(S->cg_u.alloc(N * 8));
   const size_t work = vec ? 16 : (size_t)N * 8;   // global work vectors only when not in shared memory
   NBTE_CK(S->cg_xw.alloc(work));
   NBTE_CK(S->cg_r.alloc(work));
   NBTE_CK(S->cg_p.alloc(work));
   NBTE_CK(S->cg_s.alloc(work));
   NBTE_CK(S->cg_w.alloc(work));
-  NBTE_CK(S->cg_rw.alloc((size_t)Nc * 8));
-  NBTE_CK(S->cg_rcx.alloc((size_t)Nc * 8));
-  NBTE_CK(S->cg_scx.alloc((size_t)Nc * 8));
-  S->cg_grid = grid;
-  S->cg_Nc = Nc;
-  S->cg_threads = threads;
-  NBTE_CK(cudaMemset(S->cg_x.p, 0, N * 8));   // no previous correction yet
   NBTE_CK(S->cg_slots.alloc((size_t)grid * sizeof(CGSlot)));
-  NBTE_CK(S->cg_bar.alloc(16));
-  NBTE_CK(S->cg_err.alloc(16));
-  NBTE_CK(S->cg_it.alloc(16));
-  NBTE_CK(S->cg_res.alloc(16));
   NBTE_CK(cudaMemset(S->cg_slots.p, 0, S->cg_slots.bytes));
-  NBTE_CK(cudaMemset(S->cg_bar.p, 0, 16));
-  NBTE_CK(cudaMemset(S->cg_err.p, 0, 16));
-  S->lap_built = want;
+  NBTE_CK(cudaMemset(S->cg_bar.p, 0, 16));   // arrivals must start at a multiple of the block count
+  S->cg_max_rows = max_rows;
+  S->cg_max_na = max_na;
+  S->cg_smem_vec = vec;
+  S->cg_smem_ell = ell;
+  S->cg_grid = grid;
+  S->cg_threads = threads;
+  S->cg_part_key = key;
   drop_graph(S);
   return NBTE_OK;
+}
+
+// the partition a solver uses on its own: one block per SM
+int cg_default_partition(nbte_solver* S) {
+  int nsm = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device);
+  return cg_partition(S, nsm, 0);
+}
+
+size_t cg_smem_for(const nbte_solver* S, bool c32) {
+  return cg_smem_layout(S->cg_Nc4, S->cg_max_rows, S->cg_max_na, S->cg_W, S->cg_threads, S->cg_smem_vec,
+                        S->cg_smem_ell, c32 ? 4 : 8)
+      .total;
 }
 
 // ------------------------------------------------------------------ iteration body
@@ -806,42 +839,63 @@ CGArgs cg_args(nbte_solver* S, double tol, int max_it) {
   return a;
 }
 
-// one outer iteration, stream-ordered (capturable)
+// One outer iteration, stream-ordered (capturable), in three parts around
+// the sweep and the CG so that a batch can run every solver's parts and fuse
+// the sweeps and the CGs.
+//   pre:  wall coupling (Sec. II walls, lagged), T' kept for the residual,
+//         (T', Qdot) gathered in level order;
+//   mid:  residual words cleared, collision moment reduced (Eq. (5)) and
+//         either applied (Eq. (6)) or turned into the synthetic rhs;
+//   post: the synthetic update (Eq. (12)) and the residual words to the host.
+template <typename R>
+cudaError_t enqueue_pre(nbte_solver* S, cudaStream_t st) {
+  launch_walls<R>(wall_args<R>(S), st);
+  cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  return launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
+                             (int64_t)S->D * S->mesh->m.n_cells, st);
+}
+
+template <typename R>
+cudaError_t enqueue_mid(nbte_solver* S, int scheme, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(S->res.p, 0, 16, st);
+  if (e != cudaSuccess) return e;
+  launch_update<R>(update_args<R>(S, scheme == 0 ? 0 : 3), st);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t enqueue_post(nbte_solver* S, int scheme, cudaStream_t st) {
+  if (scheme != 0) launch_update<R>(update_args<R>(S, scheme == 1 ? 1 : 2), st);
+  cudaError_t e = cudaMemcpyAsync(S->h_res, S->res.p, 24, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(S->h_misc, S->cg_err.p ? S->cg_err.p : S->res.p, 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// an FP32 coarse preconditioner suffices unless the correction is wanted to
+// near FP64 rounding
+inline bool coarse32(double cg_tol) { return cg_tol >= 1e-7; }
+
 template <typename R>
 cudaError_t enqueue_iteration(nbte_solver* S, int scheme, double cg_tol, int cg_max, cudaEvent_t ev0 = nullptr,
                               cudaEvent_t ev1 = nullptr) {
   cudaStream_t st = S->stream;
-  launch_walls<R>(wall_args<R>(S), st);
-  cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return e;
-  e = launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
-                          (int64_t)S->D * S->mesh->m.n_cells, st);
+  cudaError_t e = enqueue_pre<R>(S, st);
   if (e != cudaSuccess) return e;
   if (ev0) cudaEventRecord(ev0, st);
   e = launch_sweep<R>(sweep_args<R>(S, 0), S->K, S->G, S->n_items, S->threads, S->smem, st);
   if (e != cudaSuccess) return e;
   if (ev1) cudaEventRecord(ev1, st);
-  e = cudaMemsetAsync(S->res.p, 0, 16, st);
+  e = enqueue_mid<R>(S, scheme, st);
   if (e != cudaSuccess) return e;
-  if (scheme == 0) {
-    launch_update<R>(update_args<R>(S, 0), st);
-  } else {
-    launch_update<R>(update_args<R>(S, 3), st);
-    // an FP32 coarse preconditioner suffices unless the correction is wanted
-    // to near FP64 rounding
-    const bool c32 = cg_tol >= 1e-7;
-    const size_t smem = cg_smem_layout(S->cg_Nc4, S->cg_max_rows, S->cg_max_na, S->cg_W, S->cg_threads,
-                                       S->cg_smem_vec, S->cg_smem_ell, c32 ? 4 : 8)
-                            .total;
-    e = launch_cg(cg_args(S, cg_tol, cg_max), c32, S->cg_grid, S->cg_threads, smem, st);
+  if (scheme != 0) {
+    const bool c32 = coarse32(cg_tol);
+    e = launch_cg(cg_args(S, cg_tol, cg_max), c32, S->cg_grid, S->cg_threads, cg_smem_for(S, c32), st);
     if (e != cudaSuccess) return e;
-    launch_update<R>(update_args<R>(S, scheme == 1 ? 1 : 2), st);
   }
-  e = cudaMemcpyAsync(S->h_res, S->res.p, 24, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(S->h_misc, S->cg_err.p ? S->cg_err.p : S->res.p, 4, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return enqueue_post<R>(S, scheme, st);
 }
 
 // T' from T_init (or T_ref), wall distributions at equilibrium with it, no
@@ -950,79 +1004,37 @@ int autotune(nbte_solver* S, const nbte_solve_opts& o) {
   return NBTE_OK;
 }
 
-template <typename R>
-int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
-  const Mesh& m = S->mesh->m;
-  const int64_t N = m.n_cells;
-  cudaStream_t st = S->stream;
-  const double cg_tol = o.cg_tol > 0 ? o.cg_tol : 1e-3;
-  const int cg_max = o.cg_max_iter > 0 ? o.cg_max_iter : 5000;
-  int64_t kernels = 0;
-  // ---- initial state
-  if (!(o.warm && S->have_state)) {
-    kernels += 2;
-    int rc = init_state<R>(S, o);
-    if (rc) return rc;
-    S->have_state = true;
-  } else {
-    kernels += 1;
-    launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)N, st);
-  }
-  if (S->cg_it.p) NBTE_CK(cudaMemsetAsync(S->cg_it.p, 0, 4, st));
-  const int scheme = o.scheme;
-  const bool fixed = o.n_iter > 0;
-  const int limit = fixed ? o.n_iter : o.max_iter;
-  // ---- graph
-  bool use_graph = o.use_graph != 0;
-  const std::string gkey = S->layout_key + "/" + std::to_string(scheme) + "/" + std::to_string(cg_tol) + "/" +
-                           std::to_string(cg_max) + "/" + std::to_string(S->lap_built) + "/" +
-                           std::to_string((long long)(intptr_t)st);
-  if (use_graph && (S->graph == nullptr || S->graph_key != gkey)) {
-    drop_graph(S);
-    cudaGraph_t gr = nullptr;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      cudaError_t e = enqueue_iteration<R>(S, scheme, cg_tol, cg_max);
-      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-      if (e == cudaSuccess && e2 == cudaSuccess && gr &&
-          cudaGraphInstantiate(&S->graph, gr, 0) == cudaSuccess) {
-        S->graph_key = gkey;
-      } else {
-        S->graph = nullptr;
-        use_graph = false;
-      }
-      if (gr) cudaGraphDestroy(gr);
-    } else {
-      use_graph = false;
-    }
-    cudaGetLastError();   // clear a failed capture
-  }
-  // ---- iterate
-  const bool profile = o.profile != 0;
-  if (profile) use_graph = false;   // events bracket each sweep launch
-  const int64_t kernels_per_iter = (S->n_dbf > 0) + (S->n_imp > 0) + 2 + (scheme == 0 ? 1 : 3);
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  if (profile) {
-    NBTE_CK(cudaEventCreate(&ev0));
-    NBTE_CK(cudaEventCreate(&ev1));
-  }
-  double sweep_ms = 0.0;
-  int64_t sweeps_timed = 0;
-  auto t0 = std::chrono::steady_clock::now();
+// One solve in progress: its options, iteration count and stopping state.
+struct Run {
+  nbte_solver* S = nullptr;
+  nbte_solve_opts o{};
+  double cg_tol = 1e-3;
+  int cg_max = 5000;
+  bool fixed = false;
+  int limit = 0;
   int it = 0;
   double r = INFINITY;
   int status = NBTE_OK;
-  // with a fixed iteration count the host only looks at the device once
-  const bool check_each = !fixed || profile;
   double best_r = INFINITY;
   int it_best = 0;
   bool floor_reached = false;
-  auto check = [&]() -> bool {   // returns true to stop
+  bool done = false;
+  int64_t kernels = 0;
+  double sweep_ms = 0.0;
+  int64_t sweeps_timed = 0;
+  std::chrono::steady_clock::time_point t0, t1;
+
+  int64_t kernels_per_iter() const {
+    return (S->n_dbf > 0) + (S->n_imp > 0) + 2 + (o.scheme == 0 ? 1 : 3);
+  }
+  // after an iteration's residual words reached the host: true to stop
+  bool check() {
     if (S->h_res[2] != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
       cudaMemset(S->res.p, 0, 32);
       return true;
     }
-    if (S->h_misc[0] != 0 && scheme != 0) {
+    if (S->h_misc[0] != 0 && o.scheme != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the CG correction gave up");
       cudaMemset(S->cg_err.p, 0, 16);
       cudaMemset(S->cg_slots.p, 0, S->cg_slots.bytes);
@@ -1037,7 +1049,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
       r = INFINITY;
       return true;
     }
-    r = dmax / std::max(tmax, 1e-300);
+    r = dmax / std::max(tmax, 1e-300);   // the convergence measure (relative increment of T')
     if (tmax == 0.0 && dmax == 0.0) r = 0.0;
     if (!fixed && r < o.tol) return true;
     // FP32 sweep: the relative increment bottoms out at the rounding floor;
@@ -1052,40 +1064,54 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
         return true;
       }
     }
-    return false;
-  };
-  while (it < limit) {
-    if (use_graph) NBTE_CK(cudaGraphLaunch(S->graph, st));
-    else NBTE_CK(enqueue_iteration<R>(S, scheme, cg_tol, cg_max, ev0, ev1));
-    kernels += kernels_per_iter;
-    ++it;
-    if (!check_each) continue;
-    NBTE_CK(cudaStreamSynchronize(st));
-    if (profile) {
-      float ms = 0.f;
-      NBTE_CK(cudaEventElapsedTime(&ms, ev0, ev1));
-      sweep_ms += ms;
-      ++sweeps_timed;
-    }
-    if (check()) break;
+    return it >= limit;
   }
-  if (!check_each) {
-    NBTE_CK(cudaStreamSynchronize(st));
-    check();
+};
+
+template <typename R>
+int run_begin(Run& run, nbte_solver* S, const nbte_solve_opts& o) {
+  run.S = S;
+  run.o = o;
+  run.cg_tol = o.cg_tol > 0 ? o.cg_tol : 1e-3;
+  run.cg_max = o.cg_max_iter > 0 ? o.cg_max_iter : 5000;
+  run.fixed = o.n_iter > 0;
+  run.limit = run.fixed ? o.n_iter : o.max_iter;
+  cudaStream_t st = S->stream;
+  if (!(o.warm && S->have_state)) {
+    run.kernels += 2;
+    int rc = init_state<R>(S, o);
+    if (rc) return rc;
+    S->have_state = true;
+  } else {
+    run.kernels += 1;
+    launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)S->mesh->m.n_cells, st);
   }
-  auto t1 = std::chrono::steady_clock::now();
-  if (ev0) cudaEventDestroy(ev0);
-  if (ev1) cudaEventDestroy(ev1);
-  if (status == NBTE_OK && !fixed && !(r < o.tol) && !floor_reached) status = NBTE_ERR_NOT_CONVERGED;
+  if (S->cg_it.p) NBTE_CK(cudaMemsetAsync(S->cg_it.p, 0, 4, st));
+  run.t0 = std::chrono::steady_clock::now();
+  return NBTE_OK;
+}
+
+// results of a finished run: the last sweep replayed with the energy and
+// flux moments on (unless skipped), the energy balance, the info record
+template <typename R>
+int run_finish(Run& run, nbte_solve_info* info) {
+  nbte_solver* S = run.S;
+  const nbte_solve_opts& o = run.o;
+  const Mesh& m = S->mesh->m;
+  const int64_t N = m.n_cells;
+  cudaStream_t st = S->stream;
+  run.t1 = std::chrono::steady_clock::now();
+  int status = run.status;
+  if (status == NBTE_OK && !run.fixed && !(run.r < o.tol) && !run.floor_reached) status = NBTE_ERR_NOT_CONVERGED;
   S->have_results = status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED;
   S->have_outputs = false;
-  // ---- moments of the last sweep: replay it with the energy/flux moments on
   if ((status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED) && !o.skip_outputs) {
-    kernels += 4;
+    run.kernels += 4;
     NBTE_CK(cudaMemsetAsync(S->accE.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
     launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
-    NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ_fin.as<R>(), (int64_t)S->D * N, st));
+    NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ_fin.as<R>(), (int64_t)S->D * N,
+                                st));
     NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 1), S->K, S->G, S->n_items, S->threads, S->smem, st));
     WallHeatArgs<R> wh{};
     wh.Bp = S->Bp;
@@ -1122,17 +1148,275 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
     S->last_energy_imbalance = std::fabs(therm - qtot) / std::max(std::max(qabs, absall), 1e-300);
   }
   if (info) {
-    info->iterations = it;
-    info->residual = r;
+    info->iterations = run.it;
+    info->residual = run.r;
     info->energy_imbalance = S->last_energy_imbalance;
     info->lagged_faces = S->lagged;
-    info->seconds = std::chrono::duration<double>(t1 - t0).count();
+    info->seconds = std::chrono::duration<double>(run.t1 - run.t0).count();
     int32_t cgi = 0;
-    if (S->cg_it.p && scheme != 0) cudaMemcpy(&cgi, S->cg_it.p, 4, cudaMemcpyDeviceToHost);
+    if (S->cg_it.p && o.scheme != 0) cudaMemcpy(&cgi, S->cg_it.p, 4, cudaMemcpyDeviceToHost);
     info->cg_iterations = cgi;
-    info->sweep_seconds = sweep_ms * 1e-3;
-    info->sweep_launches = sweeps_timed;
-    info->kernel_launches = kernels;
+    info->sweep_seconds = run.sweep_ms * 1e-3;
+    info->sweep_launches = run.sweeps_timed;
+    info->kernel_launches = run.kernels;
+    info->status = status;
+  }
+  return status;
+}
+
+template <typename R>
+int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
+  Run run;
+  int rc = run_begin<R>(run, S, o);
+  if (rc) return rc;
+  cudaStream_t st = S->stream;
+  const int scheme = o.scheme;
+  // ---- graph
+  bool use_graph = o.use_graph != 0;
+  const std::string gkey = S->layout_key + "/" + std::to_string(scheme) + "/" + std::to_string(run.cg_tol) + "/" +
+                           std::to_string(run.cg_max) + "/" + std::to_string(S->lap_built) + "/" +
+                           std::to_string(S->cg_part_key) + "/" + std::to_string((long long)(intptr_t)st);
+  if (use_graph && (S->graph == nullptr || S->graph_key != gkey)) {
+    drop_graph(S);
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = enqueue_iteration<R>(S, scheme, run.cg_tol, run.cg_max);
+      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+      if (e == cudaSuccess && e2 == cudaSuccess && gr &&
+          cudaGraphInstantiate(&S->graph, gr, 0) == cudaSuccess) {
+        S->graph_key = gkey;
+      } else {
+        S->graph = nullptr;
+        use_graph = false;
+      }
+      if (gr) cudaGraphDestroy(gr);
+    } else {
+      use_graph = false;
+    }
+    cudaGetLastError();   // clear a failed capture
+  }
+  // ---- iterate
+  const bool profile = o.profile != 0;
+  if (profile) use_graph = false;   // events bracket each sweep launch
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (profile) {
+    NBTE_CK(cudaEventCreate(&ev0));
+    NBTE_CK(cudaEventCreate(&ev1));
+  }
+  // with a fixed iteration count the host only looks at the device once
+  const bool check_each = !run.fixed || profile;
+  while (run.it < run.limit) {
+    if (use_graph) NBTE_CK(cudaGraphLaunch(S->graph, st));
+    else NBTE_CK(enqueue_iteration<R>(S, scheme, run.cg_tol, run.cg_max, ev0, ev1));
+    run.kernels += run.kernels_per_iter();
+    ++run.it;
+    if (!check_each) continue;
+    NBTE_CK(cudaStreamSynchronize(st));
+    if (profile) {
+      float ms = 0.f;
+      NBTE_CK(cudaEventElapsedTime(&ms, ev0, ev1));
+      run.sweep_ms += ms;
+      ++run.sweeps_timed;
+    }
+    if (run.check()) break;
+  }
+  if (!check_each) {
+    NBTE_CK(cudaStreamSynchronize(st));
+    run.check();
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  return run_finish<R>(run, info);
+}
+
+// ------------------------------------------------------------------ batches
+// Device tables of one batch composition (the still-active solvers): for each
+// sweep variant the solvers' SweepArgs and item prefix sums, and for the CG
+// every synthetic solver's CGArgs and block prefix sums.
+template <typename R>
+struct BatchTables {
+  struct SweepGroup {
+    int K = 0, G = 0, threads = 0, items = 0;
+    bool gr = false;
+    size_t smem = 0;
+    std::vector<int> members;
+    DBuf args, start;
+  };
+  std::deque<SweepGroup> groups;   // deque: the device buffers never move
+  std::vector<int> cg_members;
+  DBuf cg_args_d, cg_start_d;
+  int cg_blocks = 0, cg_threads = 0;
+  size_t cg_smem = 0;
+  cudaGraphExec_t graph = nullptr;
+  ~BatchTables() {
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+template <typename R>
+int batch_build(BatchTables<R>& bt, std::vector<Run>& runs, const std::vector<int>& active) {
+  bt.groups.clear();
+  for (int k : active) {
+    nbte_solver* S = runs[k].S;
+    const bool gr = S->gring_stride > 0;
+    typename BatchTables<R>::SweepGroup* grp = nullptr;
+    for (auto& g : bt.groups)
+      if (g.K == S->K && g.G == S->G && g.gr == gr) grp = &g;
+    if (!grp) {
+      bt.groups.emplace_back();
+      grp = &bt.groups.back();
+      grp->K = S->K;
+      grp->G = S->G;
+      grp->gr = gr;
+    }
+    grp->members.push_back(k);
+  }
+  for (auto& g : bt.groups) {
+    std::vector<SweepArgs<R>> args;
+    std::vector<int32_t> start(1, 0);
+    for (int k : g.members) {
+      nbte_solver* S = runs[k].S;
+      args.push_back(sweep_args<R>(S, 0));
+      start.push_back(start.back() + S->n_items);
+      g.threads = std::max(g.threads, S->threads);
+      g.smem = std::max(g.smem, S->smem);
+    }
+    g.items = start.back();
+    NBTE_CK(g.args.alloc(args.size() * sizeof(SweepArgs<R>)));
+    NBTE_CK(cudaMemcpy(g.args.p, args.data(), args.size() * sizeof(SweepArgs<R>), cudaMemcpyHostToDevice));
+    NBTE_CK(upload(g.start, start));
+  }
+  // CG: every synthetic solver gets blocks in proportion to its cells (at
+  // least one); one block per SM in all
+  bt.cg_members.clear();
+  bt.cg_blocks = 0;
+  for (int k : active)
+    if (runs[k].o.scheme != 0) bt.cg_members.push_back(k);
+  if (!bt.cg_members.empty()) {
+    nbte_solver* S0 = runs[bt.cg_members[0]].S;
+    int nsm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S0->device);
+    const int n = (int)bt.cg_members.size();
+    if (n > nsm) return fail(NBTE_ERR_ARG, "more synthetic solvers in one batch than SMs");
+    double tot = 0;
+    for (int k : bt.cg_members) tot += (double)runs[k].S->mesh->m.n_cells;
+    std::vector<int> share(n);
+    int used = 0;
+    for (int j = 0; j < n; ++j) {
+      nbte_solver* S = runs[bt.cg_members[j]].S;
+      share[j] = std::max(1, (int)std::floor((nsm - n) * (double)S->mesh->m.n_cells / tot) + 1);
+      share[j] = std::min(share[j], S->cg_Nc);
+      used += share[j];
+    }
+    while (used > nsm) {   // rounding can overshoot by a few: trim the largest
+      int jm = (int)(std::max_element(share.begin(), share.end()) - share.begin());
+      --share[jm];
+      --used;
+    }
+    int T = 0;
+    for (int j = 0; j < n; ++j) {
+      int rc = cg_partition(runs[bt.cg_members[j]].S, share[j], 0);
+      if (rc) return rc;
+      T = std::max(T, runs[bt.cg_members[j]].S->cg_threads);
+    }
+    std::vector<CGArgs> args;
+    std::vector<int32_t> start(1, 0);
+    bt.cg_smem = 0;
+    const bool c32 = coarse32(runs[bt.cg_members[0]].cg_tol);
+    for (int j = 0; j < n; ++j) {
+      Run& run = runs[bt.cg_members[j]];
+      int rc = cg_partition(run.S, share[j], T);
+      if (rc) return rc;
+      args.push_back(cg_args(run.S, run.cg_tol, run.cg_max));
+      start.push_back(start.back() + run.S->cg_grid);
+      bt.cg_smem = std::max(bt.cg_smem, cg_smem_for(run.S, c32));
+    }
+    bt.cg_blocks = start.back();
+    bt.cg_threads = T;
+    NBTE_CK(bt.cg_args_d.alloc(args.size() * sizeof(CGArgs)));
+    NBTE_CK(cudaMemcpy(bt.cg_args_d.p, args.data(), args.size() * sizeof(CGArgs), cudaMemcpyHostToDevice));
+    NBTE_CK(upload(bt.cg_start_d, start));
+  }
+  if (bt.graph) {
+    cudaGraphExecDestroy(bt.graph);
+    bt.graph = nullptr;
+  }
+  return NBTE_OK;
+}
+
+template <typename R>
+cudaError_t batch_enqueue(BatchTables<R>& bt, std::vector<Run>& runs, const std::vector<int>& active,
+                          cudaStream_t st) {
+  const int scheme = runs[active[0]].o.scheme;
+  cudaError_t e;
+  for (int k : active)
+    if ((e = enqueue_pre<R>(runs[k].S, st)) != cudaSuccess) return e;
+  for (auto& g : bt.groups) {
+    e = launch_sweep_batch<R>(g.args.template as<SweepArgs<R>>(), g.start.template as<int32_t>(), (int)g.members.size(), g.K, g.G,
+                              g.gr, g.items, g.threads, g.smem, st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int k : active)
+    if ((e = enqueue_mid<R>(runs[k].S, scheme, st)) != cudaSuccess) return e;
+  if (!bt.cg_members.empty()) {
+    e = launch_cg_batch(bt.cg_args_d.template as<CGArgs>(), bt.cg_start_d.template as<int32_t>(), (int)bt.cg_members.size(),
+                        coarse32(runs[bt.cg_members[0]].cg_tol), bt.cg_blocks, bt.cg_threads, bt.cg_smem, st);
+    if (e != cudaSuccess) return e;
+  }
+  for (int k : active)
+    if ((e = enqueue_post<R>(runs[k].S, scheme, st)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// Several solvers iterated together until each stops (see nbte_solve_batch).
+template <typename R>
+int run_batch(const std::vector<nbte_solver*>& Ss, const nbte_solve_opts& o, nbte_solve_info* infos) {
+  const int n = (int)Ss.size();
+  cudaStream_t st = Ss[0]->stream;
+  std::vector<Run> runs(n);
+  for (int k = 0; k < n; ++k) {
+    int rc = run_begin<R>(runs[k], Ss[k], o);
+    if (rc) return rc;
+    NBTE_CK(cudaStreamSynchronize(Ss[k]->stream));
+  }
+  std::vector<int> active(n);
+  for (int k = 0; k < n; ++k) active[k] = k;
+  BatchTables<R> bt;
+  bool rebuild = true;
+  while (!active.empty()) {
+    if (rebuild) {
+      int rc = batch_build<R>(bt, runs, active);
+      if (rc) return rc;
+      rebuild = false;
+      if (o.use_graph) {
+        cudaGraph_t gr = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          cudaError_t e = batch_enqueue<R>(bt, runs, active, st);
+          cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+          if (!(e == cudaSuccess && e2 == cudaSuccess && gr && cudaGraphInstantiate(&bt.graph, gr, 0) == cudaSuccess))
+            bt.graph = nullptr;
+          if (gr) cudaGraphDestroy(gr);
+        }
+        cudaGetLastError();   // clear a failed capture
+      }
+    }
+    if (bt.graph) NBTE_CK(cudaGraphLaunch(bt.graph, st));
+    else NBTE_CK(batch_enqueue<R>(bt, runs, active, st));
+    NBTE_CK(cudaStreamSynchronize(st));
+    std::vector<int> still;
+    for (int k : active) {
+      Run& run = runs[k];
+      ++run.it;
+      run.kernels += run.kernels_per_iter();
+      if (run.check()) rebuild = true;
+      else still.push_back(k);
+    }
+    active.swap(still);
+  }
+  int status = NBTE_OK;
+  for (int k = 0; k < n; ++k) {
+    const int rc = run_finish<R>(runs[k], infos ? infos + k : nullptr);
+    if (rc != NBTE_OK && status == NBTE_OK) status = rc;
   }
   return status;
 }
@@ -1368,6 +1652,30 @@ int nbte_plan_stats(nbte_solver* S, const nbte_solve_opts* opts, int64_t stats[1
   return NBTE_OK;
 }
 
+// prepare one solver for a solve with options o (plan, layout, heat source,
+// Laplacian); shared by the single and the batched entry points
+static int prepare(nbte_solver* S, const nbte_solve_opts& o) {
+  if (S->B <= 0) return fail(NBTE_ERR_STATE, "nbte_set_bands must be called before solving");
+  if (S->D <= 0) return fail(NBTE_ERR_STATE, "nbte_set_quadrature must be called before solving");
+  if (!S->bcs_set) return fail(NBTE_ERR_STATE, "nbte_set_boundaries must be called before solving");
+  int rc = ensure_device(S);
+  if (rc) return rc;
+  DeviceGuard g(S->device);
+  rc = ensure_plan(S);
+  if (rc) return rc;
+  rc = autotune(S, o);
+  if (rc) return rc;
+  rc = ensure_layout(S, o);
+  if (rc) return rc;
+  rc = ensure_q(S);
+  if (rc) return rc;
+  if (o.scheme != 0) {
+    rc = ensure_laplacian(S);
+    if (rc) return rc;
+  }
+  return NBTE_OK;
+}
+
 int nbte_solve_steady(nbte_solver* S, const nbte_solve_opts* opts, nbte_solve_info* info) {
   if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
   nbte_solve_opts o;
@@ -1375,28 +1683,45 @@ int nbte_solve_steady(nbte_solver* S, const nbte_solve_opts* opts, nbte_solve_in
   if (opts) o = *opts;
   int rc = check_opts(o);
   if (rc) return rc;
-  if (S->B <= 0) return fail(NBTE_ERR_STATE, "nbte_set_bands must be called before solving");
-  if (S->D <= 0) return fail(NBTE_ERR_STATE, "nbte_set_quadrature must be called before solving");
-  if (!S->bcs_set) return fail(NBTE_ERR_STATE, "nbte_set_boundaries must be called before solving");
-  rc = ensure_device(S);
-  if (rc) return rc;
-  DeviceGuard g(S->device);
   try {
-    rc = ensure_plan(S);
+    rc = prepare(S, o);
     if (rc) return rc;
-    rc = autotune(S, o);
-    if (rc) return rc;
-    rc = ensure_layout(S, o);
-    if (rc) return rc;
-    if (S->version_q != -2) {
-      rc = ensure_q(S);
-      if (rc) return rc;
-    }
+    DeviceGuard g(S->device);
     if (o.scheme != 0) {
-      rc = ensure_laplacian(S);
+      rc = cg_default_partition(S);
       if (rc) return rc;
     }
     return S->prec ? run_solve<float>(S, o, info) : run_solve<double>(S, o, info);
+  } catch (const std::bad_alloc&) {
+    return fail(NBTE_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(NBTE_ERR_ARG, e.what());
+  }
+}
+
+int nbte_solve_batch(nbte_solver* const* solvers, int32_t n, const nbte_solve_opts* opts, nbte_solve_info* infos) {
+  if (!solvers || n < 1 || n > 148) return fail(NBTE_ERR_ARG, "n must be in [1, 148] with a solver array");
+  nbte_solve_opts o;
+  nbte_default_opts(&o);
+  if (opts) o = *opts;
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (o.T_init) return fail(NBTE_ERR_ARG, "T_init is not supported by nbte_solve_batch");
+  if (o.profile) return fail(NBTE_ERR_ARG, "profile is not supported by nbte_solve_batch");
+  std::vector<nbte_solver*> Ss(solvers, solvers + n);
+  for (int k = 0; k < n; ++k) {
+    if (!Ss[k]) return fail(NBTE_ERR_ARG, "null solver in the batch");
+    for (int j = 0; j < k; ++j)
+      if (Ss[j] == Ss[k]) return fail(NBTE_ERR_ARG, "a solver appears twice in the batch");
+  }
+  try {
+    for (int k = 0; k < n; ++k) {
+      rc = prepare(Ss[k], o);
+      if (rc) return rc;
+      if (Ss[k]->device != Ss[0]->device) return fail(NBTE_ERR_ARG, "the solvers of a batch must share a device");
+    }
+    DeviceGuard g(Ss[0]->device);
+    return o.precision ? run_batch<float>(Ss, o, infos) : run_batch<double>(Ss, o, infos);
   } catch (const std::bad_alloc&) {
     return fail(NBTE_ERR_OOM, "host allocation failed");
   } catch (const std::exception& e) {

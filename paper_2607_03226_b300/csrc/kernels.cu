@@ -263,12 +263,12 @@ __device__ __forceinline__ float warp_sumf(float s) {
 // their reciprocals while it waits (work off the critical path).
 template <int NV>
 __device__ bool grid_reduce(const double* v, double* tot, double* red_s, CGSlot* slots, unsigned long long* bar,
-                            unsigned gen, int32_t* err, double* inv = nullptr, int n_inv = 0) {
+                            unsigned gen, int32_t* err, int blk, unsigned nb, double* inv = nullptr,
+                            int n_inv = 0) {
   static_assert(NV >= 0 && NV <= 3, "a slot carries up to three sums");
   __shared__ double s_tot[3];
   __shared__ int s_abort;
   const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
-  const unsigned nb = gridDim.x;
   const int buf = gen & 1;
 #pragma unroll
   for (int j = 0; j < NV; ++j) red_s[j * T + tid] = v[j];
@@ -277,7 +277,7 @@ __device__ bool grid_reduce(const double* v, double* tot, double* red_s, CGSlot*
     double y = 0.0;
     for (int i = lane; i < T; i += 32) y += red_s[warp * T + i];
     y = warp_sum(y);
-    if (lane == 0) slots[blockIdx.x].v[buf][warp] = y;
+    if (lane == 0) slots[blk].v[buf][warp] = y;
   }
   __syncthreads();   // orders every thread's global writes (and the slot sums) before the fence below
   if (tid == 0) {
@@ -344,11 +344,10 @@ struct CoarseT<true> { using T = float; };
 // FP32 (a preconditioner only has to be fixed and SPD to rounding; the
 // iteration's vectors and inner products stay FP64).
 template <bool C32>
-__global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
+__device__ __forceinline__ void cg_body(const CGArgs& a, const int blk, const unsigned nb, unsigned char* cg_smem) {
   using CT = typename CoarseT<C32>::T;
-  extern __shared__ __align__(16) unsigned char cg_smem[];
-  const int c0 = a.blk_cell[blockIdx.x], nr = a.blk_cell[blockIdx.x + 1] - c0;
-  const int a0 = a.blk_agg[blockIdx.x], na = a.blk_agg[blockIdx.x + 1] - a0;
+  const int c0 = a.blk_cell[blk], nr = a.blk_cell[blk + 1] - c0;
+  const int a0 = a.blk_agg[blk], na = a.blk_agg[blk + 1] - a0;
   const int tid = threadIdx.x, T = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarp = T >> 5;
   const int Nc = a.Nc, nc4 = a.Nc4, W = a.W;
@@ -497,7 +496,7 @@ __global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
     v3[1] = fma(x[l], qx, v3[1]);
     v3[2] = fma(b, b, v3[2]);
   }
-  if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err)) return;
+  if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err, blk, nb)) return;
   if (tid == 0) {
     const double th = t3[1] > 0.0 ? t3[0] / t3[1] : 0.0;
     s_scal[0] = isfinite(th) ? th : 0.0;
@@ -515,7 +514,7 @@ __global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
   }
   __syncthreads();
   restrict_own(rcx);
-  if (grid_reduce<1>(v1, t1, red_s, a.slots, a.bar, gen++, a.err)) return;
+  if (grid_reduce<1>(v1, t1, red_s, a.slots, a.bar, gen++, a.err, blk, nb)) return;
   double rho = t1[0];
   const double stop = a.tol * a.tol * bb;
   int it = 0;
@@ -523,7 +522,7 @@ __global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
     for (int k = tid; k < Nc; k += T) rc_s[k] = __ldcg(rcx + k);
     __syncthreads();
     precondition();
-    if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err)) return;
+    if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err, blk, nb)) return;
     // s_scal[2], s_scal[3]: 1/gamma and 1/alpha of the previous step (thread 0)
     while (true) {
       // -- w = A u, (r,u), (w,u), (r,r), aggregate sums of w
@@ -545,7 +544,7 @@ __global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
       }
       __syncthreads();
       restrict_own(rw);
-      if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err)) return;
+      if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err, blk, nb)) return;
       const double gamma = t3[0], delta = t3[1];
       rho = t3[2];
       if (!(rho > stop) || it >= a.max_it) break;
@@ -588,7 +587,7 @@ __global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
         s_scal[3] = alpha;
       }
       ++it;
-      if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err, s_scal + 2, 2)) return;
+      if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err, blk, nb, s_scal + 2, 2)) return;
     }
   }
   // every read of the previous correction happened before the first barrier
@@ -596,10 +595,59 @@ __global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
     a.x_out[a.perm[c0 + l]] = x[l];
     a.x[c0 + l] = x[l];
   }
-  if (blockIdx.x == 0 && tid == 0) {
+  if (blk == 0 && tid == 0) {
     *a.it_out += it;
     *a.res_out = bb > 0.0 ? sqrt(rho / bb) : 0.0;
   }
+}
+
+template <bool C32>
+__global__ void __launch_bounds__(kCGThreads) cg_kernel(const CGArgs a) {
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  cg_body<C32>(a, blockIdx.x, gridDim.x, cg_smem);
+}
+
+// The corrections of several solvers in one cooperative launch: block b works
+// for solver s as its block b - blk_start[s]; each solver has its own rows,
+// barrier counter and slots, so the solvers never wait on one another.
+template <bool C32>
+__global__ void __launch_bounds__(kCGThreads) cg_batch_kernel(const CGArgs* args, const int32_t* blk_start, int n) {
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  __shared__ CGArgs sa;
+  __shared__ int s_blk, s_nb;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (blk_start[mid] <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    sa = args[lo];
+    s_blk = (int)blockIdx.x - blk_start[lo];
+    s_nb = blk_start[lo + 1] - blk_start[lo];
+  }
+  __syncthreads();
+  cg_body<C32>(sa, s_blk, (unsigned)s_nb, cg_smem);
+}
+
+cudaError_t launch_cg_batch(const CGArgs* args, const int32_t* blk_start, int n, bool coarse32, int grid,
+                            int threads, size_t smem, cudaStream_t st) {
+  if (n < 1) return cudaSuccess;
+  if (grid < 1 || threads < 128 || threads > kCGThreads || threads % 32 != 0) return cudaErrorInvalidConfiguration;
+  auto kern = coarse32 ? cg_batch_kernel<true> : cg_batch_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args, blk_start, n);
 }
 
 cudaError_t launch_cg(const CGArgs& a, bool coarse32, int grid, int threads, size_t smem, cudaStream_t st) {

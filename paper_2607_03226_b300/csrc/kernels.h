@@ -53,6 +53,12 @@ struct SweepArgs {
 template <typename R>
 cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem,
                          cudaStream_t st);
+// work items of several solvers sharing (R, K, G, ring placement) in one
+// launch; args[s] and item_start[s] (prefix sums, n_solvers+1 entries) are
+// device arrays
+template <typename R>
+cudaError_t launch_sweep_batch(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers, int K, int G,
+                               bool global_ring, int n_items, int threads, size_t smem, cudaStream_t st);
 template <typename R>
 cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st);
 
@@ -154,6 +160,10 @@ struct CGArgs {
 };
 // persistent cooperative PCG; coarse32 selects the FP32 coarse preconditioner
 cudaError_t launch_cg(const CGArgs& a, bool coarse32, int grid, int threads, size_t smem, cudaStream_t st);
+// several solvers' corrections in one cooperative launch; args[s] and
+// blk_start[s] (prefix sums of blocks, n+1 entries) are device arrays
+cudaError_t launch_cg_batch(const CGArgs* args, const int32_t* blk_start, int n, bool coarse32, int grid,
+                            int threads, size_t smem, cudaStream_t st);
 
 // dynamic shared memory of the CG kernel (byte offsets, 16-byte aligned)
 struct CgSmem {

@@ -166,20 +166,19 @@ struct RecField<double> {
 
 }  // namespace
 
+// One work item (direction i, band group g) of one solver; the whole CTA.
 template <typename R, int K, int G, bool GR>
-__global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
-  extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item, unsigned char* smem) {
   const int NS = a.n_stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + NS;
   Chunk* meta = reinterpret_cast<Chunk*>(smem + 16 * NS);
-  R* ring = GR ? a.gring + (size_t)blockIdx.x * (size_t)a.gring_stride : reinterpret_cast<R*>(smem + a.off_ring);
+  R* ring = GR ? a.gring + (size_t)item * (size_t)a.gring_stride : reinterpret_cast<R*>(smem + a.off_ring);
   unsigned char* stages = smem + a.off_stage;
   constexpr RecLayout RL = rec_layout((int)sizeof(R), K);
   constexpr int NQ = RL.size / 16;
   constexpr int GP = padded_group(G, (int)sizeof(R));   // row length of the import/export tables
 
-  const int item = blockIdx.x + a.item0;
   const int i = a.item_dir[item];
   const int g = a.item_grp[item];
   const int ncons = blockDim.x - 32;
@@ -346,6 +345,36 @@ __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
 }
 
 template <typename R, int K, int G, bool GR>
+__global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  sweep_item<R, K, G, GR>(a, blockIdx.x + a.item0, smem);
+}
+
+// Work items of several solvers in one launch: block b runs item
+// b - item_start[s] of solver s, item_start[s] <= b < item_start[s+1].  The
+// solvers share (R, K, G, ring placement); each brings its own tables, value
+// rings and shared-memory layout (the launch takes the largest).
+template <typename R, int K, int G, bool GR>
+__global__ void __launch_bounds__(544) sweep_batch_kernel(const SweepArgs<R>* args, const int32_t* item_start,
+                                                          int n_solvers) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ SweepArgs<R> sa;
+  __shared__ int s_item;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n_solvers - 1;
+    while (lo < hi) {   // last solver whose first item is <= blockIdx.x
+      const int mid = (lo + hi + 1) / 2;
+      if (item_start[mid] <= (int)blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    sa = args[lo];
+    s_item = (int)blockIdx.x - item_start[lo];
+  }
+  __syncthreads();
+  sweep_item<R, K, G, GR>(sa, s_item, smem);
+}
+
+template <typename R, int K, int G, bool GR>
 static cudaError_t launch_one(const SweepArgs<R>& a, int n_items, int threads, size_t smem, cudaStream_t st) {
   auto kern = sweep_kernel<R, K, G, GR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -381,6 +410,49 @@ static cudaError_t launch_gr(const SweepArgs<R>& a, int K, int G, int n_items, i
   }
 }
 
+template <typename R, int K, int G, bool GR>
+static cudaError_t launch_batch_one(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers,
+                                    int n_items, int threads, size_t smem, cudaStream_t st) {
+  auto kern = sweep_batch_kernel<R, K, G, GR>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<n_items, threads, smem, st>>>(args, item_start, n_solvers);
+  return cudaGetLastError();
+}
+
+template <typename R, int K, bool GR>
+static cudaError_t launch_batch_k(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers, int G,
+                                  int n_items, int threads, size_t smem, cudaStream_t st) {
+  switch (G) {
+    case 1: return launch_batch_one<R, K, 1, GR>(args, item_start, n_solvers, n_items, threads, smem, st);
+    case 2: return launch_batch_one<R, K, 2, GR>(args, item_start, n_solvers, n_items, threads, smem, st);
+    case 4: return launch_batch_one<R, K, 4, GR>(args, item_start, n_solvers, n_items, threads, smem, st);
+    case 8:
+      if constexpr (sizeof(R) == 4)
+        return launch_batch_one<R, K, 8, GR>(args, item_start, n_solvers, n_items, threads, smem, st);
+      return cudaErrorInvalidConfiguration;
+    default:
+      return cudaErrorInvalidConfiguration;
+  }
+}
+
+template <typename R>
+cudaError_t launch_sweep_batch(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers, int K, int G,
+                               bool global_ring, int n_items, int threads, size_t smem, cudaStream_t st) {
+  if (n_solvers < 1 || n_items < 1) return cudaSuccess;
+#define NBTE_BK(Kv)                                                                                            \
+  case Kv:                                                                                                     \
+    return global_ring                                                                                         \
+               ? launch_batch_k<R, Kv, true>(args, item_start, n_solvers, G, n_items, threads, smem, st)      \
+               : launch_batch_k<R, Kv, false>(args, item_start, n_solvers, G, n_items, threads, smem, st);
+  switch (K) {
+    NBTE_BK(1) NBTE_BK(2) NBTE_BK(3) NBTE_BK(4) NBTE_BK(5)
+    default:
+      return cudaErrorInvalidConfiguration;
+  }
+#undef NBTE_BK
+}
+
 template <typename R>
 cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
   return a.gring ? launch_gr<R, true>(a, K, G, n_items, threads, smem, st)
@@ -405,6 +477,10 @@ cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, in
 }
 
 template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_sweep_batch<float>(const SweepArgs<float>*, const int32_t*, int, int, int, bool, int, int,
+                                               size_t, cudaStream_t);
+template cudaError_t launch_sweep_batch<double>(const SweepArgs<double>*, const int32_t*, int, int, int, bool, int,
+                                                int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, int, int, size_t, cudaStream_t);
 template cudaError_t launch_gather_tq<float>(float*, const int32_t*, const float*, int64_t, cudaStream_t);
 template cudaError_t launch_gather_tq<double>(double*, const int32_t*, const double*, int64_t, cudaStream_t);

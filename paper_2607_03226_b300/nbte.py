@@ -37,7 +37,7 @@ EXPORTS = [
     "nbte_solver_set_stream", "nbte_set_bands", "nbte_set_quadrature", "nbte_set_boundaries",
     "nbte_set_heat_source", "nbte_default_opts", "nbte_solve_steady", "nbte_get_temperature",
     "nbte_get_heat_flux", "nbte_get_wall_heat", "nbte_plan_stats", "nbte_last_error", "nbte_version",
-    "nbte_laplacian_solve_noalloc", "nbte_get_distribution",
+    "nbte_laplacian_solve_noalloc", "nbte_get_distribution", "nbte_solve_batch",
 ]
 
 
@@ -57,7 +57,8 @@ class nbte_solve_opts(C.Structure):
 class nbte_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("residual", C.c_double), ("energy_imbalance", C.c_double),
                 ("lagged_faces", C.c_int64), ("seconds", C.c_double), ("cg_iterations", C.c_int64),
-                ("sweep_seconds", C.c_double), ("sweep_launches", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("sweep_seconds", C.c_double), ("sweep_launches", C.c_int64), ("kernel_launches", C.c_int64),
+                ("status", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -103,6 +104,8 @@ def load(path: str | None = None):
         "nbte_get_heat_flux": ([_P, _D], C.c_int),
         "nbte_get_wall_heat": ([_P, C.c_int32, _D], C.c_int),
         "nbte_get_distribution": ([_P, C.c_int32, C.c_int32, _D], C.c_int),
+        "nbte_solve_batch": ([C.POINTER(_P), C.c_int32, C.POINTER(nbte_solve_opts), C.POINTER(nbte_solve_info)],
+                             C.c_int),
         "nbte_plan_stats": ([_P, C.POINTER(nbte_solve_opts), _I64], C.c_int),
         "nbte_last_error": ([], C.c_char_p),
         "nbte_version": ([], C.c_char_p),
@@ -233,6 +236,22 @@ def nbte_solve_steady(solver, opts):
     rc = _check(load().nbte_solve_steady(solver, C.byref(opts), C.byref(info)),
                 allow=(NBTE_ERR_NOT_CONVERGED,))
     return rc, info
+
+
+def nbte_solve_batch(solvers, opts):
+    """Solve several solvers together; returns (rc, [info per solver])."""
+    n = len(solvers)
+    arr = (_P * n)(*solvers)
+    infos = (nbte_solve_info * n)()
+    rc = _check(load().nbte_solve_batch(arr, n, C.byref(opts), infos), allow=(NBTE_ERR_NOT_CONVERGED,))
+    return rc, list(infos)
+
+
+def solve_batch(solvers, **kw):
+    """Solve several :class:`Solver` objects together (one options set);
+    returns the per-solver info dicts."""
+    rc, infos = nbte_solve_batch([s.solver for s in solvers], make_opts(**kw))
+    return [i.as_dict() for i in infos]
 
 
 def nbte_get_temperature(solver, kind, n_cells):

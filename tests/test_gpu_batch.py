@@ -1,0 +1,75 @@
+"""Batched solves (nbte_solve_batch): several independent problems of
+different meshes, band counts and heat loads iterated together, with fused
+sweep launches and one cooperative CG launch.  Each result must equal the
+same problem solved alone: bitwise for the temperature after sequential
+iterations (the sweep and update arithmetic is the same per work item; the
+heat flux is accumulated with atomics and agrees to rounding), within the stated tolerances
+for converged synthetic solves (the CG's block share differs, which changes
+only its rounding): FP64 temperature 1e-9, FP32 sweep 2e-6 (twice the FP32
+bound, both sides carrying it)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from cases import CASES, rel_T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nbte_mod(gpu_lib):
+    from paper_2607_03226_b300 import nbte
+    return nbte
+
+
+def _problems():
+    out = [CASES[n]() for n in ("square_mixed", "fin2d_mixed", "fin3d_tets", "cube_hex")]
+    hot = CASES["fin2d_mixed"]()
+    hot.Q = None if hot.Q is None else 3.0 * hot.Q
+    out.append(hot)
+    out.append(W.problems.finfet2d(h=4e-9, B=6, n_pol_half=2, n_az=8))
+    return out
+
+
+def test_batch_sequential_iterations_bitwise(nbte_mod):
+    """Fixed layout on both sides (the autotuner's timing-based choice could
+    differ between the two solver objects and with it the summation order)."""
+    probs = _problems()
+    alone = []
+    for p in probs:
+        s = nbte_mod.Solver(p)
+        s.solve(scheme="sequential", precision="fp64", n_iter=3, band_group=2, cta_threads=160)
+        alone.append((s.temperature(0), s.heat_flux()))
+        s.close()
+    ss = [nbte_mod.Solver(p) for p in probs]
+    infos = nbte_mod.solve_batch(ss, scheme="sequential", precision="fp64", n_iter=3, band_group=2,
+                                 cta_threads=160)
+    for s, (T, q), info in zip(ss, alone, infos):
+        assert info["iterations"] == 3 and info["status"] == 0
+        assert np.array_equal(s.temperature(0), T)
+        # q is accumulated with FP64 atomics over directions: order-dependent rounding
+        assert np.abs(s.heat_flux() - q).max() <= 1e-12 * np.abs(q).max()
+        s.close()
+
+
+@pytest.mark.parametrize("precision,tol,use_graph", [("fp64", 1e-9, False), ("fp64", 1e-9, True),
+                                                     ("fp32", 2e-6, True)])
+def test_batch_converged_same_as_alone(nbte_mod, precision, tol, use_graph):
+    probs = _problems()
+    kw = dict(scheme="synthetic", precision=precision, tol=1e-12 if precision == "fp64" else 1e-9,
+              max_iter=20000, use_graph=use_graph)
+    alone = []
+    for p in probs:
+        s = nbte_mod.Solver(p)
+        info = s.solve(**kw)
+        assert info["status"] == 0
+        alone.append((s.temperature(0), info["iterations"]))
+        s.close()
+    ss = [nbte_mod.Solver(p) for p in probs]
+    infos = nbte_mod.solve_batch(ss, **kw)
+    for p, s, (T, it), info in zip(probs, ss, alone, infos):
+        assert info["status"] == 0
+        err = rel_T(s.temperature(0), T, p.T_ref)
+        print(f"{p.name}: alone {it} iterations, in the batch {info['iterations']}, T difference {err:.2e}")
+        assert err < tol
+        s.close()
