@@ -272,6 +272,44 @@ int nbte_get_distribution(nbte_solver* solver, int32_t direction, int32_t band, 
  * nbte_solve_opts), so the layout reported is the one a solve will use.     */
 int nbte_plan_stats(nbte_solver* solver, const nbte_solve_opts* opts, int64_t stats[12]);
 
+/* ------------------------------------------------------------- serving ----
+ * A request queue in front of the batched iteration (continuous batching).
+ * Submitted solves are planned on host threads (n_planners), admitted to the
+ * device in arrival order while their estimated device memory fits
+ * budget_bytes (0 = 80% of the free device memory at creation; a solve larger
+ * than the budget runs alone), and iterated together with every admitted
+ * solve as in nbte_solve_batch, at most max_active (1..148) at a time.
+ * Arrivals join and converged solves leave between iterations.  Every
+ * request uses opts (T_init NULL, profile 0; band_group / cta_threads 0 take
+ * the planner's heuristic layout, not the autotuner).  The device is the
+ * caller's current device at creation.
+ *
+ * A submitted solver (mesh, bands, quadrature, boundaries, heat source set)
+ * stays owned by the caller, who must not use or destroy it until the
+ * request is done.  When done, its results are readable as after
+ * nbte_solve_steady (temperature, flux, wall heat); the device memory the
+ * iteration held is released (nbte_get_distribution then reports
+ * NBTE_ERR_STATE until the solver is solved again).                         */
+typedef struct nbte_server nbte_server;
+int nbte_server_create(const nbte_solve_opts* opts, size_t budget_bytes, int32_t max_active, int32_t n_planners,
+                       nbte_server** out);
+/* Queue a solve; *request receives its id.  NBTE_ERR_STATE if the solver is
+ * not fully set up or already queued.                                       */
+int nbte_server_submit(nbte_server* server, nbte_solver* solver, int64_t* request);
+/* *state: 0 queued, 1 planned, 2 running, 3 done.  When done, returns the
+ * solve's status, fills info (may be NULL) and seconds[0] = submit-to-done,
+ * seconds[1] = submit-to-admission (seconds may be NULL).                   */
+int nbte_server_poll(nbte_server* server, int64_t request, int32_t* state, nbte_solve_info* info,
+                     double* seconds);
+/* Block until every submitted request is done (timeout_s <= 0: no limit;
+ * NBTE_ERR_NOT_CONVERGED when the timeout passes first).                    */
+int nbte_server_drain(nbte_server* server, double timeout_s);
+/* stats[0] batched iterations run, [1] requests submitted, [2] done,
+ * [3] estimated device bytes held by admitted requests.                     */
+int nbte_server_stats(nbte_server* server, int64_t stats[4]);
+/* Stops the threads; requests not yet done are abandoned.                   */
+int nbte_server_destroy(nbte_server* server);
+
 /* --------------------------------------------------- allocation-free solve --
  * nbte_laplacian_solve_noalloc: solve A x = rhs for a sparse symmetric
  * positive-definite A by Jacobi-preconditioned conjugate gradients, without

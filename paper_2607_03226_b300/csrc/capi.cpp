@@ -8,11 +8,13 @@
 
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
 #include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -346,7 +348,11 @@ bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 int64_t tune_key(const nbte_solver* S) { return S->plan_built * 1000003 + S->version_bands; }
 
 // ------------------------------------------------------------------ layout
-int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
+// Chooses and allocates the sweep layout for options o.  With `estimate`
+// non-null nothing is allocated: *estimate receives the device bytes the
+// layout would hold (records, tables, distributions' in-flight buffers,
+// per-cell fields), for admission by memory budget.
+int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = nullptr) {
   if (S->B <= 0) return fail(NBTE_ERR_STATE, "nbte_set_bands must be called before solving");
   const int prec = o.precision;
   const int sz = prec ? 4 : 8;
@@ -431,6 +437,17 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o) {
   while (ns > 2 && total(ns) > std::min<int64_t>(budget(per_sm), kSweepSmemMax)) --ns;
   const int Bp = ng * G;
   const int threads = cap + 32;
+  if (estimate) {
+    const size_t N = (size_t)S->mesh->m.n_cells, D = (size_t)S->D, Gp = (size_t)padded_group(G, sz);
+    size_t b = D * N * (RL.size + 4 + 2 * sz);                          // records, position cells, (T', Qdot)
+    b += (size_t)D * ng * N * sz;                                        // collision partials
+    b += (size_t)ng * (S->n_exp + S->n_imp) * Gp * sz;                   // export / import rows
+    if (gr) b += (size_t)D * ng * (((size_t)(S->max_slots + 1) * G + 3) / 4 * 4) * sz;   // global rings
+    b += N * (4 * sz + 12 * 8 + 8 * (size_t)S->mesh->m.dim);            // per-cell fields
+    b += D * N / 8 + (size_t)S->n_dbf * Bp * 8 + (size_t)S->n_wf * 16;  // chunks, diffuse sums, wall heat
+    *estimate = b;
+    return NBTE_OK;
+  }
   const std::string key = std::to_string(prec) + "/" + std::to_string(G) + "/" + std::to_string(cap) + "/" +
                           std::to_string(S->version_bands) + "/" + std::to_string(S->plan_built) + "/" +
                           std::to_string(ns) + (gr ? "/global" : "/shared");
@@ -1254,10 +1271,10 @@ struct BatchTables {
 };
 
 template <typename R>
-int batch_build(BatchTables<R>& bt, std::vector<Run>& runs, const std::vector<int>& active) {
+int batch_build(BatchTables<R>& bt, const std::vector<Run*>& act) {
   bt.groups.clear();
-  for (int k : active) {
-    nbte_solver* S = runs[k].S;
+  for (int k = 0; k < (int)act.size(); ++k) {
+    nbte_solver* S = act[k]->S;
     const bool gr = S->gring_stride > 0;
     typename BatchTables<R>::SweepGroup* grp = nullptr;
     for (auto& g : bt.groups)
@@ -1275,7 +1292,7 @@ int batch_build(BatchTables<R>& bt, std::vector<Run>& runs, const std::vector<in
     std::vector<SweepArgs<R>> args;
     std::vector<int32_t> start(1, 0);
     for (int k : g.members) {
-      nbte_solver* S = runs[k].S;
+      nbte_solver* S = act[k]->S;
       args.push_back(sweep_args<R>(S, 0));
       start.push_back(start.back() + S->n_items);
       g.threads = std::max(g.threads, S->threads);
@@ -1290,20 +1307,20 @@ int batch_build(BatchTables<R>& bt, std::vector<Run>& runs, const std::vector<in
   // least one); one block per SM in all
   bt.cg_members.clear();
   bt.cg_blocks = 0;
-  for (int k : active)
-    if (runs[k].o.scheme != 0) bt.cg_members.push_back(k);
+  for (int k = 0; k < (int)act.size(); ++k)
+    if (act[k]->o.scheme != 0) bt.cg_members.push_back(k);
   if (!bt.cg_members.empty()) {
-    nbte_solver* S0 = runs[bt.cg_members[0]].S;
+    nbte_solver* S0 = act[bt.cg_members[0]]->S;
     int nsm = 1;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S0->device);
     const int n = (int)bt.cg_members.size();
     if (n > nsm) return fail(NBTE_ERR_ARG, "more synthetic solvers in one batch than SMs");
     double tot = 0;
-    for (int k : bt.cg_members) tot += (double)runs[k].S->mesh->m.n_cells;
+    for (int k : bt.cg_members) tot += (double)act[k]->S->mesh->m.n_cells;
     std::vector<int> share(n);
     int used = 0;
     for (int j = 0; j < n; ++j) {
-      nbte_solver* S = runs[bt.cg_members[j]].S;
+      nbte_solver* S = act[bt.cg_members[j]]->S;
       share[j] = std::max(1, (int)std::floor((nsm - n) * (double)S->mesh->m.n_cells / tot) + 1);
       share[j] = std::min(share[j], S->cg_Nc);
       used += share[j];
@@ -1315,16 +1332,16 @@ int batch_build(BatchTables<R>& bt, std::vector<Run>& runs, const std::vector<in
     }
     int T = 0;
     for (int j = 0; j < n; ++j) {
-      int rc = cg_partition(runs[bt.cg_members[j]].S, share[j], 0);
+      int rc = cg_partition(act[bt.cg_members[j]]->S, share[j], 0);
       if (rc) return rc;
-      T = std::max(T, runs[bt.cg_members[j]].S->cg_threads);
+      T = std::max(T, act[bt.cg_members[j]]->S->cg_threads);
     }
     std::vector<CGArgs> args;
     std::vector<int32_t> start(1, 0);
     bt.cg_smem = 0;
-    const bool c32 = coarse32(runs[bt.cg_members[0]].cg_tol);
+    const bool c32 = coarse32(act[bt.cg_members[0]]->cg_tol);
     for (int j = 0; j < n; ++j) {
-      Run& run = runs[bt.cg_members[j]];
+      Run& run = *act[bt.cg_members[j]];
       int rc = cg_partition(run.S, share[j], T);
       if (rc) return rc;
       args.push_back(cg_args(run.S, run.cg_tol, run.cg_max));
@@ -1345,27 +1362,42 @@ int batch_build(BatchTables<R>& bt, std::vector<Run>& runs, const std::vector<in
 }
 
 template <typename R>
-cudaError_t batch_enqueue(BatchTables<R>& bt, std::vector<Run>& runs, const std::vector<int>& active,
-                          cudaStream_t st) {
-  const int scheme = runs[active[0]].o.scheme;
+cudaError_t batch_enqueue(BatchTables<R>& bt, const std::vector<Run*>& act, cudaStream_t st) {
+  const int scheme = act[0]->o.scheme;
   cudaError_t e;
-  for (int k : active)
-    if ((e = enqueue_pre<R>(runs[k].S, st)) != cudaSuccess) return e;
+  for (Run* run : act)
+    if ((e = enqueue_pre<R>(run->S, st)) != cudaSuccess) return e;
   for (auto& g : bt.groups) {
     e = launch_sweep_batch<R>(g.args.template as<SweepArgs<R>>(), g.start.template as<int32_t>(), (int)g.members.size(), g.K, g.G,
                               g.gr, g.items, g.threads, g.smem, st);
     if (e != cudaSuccess) return e;
   }
-  for (int k : active)
-    if ((e = enqueue_mid<R>(runs[k].S, scheme, st)) != cudaSuccess) return e;
+  for (Run* run : act)
+    if ((e = enqueue_mid<R>(run->S, scheme, st)) != cudaSuccess) return e;
   if (!bt.cg_members.empty()) {
-    e = launch_cg_batch(bt.cg_args_d.template as<CGArgs>(), bt.cg_start_d.template as<int32_t>(), (int)bt.cg_members.size(),
-                        coarse32(runs[bt.cg_members[0]].cg_tol), bt.cg_blocks, bt.cg_threads, bt.cg_smem, st);
+    e = launch_cg_batch(bt.cg_args_d.template as<CGArgs>(), bt.cg_start_d.template as<int32_t>(),
+                        (int)bt.cg_members.size(), coarse32(act[bt.cg_members[0]]->cg_tol), bt.cg_blocks,
+                        bt.cg_threads, bt.cg_smem, st);
     if (e != cudaSuccess) return e;
   }
-  for (int k : active)
-    if ((e = enqueue_post<R>(runs[k].S, scheme, st)) != cudaSuccess) return e;
+  for (Run* run : act)
+    if ((e = enqueue_post<R>(run->S, scheme, st)) != cudaSuccess) return e;
   return cudaSuccess;
+}
+
+// capture one batched iteration of the active set into bt.graph (left null
+// if capture fails; the caller then enqueues directly)
+template <typename R>
+void batch_capture(BatchTables<R>& bt, const std::vector<Run*>& act, cudaStream_t st) {
+  cudaGraph_t gr = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    cudaError_t e = batch_enqueue<R>(bt, act, st);
+    cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+    if (!(e == cudaSuccess && e2 == cudaSuccess && gr && cudaGraphInstantiate(&bt.graph, gr, 0) == cudaSuccess))
+      bt.graph = nullptr;
+    if (gr) cudaGraphDestroy(gr);
+  }
+  cudaGetLastError();   // clear a failed capture
 }
 
 // Several solvers iterated together until each stops (see nbte_solve_batch).
@@ -1379,37 +1411,26 @@ int run_batch(const std::vector<nbte_solver*>& Ss, const nbte_solve_opts& o, nbt
     if (rc) return rc;
     NBTE_CK(cudaStreamSynchronize(Ss[k]->stream));
   }
-  std::vector<int> active(n);
-  for (int k = 0; k < n; ++k) active[k] = k;
+  std::vector<Run*> active(n);
+  for (int k = 0; k < n; ++k) active[k] = &runs[k];
   BatchTables<R> bt;
   bool rebuild = true;
   while (!active.empty()) {
     if (rebuild) {
-      int rc = batch_build<R>(bt, runs, active);
+      int rc = batch_build<R>(bt, active);
       if (rc) return rc;
       rebuild = false;
-      if (o.use_graph) {
-        cudaGraph_t gr = nullptr;
-        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-          cudaError_t e = batch_enqueue<R>(bt, runs, active, st);
-          cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-          if (!(e == cudaSuccess && e2 == cudaSuccess && gr && cudaGraphInstantiate(&bt.graph, gr, 0) == cudaSuccess))
-            bt.graph = nullptr;
-          if (gr) cudaGraphDestroy(gr);
-        }
-        cudaGetLastError();   // clear a failed capture
-      }
+      if (o.use_graph) batch_capture<R>(bt, active, st);
     }
     if (bt.graph) NBTE_CK(cudaGraphLaunch(bt.graph, st));
-    else NBTE_CK(batch_enqueue<R>(bt, runs, active, st));
+    else NBTE_CK(batch_enqueue<R>(bt, active, st));
     NBTE_CK(cudaStreamSynchronize(st));
-    std::vector<int> still;
-    for (int k : active) {
-      Run& run = runs[k];
-      ++run.it;
-      run.kernels += run.kernels_per_iter();
-      if (run.check()) rebuild = true;
-      else still.push_back(k);
+    std::vector<Run*> still;
+    for (Run* run : active) {
+      ++run->it;
+      run->kernels += run->kernels_per_iter();
+      if (run->check()) rebuild = true;
+      else still.push_back(run);
     }
     active.swap(still);
   }
@@ -1421,7 +1442,219 @@ int run_batch(const std::vector<nbte_solver*>& Ss, const nbte_solve_opts& o, nbt
   return status;
 }
 
+// the solver's device (the caller's current one), stream and pinned words
+int ensure_device(nbte_solver* S) {
+  if (S->device < 0) {
+    NBTE_CK(cudaGetDevice(&S->device));
+  }
+  if (!S->own_stream) {
+    DeviceGuard g(S->device);
+    NBTE_CK(cudaStreamCreateWithFlags(&S->own_stream, cudaStreamNonBlocking));
+    if (!S->stream) S->stream = S->own_stream;
+    NBTE_CK(cudaMallocHost(&S->h_res, 32));
+    NBTE_CK(cudaMallocHost(&S->h_misc, 16));
+    S->h_misc[0] = 0;
+  }
+  return NBTE_OK;
+}
+
+// Device memory of the synthetic correction (estimate, before its setup).
+size_t estimate_cg_bytes(const nbte_solver* S) {
+  const size_t N = (size_t)S->mesh->m.n_cells, W = (size_t)S->mesh->m.nfc;
+  const size_t Nc = std::min<size_t>(kMaxCoarse, std::max<size_t>(1, N <= 4096 ? N / 16 : std::min<size_t>(1536, N / 32)));
+  const size_t Nc4 = (Nc + 3) / 4 * 4;
+  return N * (W * 12 + 8 * 8 + 3 * 4) + Nc * Nc4 * 12 + Nc * 48;
+}
+
+// After a served solve: keep what the result getters read (T, the kinetic
+// temperature, energy/flux moments, wall heat) and free everything the
+// iteration held, so finished requests do not occupy the server's budget.
+void shrink(nbte_solver* S) {
+  DeviceGuard g(S->device);
+  drop_graph(S);
+  DBuf* big[] = {&S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->chunks, &S->chunk_off, &S->tqp,
+                 &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part, &S->Tprev, &S->Delta, &S->rhs,
+                 &S->delta, &S->dsum, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s, &S->cg_w, &S->cg_x, &S->cg_xw,
+                 &S->cg_rw, &S->cg_rcx, &S->cg_scx, &S->cg_Ainv, &S->cg_Ainv64, &S->L_ecol, &S->L_eval,
+                 &S->L_diag, &S->L_dinv, &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell,
+                 &S->cg_blk_agg, &S->cg_slots};
+  for (DBuf* b : big) b->release();
+  S->layout_key.clear();
+  S->rec_key.clear();
+  S->chunk_key.clear();
+  S->lap_built = -1;
+  S->cg_part_key = -1;
+  S->have_state = false;
+}
+
 }  // namespace
+
+// ------------------------------------------------------------------ serving
+// A request queue in front of the batched iteration.  Submitted solves are
+// planned on host threads, admitted to the device while their estimated
+// memory fits the budget, and iterated together with every other admitted
+// solve; arrivals join and converged solves leave between iterations.
+struct ServedSolve {
+  int64_t id = 0;
+  nbte_solver* S = nullptr;
+  int state = 0;   // 0 queued, 1 planned, 2 running, 3 done
+  size_t bytes = 0;
+  int status = NBTE_OK;
+  nbte_solve_info info{};
+  Run run;
+  std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
+};
+
+struct nbte_server {
+  nbte_solve_opts opts{};
+  int device = 0;
+  size_t budget = 0, used = 0;
+  int max_active = 64;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<ServedSolve*> to_plan, planned;
+  std::map<int64_t, std::unique_ptr<ServedSolve>> all;
+  int64_t next_id = 1;
+  bool stop = false;
+  std::vector<std::thread> planners;
+  std::thread worker;
+  int64_t iterations = 0;   // batched iterations run
+
+  void plan_loop();
+  template <typename R>
+  void work_loop();
+};
+
+void nbte_server::plan_loop() {
+  cudaSetDevice(device);
+  while (true) {
+    ServedSolve* q = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_work.wait(lk, [&] { return stop || !to_plan.empty(); });
+      if (stop) return;
+      q = to_plan.front();
+      to_plan.pop_front();
+    }
+    nbte_solver* S = q->S;
+    S->device = device;
+    int rc = ensure_device(S);
+    if (!rc) rc = ensure_plan(S);
+    size_t b = 0;
+    if (!rc) rc = ensure_layout(S, opts, &b);
+    if (!rc && opts.scheme != 0) {
+      b += estimate_cg_bytes(S);
+      rc = ensure_laplacian(S);   // host-heavy (aggregation, dense coarse inverse): off the GPU loop
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (rc) {
+      q->status = rc;
+      q->info.status = rc;
+      q->state = 3;
+      q->t_done = std::chrono::steady_clock::now();
+      cv_done.notify_all();
+    } else {
+      q->bytes = b;
+      q->state = 1;
+      planned.push_back(q);
+      cv_work.notify_all();
+    }
+  }
+}
+
+template <typename R>
+void nbte_server::work_loop() {
+  cudaSetDevice(device);
+  std::vector<ServedSolve*> active;
+  BatchTables<R> bt;
+  bool rebuild = true;
+  while (true) {
+    std::vector<ServedSolve*> admit;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      if (active.empty())
+        cv_work.wait(lk, [&] { return stop || !planned.empty(); });
+      if (stop) return;
+      // admission in arrival order while the estimated memory fits (a solve
+      // larger than the whole budget runs alone)
+      while (!planned.empty() && (int)(active.size() + admit.size()) < max_active) {
+        ServedSolve* q = planned.front();
+        if (used + q->bytes > budget && !(active.empty() && admit.empty())) break;
+        planned.pop_front();
+        used += q->bytes;
+        q->state = 2;
+        q->t_admit = std::chrono::steady_clock::now();
+        admit.push_back(q);
+      }
+    }
+    for (ServedSolve* q : admit) {
+      DeviceGuard g(q->S->device);
+      int rc = ensure_layout(q->S, opts);
+      if (!rc) rc = ensure_q(q->S);
+      if (!rc) rc = run_begin<R>(q->run, q->S, opts);
+      if (!rc) rc = cudaStreamSynchronize(q->S->stream) == cudaSuccess ? NBTE_OK : NBTE_ERR_CUDA;
+      if (rc) {
+        shrink(q->S);
+        std::lock_guard<std::mutex> lk(mu);
+        used -= q->bytes;
+        q->status = rc;
+        q->info.status = rc;
+        q->state = 3;
+        q->t_done = std::chrono::steady_clock::now();
+        cv_done.notify_all();
+        continue;
+      }
+      active.push_back(q);
+      rebuild = true;
+    }
+    if (active.empty()) continue;
+    std::vector<Run*> act;
+    for (ServedSolve* q : active) act.push_back(&q->run);
+    if (rebuild) {
+      if (batch_build<R>(bt, act) != NBTE_OK) {
+        for (ServedSolve* q : active) q->run.status = NBTE_ERR_ARG;
+      } else {
+        rebuild = false;
+        if (opts.use_graph) batch_capture<R>(bt, act, stream);
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    if (rebuild) {
+      e = cudaErrorInvalidValue;
+    } else if (bt.graph) {
+      e = cudaGraphLaunch(bt.graph, stream);
+    } else {
+      e = batch_enqueue<R>(bt, act, stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    ++iterations;
+    std::vector<ServedSolve*> still, finished;
+    for (ServedSolve* q : active) {
+      Run& run = q->run;
+      bool stop_it = true;
+      if (e == cudaSuccess && run.status == NBTE_OK) {
+        ++run.it;
+        run.kernels += run.kernels_per_iter();
+        stop_it = run.check();
+      } else if (run.status == NBTE_OK) {
+        run.status = fail(NBTE_ERR_CUDA, std::string("CUDA error in a served iteration: ") + cudaGetErrorString(e));
+      }
+      (stop_it ? finished : still).push_back(q);
+    }
+    for (ServedSolve* q : finished) {
+      q->status = run_finish<R>(q->run, &q->info);
+      shrink(q->S);
+      std::lock_guard<std::mutex> lk(mu);
+      used -= q->bytes;
+      q->state = 3;
+      q->t_done = std::chrono::steady_clock::now();
+      rebuild = true;
+    }
+    if (!finished.empty()) cv_done.notify_all();
+    active.swap(still);
+  }
+}
 
 // ============================================================================ C ABI
 extern "C" {
@@ -1478,20 +1711,6 @@ int nbte_solver_create(const nbte_mesh* mesh, double T_ref, nbte_solver** out) {
   return NBTE_OK;
 }
 
-static int ensure_device(nbte_solver* S) {
-  if (S->device < 0) {
-    NBTE_CK(cudaGetDevice(&S->device));
-  }
-  if (!S->own_stream) {
-    DeviceGuard g(S->device);
-    NBTE_CK(cudaStreamCreateWithFlags(&S->own_stream, cudaStreamNonBlocking));
-    if (!S->stream) S->stream = S->own_stream;
-    NBTE_CK(cudaMallocHost(&S->h_res, 32));
-    NBTE_CK(cudaMallocHost(&S->h_misc, 16));
-    S->h_misc[0] = 0;
-  }
-  return NBTE_OK;
-}
 
 int nbte_solver_destroy(nbte_solver* solver) {
   if (!solver) return NBTE_OK;
@@ -1818,4 +2037,122 @@ int nbte_get_wall_heat(const nbte_solver* S, int32_t tag, double* out) {
   return NBTE_OK;
 }
 
+// ---------------------------------------------------------------- serving
+int nbte_server_create(const nbte_solve_opts* opts, size_t budget_bytes, int32_t max_active, int32_t n_planners,
+                       nbte_server** out) {
+  if (!out) return fail(NBTE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  nbte_solve_opts o;
+  nbte_default_opts(&o);
+  if (opts) o = *opts;
+  int rc = check_opts(o);
+  if (rc) return rc;
+  if (o.T_init) return fail(NBTE_ERR_ARG, "T_init is not supported by the server");
+  if (o.profile) return fail(NBTE_ERR_ARG, "profile is not supported by the server");
+  if (max_active < 1 || max_active > 148) return fail(NBTE_ERR_ARG, "max_active must be in [1, 148]");
+  if (n_planners < 1 || n_planners > 64) return fail(NBTE_ERR_ARG, "n_planners must be in [1, 64]");
+  std::unique_ptr<nbte_server> srv(new (std::nothrow) nbte_server());
+  if (!srv) return fail(NBTE_ERR_OOM, "host allocation failed");
+  srv->opts = o;
+  NBTE_CK(cudaGetDevice(&srv->device));
+  if (budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    NBTE_CK(cudaMemGetInfo(&fr, &tot));
+    budget_bytes = fr / 10 * 8;
+  }
+  srv->budget = budget_bytes;
+  srv->max_active = max_active;
+  NBTE_CK(cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking));
+  nbte_server* p = srv.get();
+  for (int k = 0; k < n_planners; ++k) p->planners.emplace_back([p] { p->plan_loop(); });
+  if (o.precision) p->worker = std::thread([p] { p->work_loop<float>(); });
+  else p->worker = std::thread([p] { p->work_loop<double>(); });
+  *out = srv.release();
+  return NBTE_OK;
+}
+
+int nbte_server_submit(nbte_server* srv, nbte_solver* solver, int64_t* request) {
+  if (!srv || !solver || !request) return fail(NBTE_ERR_ARG, "null argument");
+  if (solver->B <= 0 || solver->D <= 0 || !solver->bcs_set)
+    return fail(NBTE_ERR_STATE, "bands, quadrature and boundaries must be set before submitting");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  for (auto& kv : srv->all)
+    if (kv.second->S == solver && kv.second->state != 3) return fail(NBTE_ERR_STATE, "solver already submitted");
+  std::unique_ptr<ServedSolve> q(new ServedSolve());
+  q->id = srv->next_id++;
+  q->S = solver;
+  q->t_submit = std::chrono::steady_clock::now();
+  *request = q->id;
+  srv->to_plan.push_back(q.get());
+  srv->all[q->id] = std::move(q);
+  srv->cv_work.notify_all();
+  return NBTE_OK;
+}
+
+int nbte_server_poll(nbte_server* srv, int64_t request, int32_t* state, nbte_solve_info* info, double* seconds) {
+  if (!srv || !state) return fail(NBTE_ERR_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->all.find(request);
+  if (it == srv->all.end()) return fail(NBTE_ERR_ARG, "unknown request");
+  const ServedSolve& q = *it->second;
+  *state = q.state;
+  if (q.state == 3) {
+    if (info) *info = q.info;
+    if (seconds) {
+      seconds[0] = std::chrono::duration<double>(q.t_done - q.t_submit).count();
+      seconds[1] = q.t_admit.time_since_epoch().count() ? std::chrono::duration<double>(q.t_admit - q.t_submit).count()
+                                                        : seconds[0];
+    }
+    return q.status;
+  }
+  return NBTE_OK;
+}
+
+int nbte_server_drain(nbte_server* srv, double timeout_s) {
+  if (!srv) return fail(NBTE_ERR_ARG, "null argument");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto done = [&] {
+    for (auto& kv : srv->all)
+      if (kv.second->state != 3) return false;
+    return true;
+  };
+  if (timeout_s > 0) {
+    if (!srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), done))
+      return fail(NBTE_ERR_NOT_CONVERGED, "requests still running after the timeout");
+  } else {
+    srv->cv_done.wait(lk, done);
+  }
+  return NBTE_OK;
+}
+
+int nbte_server_stats(nbte_server* srv, int64_t stats[4]) {
+  if (!srv || !stats) return fail(NBTE_ERR_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  int64_t done = 0;
+  for (auto& kv : srv->all) done += kv.second->state == 3;
+  stats[0] = srv->iterations;
+  stats[1] = (int64_t)srv->all.size();
+  stats[2] = done;
+  stats[3] = (int64_t)srv->used;
+  return NBTE_OK;
+}
+
+int nbte_server_destroy(nbte_server* srv) {
+  if (!srv) return NBTE_OK;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_work.notify_all();
+  for (auto& t : srv->planners) t.join();
+  if (srv->worker.joinable()) srv->worker.join();
+  if (srv->stream) {
+    cudaStreamSynchronize(srv->stream);
+    cudaStreamDestroy(srv->stream);
+  }
+  delete srv;
+  return NBTE_OK;
+}
+
 }  // extern "C"
+

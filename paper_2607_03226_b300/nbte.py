@@ -37,7 +37,8 @@ EXPORTS = [
     "nbte_solver_set_stream", "nbte_set_bands", "nbte_set_quadrature", "nbte_set_boundaries",
     "nbte_set_heat_source", "nbte_default_opts", "nbte_solve_steady", "nbte_get_temperature",
     "nbte_get_heat_flux", "nbte_get_wall_heat", "nbte_plan_stats", "nbte_last_error", "nbte_version",
-    "nbte_laplacian_solve_noalloc", "nbte_get_distribution", "nbte_solve_batch",
+    "nbte_laplacian_solve_noalloc", "nbte_get_distribution", "nbte_solve_batch", "nbte_server_create",
+    "nbte_server_submit", "nbte_server_poll", "nbte_server_drain", "nbte_server_stats", "nbte_server_destroy",
 ]
 
 
@@ -106,6 +107,12 @@ def load(path: str | None = None):
         "nbte_get_distribution": ([_P, C.c_int32, C.c_int32, _D], C.c_int),
         "nbte_solve_batch": ([C.POINTER(_P), C.c_int32, C.POINTER(nbte_solve_opts), C.POINTER(nbte_solve_info)],
                              C.c_int),
+        "nbte_server_create": ([C.POINTER(nbte_solve_opts), C.c_size_t, C.c_int32, C.c_int32, C.POINTER(_P)], C.c_int),
+        "nbte_server_submit": ([_P, _P, _I64], C.c_int),
+        "nbte_server_poll": ([_P, C.c_int64, _I32, C.POINTER(nbte_solve_info), _D], C.c_int),
+        "nbte_server_drain": ([_P, C.c_double], C.c_int),
+        "nbte_server_stats": ([_P, _I64], C.c_int),
+        "nbte_server_destroy": ([_P], C.c_int),
         "nbte_plan_stats": ([_P, C.POINTER(nbte_solve_opts), _I64], C.c_int),
         "nbte_last_error": ([], C.c_char_p),
         "nbte_version": ([], C.c_char_p),
@@ -252,6 +259,56 @@ def solve_batch(solvers, **kw):
     returns the per-solver info dicts."""
     rc, infos = nbte_solve_batch([s.solver for s in solvers], make_opts(**kw))
     return [i.as_dict() for i in infos]
+
+
+class Server:
+    """Continuous-batching request queue (nbte_server_*): submit set-up
+    :class:`Solver` objects, poll or drain, read results from the solvers."""
+
+    def __init__(self, budget_bytes=0, max_active=64, n_planners=2, **opts):
+        self._opts = make_opts(**opts)
+        h = _P()
+        _check(load().nbte_server_create(C.byref(self._opts), int(budget_bytes), int(max_active), int(n_planners),
+                                         C.byref(h)))
+        self.server = h
+
+    def submit(self, solver):
+        rid = C.c_int64()
+        _check(load().nbte_server_submit(self.server, solver.solver, C.byref(rid)))
+        return rid.value
+
+    def poll(self, request):
+        """None while queued or running, else (info dict, seconds submit-to-done,
+        seconds submit-to-admission)."""
+        state = C.c_int32()
+        info = nbte_solve_info()
+        sec = (C.c_double * 2)()
+        rc = load().nbte_server_poll(self.server, int(request), C.byref(state), C.byref(info), sec)
+        if state.value != 3:
+            _check(rc)
+            return None
+        d = info.as_dict()
+        d["status"] = rc
+        return d, sec[0], sec[1]
+
+    def drain(self, timeout_s=0.0):
+        _check(load().nbte_server_drain(self.server, float(timeout_s)))
+
+    def stats(self):
+        st = np.zeros(4, dtype=np.int64)
+        _check(load().nbte_server_stats(self.server, st.ctypes.data_as(_I64)))
+        return dict(zip(["iterations", "submitted", "done", "bytes_in_use"], (int(x) for x in st)))
+
+    def close(self):
+        if getattr(self, "server", None):
+            load().nbte_server_destroy(self.server)
+            self.server = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def nbte_get_temperature(solver, kind, n_cells):
