@@ -275,6 +275,115 @@ def cpu_baseline(max_seconds=20.0, steps=1, warmup=1):
             "seconds_per_step": dt}
 
 
+def run_stream(args):
+    """Serving: a seeded stream of steady solves (2D tri / 3D hex / 3D tet
+    geometries, mixed sizes, band counts, direction sets, heat loads and
+    walls) with Poisson arrivals.  One-at-a-time arm: each request solved
+    alone with nbte_solve_steady (planning included), its FIFO queueing
+    replayed from the measured service times.  Served arm: the same requests
+    submitted in real time to the continuous-batching server.  Both report
+    throughput and p50/p99 time-to-converged (arrival to converged field)."""
+    import threading
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2607_03226_b300 import nbte
+
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    reqs = W.stream.requests(args.requests, rate=1.0, n_range=(args.min_cells, args.max_cells))
+    probs = [W.stream.build(r) for r in reqs]
+    opts = dict(scheme="synthetic", precision=args.precision, tol=args.stream_tol, max_iter=20000,
+                band_group=2, cta_threads=160, use_graph=True, skip_outputs=False)
+    upd = [p.updates_per_iteration for p in probs]
+    # ---- one at a time
+    service, iters = [], []
+    for p in probs:
+        s = nbte.Solver(p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = s.solve(**opts)
+        service.append(time.perf_counter() - t0)
+        iters.append(info["iterations"])
+        s.close()
+    mu = len(service) / sum(service)                     # one-at-a-time service rate (requests/s)
+    rate = args.load * mu
+    rng = np.random.default_rng(2607032265)
+    arrival = np.cumsum(rng.exponential(1.0 / rate, size=len(probs)))
+    arrival -= arrival[0]
+    finish, free = [], 0.0
+    for a, sv in zip(arrival, service):
+        free = max(free, a) + sv
+        finish.append(free)
+    lat1 = np.array(finish) - arrival
+    work = sum(u * it for u, it in zip(upd, iters))
+    one = {"throughput_req_s": len(probs) / finish[-1], "updates_per_s": work / finish[-1],
+           "p50_s": float(np.percentile(lat1, 50)), "p99_s": float(np.percentile(lat1, 99)),
+           "mean_service_s": float(np.mean(service))}
+    # ---- served
+    solvers = [nbte.Solver(p) for p in probs]
+    srv = nbte.Server(max_active=args.max_active, n_planners=args.planners, **opts)
+    ids = [None] * len(probs)
+    t_start = time.perf_counter()
+
+    def feeder():
+        for k, a in enumerate(arrival):
+            dt = t_start + a - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids[k] = srv.submit(solvers[k])
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    srv.drain(timeout_s=3600)
+    makespan = time.perf_counter() - t_start
+    lat2, iters2, errs = [], [], 0
+    for k in range(len(probs)):
+        info, total, queued = srv.poll(ids[k])
+        lat2.append(total)
+        iters2.append(info["iterations"])
+        errs += info["status"] != 0
+    work2 = sum(u * it for u, it in zip(upd, iters2))
+    st = srv.stats()
+    srv.close()
+    for s in solvers:
+        s.close()
+    lat2 = np.array(lat2)
+    served = {"throughput_req_s": len(probs) / makespan, "updates_per_s": work2 / makespan,
+              "p50_s": float(np.percentile(lat2, 50)), "p99_s": float(np.percentile(lat2, 99)),
+              "batched_iterations": st["iterations"], "failed": int(errs)}
+    # ---- capacity: every request submitted at once (throughput is then the
+    # server's, not the arrival rate's); one at a time it is the summed service
+    solvers = [nbte.Solver(p) for p in probs]
+    srv = nbte.Server(max_active=args.max_active, n_planners=args.planners, **opts)
+    t0 = time.perf_counter()
+    ids = [srv.submit(s) for s in solvers]
+    srv.drain(timeout_s=3600)
+    burst = time.perf_counter() - t0
+    iters3 = [srv.poll(i)[0]["iterations"] for i in ids]
+    srv.close()
+    for s in solvers:
+        s.close()
+    work3 = sum(u * it for u, it in zip(upd, iters3))
+    capacity = {"served_updates_per_s": work3 / burst, "served_req_s": len(probs) / burst,
+                "one_at_a_time_updates_per_s": work / sum(service), "one_at_a_time_req_s": mu,
+                "served_makespan_s": burst, "one_at_a_time_makespan_s": sum(service)}
+    out = {"metric": "serve time-to-converged p50 (p99 beside)", "value": served["p50_s"], "unit": "s",
+           "n_gpus": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 sweep / f64 moments+update+CG" if args.precision == "fp32" else "f64",
+           "data": "synthetic (seeded request stream)",
+           "config": {"workload": "stream: Poisson arrivals of 2D tri / 3D hex / 3D tet steady solves",
+                      "requests": len(probs), "cells": [args.min_cells, args.max_cells],
+                      "load": args.load, "arrival_rate_req_s": rate, "tol": args.stream_tol,
+                      "max_active": args.max_active, "layout": "band_group=2 cta_threads=160"},
+           "served": served, "one_at_a_time": one, "capacity": capacity,
+           "speedup_capacity": capacity["served_updates_per_s"] / capacity["one_at_a_time_updates_per_s"]}
+    print(json.dumps(out))
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -303,9 +412,19 @@ def main():
     ap.add_argument("--cg-max-iter", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="finfet2d", choices=["finfet2d", "stream"])
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--min-cells", type=int, default=20000)
+    ap.add_argument("--max-cells", type=int, default=500000)
+    ap.add_argument("--load", type=float, default=0.9)
+    ap.add_argument("--stream-tol", type=float, default=1e-8)
+    ap.add_argument("--max-active", type=int, default=32)
+    ap.add_argument("--planners", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "stream":
+        run_stream(args)
     else:
         run_gpu(args)
 
