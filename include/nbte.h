@@ -157,7 +157,7 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  *            memory (one region per work item, L2-resident while it runs).
  *            Results are identical either way.
  * cg_tol, cg_max_iter: relative residual and cap of the conjugate-gradient
- *            solve of the synthetic correction (0 = defaults 1e-3, 5000); the
+ *            solve of the synthetic correction (0 = defaults 1e-2, 5000); the
  *            correction only changes the rate of convergence, not the limit.
  *            Each solve starts from the previous correction scaled by its
  *            Galerkin factor.

@@ -1025,7 +1025,7 @@ int autotune(nbte_solver* S, const nbte_solve_opts& o) {
 struct Run {
   nbte_solver* S = nullptr;
   nbte_solve_opts o{};
-  double cg_tol = 1e-3;
+  double cg_tol = 1e-2;
   int cg_max = 5000;
   bool fixed = false;
   int limit = 0;
@@ -1089,7 +1089,7 @@ template <typename R>
 int run_begin(Run& run, nbte_solver* S, const nbte_solve_opts& o) {
   run.S = S;
   run.o = o;
-  run.cg_tol = o.cg_tol > 0 ? o.cg_tol : 1e-3;
+  run.cg_tol = o.cg_tol > 0 ? o.cg_tol : 1e-2;
   run.cg_max = o.cg_max_iter > 0 ? o.cg_max_iter : 5000;
   run.fixed = o.n_iter > 0;
   run.limit = run.fixed ? o.n_iter : o.max_iter;
