@@ -156,6 +156,12 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  *            1 = shared memory (NBTE_ERR_ARG if it does not fit); 2 = global
  *            memory (one region per work item, L2-resident while it runs).
  *            Results are identical either way.
+ * init:      starting temperature when not warm: 0 = T_init (or T_ref);
+ *            1 = the diffusion-limit (Fourier) solution, L T' = Qdot V with
+ *            the thermalizing walls' temperatures as Dirichlet data and no
+ *            flux through other walls, L the synthetic correction's TPFA
+ *            operator, solved by its CG to 1e-12 (excludes T_init).  Only
+ *            the starting point changes, never the converged field.
  * cg_tol, cg_max_iter: relative residual and cap of the conjugate-gradient
  *            solve of the synthetic correction (0 = defaults 1e-2, 5000); the
  *            correction only changes the rate of convergence, not the limit.
@@ -188,6 +194,7 @@ typedef struct {
   int32_t profile;
   int32_t cta_threads;
   int32_t ring;
+  int32_t init;
 } nbte_solve_opts;
 
 /* Filled on return from nbte_solve_steady (also on NOT_CONVERGED):

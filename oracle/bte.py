@@ -295,6 +295,26 @@ class OracleSolver:
         self._lap_matrix = L.tocsr()
         return self._lap
 
+    def fourier_guess(self):
+        """Initial temperature deviation from the diffusion limit (the
+        Fourier solution the paper starts from, Sec. IV): ``L T' = Qdot V +
+        sum over thermalizing faces g_f T'_w``, the same TPFA operator as the
+        synthetic correction (:meth:`laplacian`) with the thermalizing wall
+        temperatures as Dirichlet data; other walls carry no flux.  Only the
+        starting point changes, never the fixed point."""
+        g = self.g
+        lap = self.laplacian()
+        kap = self.kappa_bulk()
+        k1 = self.numerical_diffusivity()
+        area = np.linalg.norm(g.hf_An, axis=1)
+        n = g.hf_An / area[:, None]
+        sel = self.btype == THERMALIZING
+        th = self.bhf[sel]
+        dist = np.abs(np.sum((g.hf_xf[th] - g.xc[g.hf_cell[th]]) * n[th], axis=1))
+        gf = (kap + k1 * 2.0 * dist) * area[th] / dist
+        rhs = self.Qdot * g.V + np.bincount(g.hf_cell[th], weights=gf * self.bTw[sel], minlength=self.N)
+        return lap.solve(rhs)
+
     def wall_flux(self, eb, e_in):
         """Net outward heat flow through each boundary tag,
         sum_l sum_i w_i v_l (s_i . An_f) e~_f over the tag's faces."""
@@ -324,17 +344,24 @@ class OracleSolver:
         return div
 
     # ------------------------------------------------------------------ driver
-    def solve(self, scheme=None, tol=None, max_iter=None, n_iter=None, T_init=None,
+    def solve(self, scheme=None, tol=None, max_iter=None, n_iter=None, T_init=None, init="tref",
               store_e=False, verbose=False):
         """Run the outer iteration.
 
         ``n_iter`` runs exactly that many sweeps (no convergence test);
         otherwise iterate until ``r = |T'^{n+1} - T'^n|_inf / |T'^{n+1}|_inf < tol``.
-        Returned temperatures are absolute (K)."""
+        ``init="fourier"`` starts from :meth:`fourier_guess` (walls at
+        equilibrium with it) instead of T_init / T_ref.  Returned temperatures
+        are absolute (K)."""
         scheme = scheme or self.p.scheme
         tol = self.p.tol if tol is None else tol
         max_iter = self.p.max_iter if max_iter is None else max_iter
-        T = np.zeros(self.N) if T_init is None else np.asarray(T_init, dtype=np.float64) - self.T_ref
+        if init == "fourier":
+            T = self.fourier_guess()
+        elif init == "tref":
+            T = np.zeros(self.N) if T_init is None else np.asarray(T_init, dtype=np.float64) - self.T_ref
+        else:
+            raise ValueError(init)
         eb = self.equilibrium_walls(T)
         hist = []
         it = 0

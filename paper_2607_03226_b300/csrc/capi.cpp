@@ -142,6 +142,7 @@ struct nbte_solver {
   int cg_max_rows = 0, cg_max_na = 0, cg_smem_vec = 0, cg_smem_ell = 0;
   int64_t cg_part_key = -1;
   std::vector<int32_t> h_agg_cell, h_agg_p;   // aggregate row ranges / aggregate of each row (aggregate order)
+  std::vector<double> h_fourier_bc;           // [N] Dirichlet rhs of the diffusion initial guess
   // ---- laplacian (synthetic)
   int64_t lap_built = -1;
   DBuf L_ecol, L_eval, L_diag, L_dinv;
@@ -153,6 +154,8 @@ struct nbte_solver {
   bool have_outputs = false;   // E, q, wall heat of the last sweep
   unsigned long long* h_res = nullptr;   // pinned: [2] residual words
   int32_t* h_misc = nullptr;             // pinned: [2] device error, cg iterations
+  mutable double* h_stage = nullptr;     // pinned staging of result fields read back to the host
+  mutable size_t h_stage_n = 0;
   cudaGraphExec_t graph = nullptr;
   std::string graph_key;
   double last_energy_imbalance = 0;
@@ -162,6 +165,7 @@ struct nbte_solver {
     if (graph) cudaGraphExecDestroy(graph);
     if (h_res) cudaFreeHost(h_res);
     if (h_misc) cudaFreeHost(h_misc);
+    if (h_stage) cudaFreeHost(h_stage);
     if (own_stream) cudaStreamDestroy(own_stream);
   }
 };
@@ -564,6 +568,10 @@ int ensure_laplacian(nbte_solver* S) {
   const double k1 = 0.25 * mean_abs * cv;
   Laplacian L;
   build_laplacian(m, S->bcs, kb, k1, L);
+  // Dirichlet data of the diffusion initial guess: sum over thermalizing
+  // faces of g_f (T_wall - T_ref), per internal cell
+  S->h_fourier_bc.resize(m.n_cells);
+  for (int64_t c = 0; c < m.n_cells; ++c) S->h_fourier_bc[c] = L.bc_gT[c] - S->T_ref * L.bc_g[c];
   const int64_t N = m.n_cells;
   // ---- coarse space: geometric aggregates, rows reordered so each
   // aggregate's cells are contiguous, blocks owning whole aggregates
@@ -931,6 +939,28 @@ int init_state(nbte_solver* S, const nbte_solve_opts& o) {
     }
   }
   NBTE_CK(cudaMemcpyAsync(S->T.p, T0.data(), N * 8, cudaMemcpyHostToDevice, st));
+  if (o.init == 1) {
+    // diffusion initial guess: L T' = Qdot V + sum_thermalizing g_f T'_w,
+    // the synthetic correction's operator with the wall temperatures as
+    // Dirichlet data, solved with the same CG to FP64 accuracy
+    std::vector<double> rhs(N);
+    for (int64_t c = 0; c < N; ++c) rhs[c] = S->Q[c] * m.V[c] + S->h_fourier_bc[c];
+    NBTE_CK(cudaMemcpyAsync(S->rhs.p, rhs.data(), N * 8, cudaMemcpyHostToDevice, st));
+    NBTE_CK(cudaMemsetAsync(S->cg_x.p, 0, N * 8, st));
+    NBTE_CK(cudaMemsetAsync(S->cg_err.p, 0, 4, st));
+    NBTE_CK(launch_cg(cg_args(S, 1e-12, 20000), false, S->cg_grid, S->cg_threads, cg_smem_for(S, false), st));
+    NBTE_CK(cudaMemcpyAsync(S->T.p, S->delta.p, N * 8, cudaMemcpyDeviceToDevice, st));
+    NBTE_CK(cudaMemsetAsync(S->cg_x.p, 0, N * 8, st));   // later corrections start from zero
+    int32_t err = 0;
+    NBTE_CK(cudaMemcpyAsync(&err, S->cg_err.p, 4, cudaMemcpyDeviceToHost, st));
+    NBTE_CK(cudaStreamSynchronize(st));
+    if (err != 0) {
+      cudaMemset(S->cg_err.p, 0, 16);
+      cudaMemset(S->cg_slots.p, 0, S->cg_slots.bytes);
+      cudaMemset(S->cg_bar.p, 0, 16);
+      return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the initial diffusion solve gave up");
+    }
+  }
   NBTE_CK(cudaMemsetAsync(S->Delta.p, 0, N * 8, st));
   NBTE_CK(cudaMemsetAsync(S->Tkin.p, 0, N * 8, st));
   launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)N, st);
@@ -997,6 +1027,7 @@ int autotune(nbte_solver* S, const nbte_solve_opts& o) {
       c.band_group = G;
       c.cta_threads = cap + 32;
       c.warm = 0;
+      c.init = 0;
       if (ensure_layout(S, c) != NBTE_OK) continue;   // does not fit this mesh
       int rc = ensure_q(S);
       if (rc) return rc;
@@ -1543,7 +1574,7 @@ void nbte_server::plan_loop() {
     if (!rc) rc = ensure_plan(S);
     size_t b = 0;
     if (!rc) rc = ensure_layout(S, opts, &b);
-    if (!rc && opts.scheme != 0) {
+    if (!rc && (opts.scheme != 0 || opts.init == 1)) {
       b += estimate_cg_bytes(S);
       rc = ensure_laplacian(S);   // host-heavy (aggregation, dense coarse inverse): off the GPU loop
     }
@@ -1592,6 +1623,7 @@ void nbte_server::work_loop() {
       DeviceGuard g(q->S->device);
       int rc = ensure_layout(q->S, opts);
       if (!rc) rc = ensure_q(q->S);
+      if (!rc && opts.init == 1) rc = cg_default_partition(q->S);
       if (!rc) rc = run_begin<R>(q->run, q->S, opts);
       if (!rc) rc = cudaStreamSynchronize(q->S->stream) == cudaSuccess ? NBTE_OK : NBTE_ERR_CUDA;
       if (rc) {
@@ -1835,6 +1867,8 @@ static int check_opts(const nbte_solve_opts& o) {
   if (o.n_iter == 0 && !(o.tol > 0 && std::isfinite(o.tol))) return fail(NBTE_ERR_ARG, "tol must be positive");
   if (o.n_iter == 0 && o.max_iter <= 0) return fail(NBTE_ERR_ARG, "max_iter must be positive");
   if (o.ring < 0 || o.ring > 2) return fail(NBTE_ERR_ARG, "ring must be 0, 1 or 2");
+  if (o.init < 0 || o.init > 1) return fail(NBTE_ERR_ARG, "init must be 0 or 1");
+  if (o.init == 1 && o.T_init) return fail(NBTE_ERR_ARG, "init = 1 (diffusion guess) excludes T_init");
   return NBTE_OK;
 }
 
@@ -1888,8 +1922,10 @@ static int prepare(nbte_solver* S, const nbte_solve_opts& o) {
   if (rc) return rc;
   rc = ensure_q(S);
   if (rc) return rc;
-  if (o.scheme != 0) {
+  if (o.scheme != 0 || o.init == 1) {
     rc = ensure_laplacian(S);
+    if (rc) return rc;
+    rc = cg_default_partition(S);
     if (rc) return rc;
   }
   return NBTE_OK;
@@ -1906,10 +1942,6 @@ int nbte_solve_steady(nbte_solver* S, const nbte_solve_opts* opts, nbte_solve_in
     rc = prepare(S, o);
     if (rc) return rc;
     DeviceGuard g(S->device);
-    if (o.scheme != 0) {
-      rc = cg_default_partition(S);
-      if (rc) return rc;
-    }
     return S->prec ? run_solve<float>(S, o, info) : run_solve<double>(S, o, info);
   } catch (const std::bad_alloc&) {
     return fail(NBTE_ERR_OOM, "host allocation failed");
@@ -1948,6 +1980,25 @@ int nbte_solve_batch(nbte_solver* const* solvers, int32_t n, const nbte_solve_op
   }
 }
 
+}  // extern "C"
+
+// pinned host staging of n doubles for result read-back (grows on demand)
+static double* host_stage(const nbte_solver* S, size_t n) {
+  if (S->h_stage_n < n) {
+    if (S->h_stage) cudaFreeHost(S->h_stage);
+    S->h_stage = nullptr;
+    S->h_stage_n = 0;
+    if (cudaMallocHost(&S->h_stage, n * 8) != cudaSuccess) {
+      S->h_stage = nullptr;
+      return nullptr;
+    }
+    S->h_stage_n = n;
+  }
+  return S->h_stage;
+}
+
+extern "C" {
+
 int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
   if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
   if (!S->have_results) return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
@@ -1956,9 +2007,10 @@ int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
   DeviceGuard g(S->device);
   const Mesh& m = S->mesh->m;
   const int64_t N = m.n_cells;
-  std::vector<double> tmp(N);
+  double* tmp = host_stage(S, (size_t)N);
+  if (!tmp) return fail(NBTE_ERR_OOM, "pinned host allocation failed");
   const DBuf& src = kind == 0 ? S->T : (kind == 1 ? S->accE : S->Tkin);
-  NBTE_CK(cudaMemcpyAsync(tmp.data(), src.p, N * 8, cudaMemcpyDeviceToHost, S->stream));
+  NBTE_CK(cudaMemcpyAsync(tmp, src.p, N * 8, cudaMemcpyDeviceToHost, S->stream));
   NBTE_CK(cudaStreamSynchronize(S->stream));
   for (int64_t c = 0; c < N; ++c) {
     const double t = kind == 1 ? tmp[c] / S->Ctot : tmp[c];
@@ -1974,8 +2026,9 @@ int nbte_get_heat_flux(const nbte_solver* S, double* out) {
   DeviceGuard g(S->device);
   const Mesh& m = S->mesh->m;
   const int64_t N = m.n_cells;
-  std::vector<double> tmp((size_t)N * m.dim);
-  NBTE_CK(cudaMemcpyAsync(tmp.data(), S->accQ.p, tmp.size() * 8, cudaMemcpyDeviceToHost, S->stream));
+  double* tmp = host_stage(S, (size_t)N * m.dim);
+  if (!tmp) return fail(NBTE_ERR_OOM, "pinned host allocation failed");
+  NBTE_CK(cudaMemcpyAsync(tmp, S->accQ.p, (size_t)N * m.dim * 8, cudaMemcpyDeviceToHost, S->stream));
   NBTE_CK(cudaStreamSynchronize(S->stream));
   for (int64_t c = 0; c < N; ++c)
     for (int d = 0; d < m.dim; ++d) out[m.perm[c] * m.dim + d] = tmp[c * m.dim + d];

@@ -96,6 +96,9 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
 struct Laplacian {
   std::vector<int32_t> row_ptr, col;
   std::vector<double> val, diag;
+  // per cell, over its thermalizing faces: sum g_f and sum g_f T_wall (the
+  // Dirichlet data of a diffusion solve with the wall temperatures)
+  std::vector<double> bc_g, bc_gT;
 };
 void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bulk, double k1,
                      Laplacian& L);

@@ -450,11 +450,17 @@ void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bul
   const int dim = m.dim, nfc = m.nfc;
   const int64_t N = m.n_cells;
   std::map<int32_t, int> type;
-  for (auto& b : bcs) type[b.tag] = b.type;
+  std::map<int32_t, double> twall;
+  for (auto& b : bcs) {
+    type[b.tag] = b.type;
+    twall[b.tag] = b.T_wall;
+  }
   L.row_ptr.assign(N + 1, 0);
   L.col.clear();
   L.val.clear();
   L.diag.assign(N, 0.0);
+  L.bc_g.assign(N, 0.0);
+  L.bc_gT.assign(N, 0.0);
   for (int64_t c = 0; c < N; ++c) {
     double dg = 0.0;
     for (int k = 0; k < nfc; ++k) {
@@ -475,7 +481,10 @@ void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bul
         double dist = 0;
         for (int d = 0; d < dim; ++d) dist += (m.xf[h * dim + d] - m.xc[c * dim + d]) * m.An[h * dim + d] / area;
         dist = std::fabs(dist);
-        dg += (kappa_bulk + k1 * 2.0 * dist) * area / dist;
+        const double gw = (kappa_bulk + k1 * 2.0 * dist) * area / dist;
+        dg += gw;
+        L.bc_g[c] += gw;
+        L.bc_gT[c] += gw * twall.at(m.tag[h]);
       }
     }
     L.col.push_back((int32_t)c);

@@ -229,3 +229,25 @@ def test_distribution_every_task(nbte_mod, name, precision, tol):
     print(f"{name} {precision}: worst task error {worst:.2e}")
     assert worst < tol
     s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fourier_initial_guess(nbte_mod, name):
+    """Iterations from the diffusion-limit initial guess (init="fourier")
+    against the oracle's, which solves the guess exactly; the device solves it
+    by CG to a 1e-12 relative residual, so the bound is 1e-8.  The converged
+    field does not depend on the starting point (1e-9)."""
+    p = CASES[name]()
+    s = nbte_mod.Solver(p)
+    for n in (1, 2):
+        s.solve(scheme="sequential", precision="fp64", n_iter=n, init="fourier")
+        r = oracle_run(name, scheme="sequential", n_iter=n, init="fourier")
+        err = rel_T(s.temperature(0), r["T"], p.T_ref)
+        print(f"{name}: {n} iteration(s) from the Fourier guess, T error {err:.2e}")
+        assert err < 1e-8
+    a = s.solve(scheme="synthetic", precision="fp64", tol=1e-13, max_iter=20000, init="fourier")
+    Ta = s.temperature(0)
+    b = s.solve(scheme="synthetic", precision="fp64", tol=1e-13, max_iter=20000)
+    assert a["status"] == 0 and b["status"] == 0
+    assert rel_T(Ta, s.temperature(0), p.T_ref) < 1e-9
+    s.close()

@@ -11,6 +11,7 @@ from workloads.problems import Boundary, Problem, THERMALIZING, DIFFUSE, SPECULA
 from oracle import OracleSolver, quadrature_moments
 
 from bruteforce import solve_fixed_point
+from cases import CASES
 
 
 # ----------------------------------------------------------------------------- I1
@@ -312,3 +313,27 @@ def test_diffusive_limit_linear_profile():
     assert 0.0 < jump < 0.1
     q_ref = p.C[0] * v * 2.0 / (np.pi + 2 * L / mfp)
     assert abs(r["q"][:, 0].mean() / q_ref - 1.0) < 0.03
+
+
+def test_fourier_guess_linear_between_thermalizing_walls():
+    """Diffusion-limit initial guess on the in-plane square (walls 301 / 299 K
+    left / right, specular top / bottom, no source): the TPFA solution with
+    uniform conductivity is exactly linear in x, T = 301 - 2 x / L, at every
+    cell centre (the two-point flux of a linear field is exact, also at the
+    half-cell wall distance)."""
+    p = W.problems.square_inplane(n=20)
+    o = OracleSolver(p)
+    T = o.fourier_guess() + p.T_ref
+    L = 100e-9
+    x = o.g.xc[:, 0]
+    assert np.abs(T - (301.0 - 2.0 * x / L)).max() < 1e-10
+
+
+def test_fourier_guess_same_fixed_point():
+    """Starting from the Fourier guess changes the iterates, not the limit."""
+    p = CASES["square_mixed"]()
+    o = OracleSolver(p)
+    a = o.solve(scheme="synthetic", tol=1e-13, max_iter=20000)
+    b = o.solve(scheme="synthetic", tol=1e-13, max_iter=20000, init="fourier")
+    dev = np.abs(a["T"] - p.T_ref).max()
+    assert np.abs(a["T"] - b["T"]).max() < 1e-10 * dev
