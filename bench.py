@@ -41,6 +41,23 @@ def _dist():
     return ws, rank
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_step, steps, world_size, t_max_ms):
+    """Whole-job throughput: every rank processed units_per_step per step
+    (replicas, weak scaling), over the slowest rank's time."""
+    return units_per_step * steps * world_size / (t_max_ms * 1e-3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -183,12 +200,8 @@ def run_gpu(args):
         torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     clocks = clk.summary()
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = upd * args.steps * ws / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, dist, "cuda")
+    value = aggregate_rate(upd, args.steps, ws, t_max)
 
     # sweep-kernel duration with events around each launch (same stream)
     prof = solver.solve(n_iter=args.steps, warm=True, profile=True, **{k: v for k, v in kw.items()
