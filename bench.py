@@ -12,6 +12,7 @@ correction added) and the time to a converged field for both schemes.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--precision fp32|fp64] [--scheme synthetic|sequential]
     python bench.py --workload stream [--requests R] [--load L]     (serving)
+    python bench.py --workload cube3d|finfet3d [--precision fp64]   (time to converged field)
 
 Prints one JSON line.  Under torchrun (N > 1) every rank solves its own
 replica (no data exchange); rank 0 prints the aggregate over all ranks.
@@ -430,6 +431,68 @@ def run_stream(args):
     print(json.dumps(out))
 
 
+def run_converge(args):
+    """The 3D workloads' measurement: time and iterations to a converged
+    field, synthetic against sequential, from T_ref and from the diffusion
+    (Fourier) guess, plus the per-step rate of each scheme.  FP64 sweeps
+    reach the 1e-8 tolerance these workloads are specified with; FP32 sweeps
+    stop at their rounding floor (about 5e-8), so they are run to 1e-6."""
+    import torch
+    import workloads as W
+    from paper_2607_03226_b300 import nbte
+
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    p = getattr(W.problems, args.workload)()
+    solver = nbte.Solver(p)
+    tol = 1e-8 if args.precision == "fp64" else 1e-6
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    runs = {}
+    for sch in ("synthetic", "sequential"):
+        for init in ("tref", "fourier"):
+            kw = dict(scheme=sch, precision=args.precision, tol=tol, max_iter=args.max_iter, cg_tol=args.cg_tol,
+                      use_graph=True, skip_outputs=True, init=init)
+            solver.solve(n_iter=2, **{k: v for k, v in kw.items() if k not in ("tol", "max_iter")})  # plan, tune, graph
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = solver.solve(**kw)
+            torch.cuda.synchronize()
+            runs[f"{sch}_{init}"] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                                     "residual": info["residual"], "status": info["status"],
+                                     "cg_iterations": info["cg_iterations"]}
+            print(json.dumps({sch + "_" + init: runs[f"{sch}_{init}"]}), file=sys.stderr, flush=True)
+    steps = {}
+    for sch in ("synthetic", "sequential"):
+        kw = dict(scheme=sch, precision=args.precision, cg_tol=args.cg_tol, use_graph=True, skip_outputs=True)
+        solver.solve(n_iter=3, warm=True, **kw)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        solver.solve(n_iter=args.steps, warm=True, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        steps[sch] = {"ms_per_step": ms, "updates_per_s": p.updates_per_iteration / (ms * 1e-3)}
+    st = solver.plan_stats(precision=args.precision, scheme="synthetic")
+    solver.close()
+    best = min(runs, key=lambda k: runs[k]["seconds"] if runs[k]["status"] == 0 else 1e30)
+    out = {"metric": "time to converged field", "value": runs[best]["seconds"], "unit": "s", "n_gpus": 1,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 sweep / f64 moments+update+CG" if args.precision == "fp32" else "f64",
+           "data": "synthetic (seeded mesh and spectrum)",
+           "config": {"workload": args.workload, "n_cells": p.n_cells, "bands": p.n_bands, "directions": p.n_dirs,
+                      "tol": tol, "precision": args.precision, "cg_tol": args.cg_tol, "best": best,
+                      "band_group": st["band_group"], "cta_threads": st["cta_threads"],
+                      "ring": "global" if st["ring"] == 2 else "shared"},
+           "runs": runs, "steps": steps,
+           "synthetic_vs_sequential_iterations": runs["sequential_tref"]["iterations"] /
+           max(1, runs["synthetic_tref"]["iterations"])}
+    print(json.dumps(out))
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -458,7 +521,8 @@ def main():
     ap.add_argument("--cg-max-iter", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="finfet2d", choices=["finfet2d", "stream"])
+    ap.add_argument("--workload", default="finfet2d", choices=["finfet2d", "stream", "cube3d", "finfet3d"])
+    ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--min-cells", type=int, default=20000)
     ap.add_argument("--max-cells", type=int, default=500000)
@@ -471,6 +535,8 @@ def main():
         run_reference(args)
     elif args.workload == "stream":
         run_stream(args)
+    elif args.workload in ("cube3d", "finfet3d"):
+        run_converge(args)
     else:
         run_gpu(args)
 
