@@ -128,10 +128,10 @@ struct nbte_solver {
   // ---- band layout (depends on bands, precision and tuning)
   std::string layout_key, rec_key, chunk_key;
   int prec = 0, G = 1, Gpad = 4, n_groups = 1, Bp = 1, n_items = 0, threads = 160, n_stages = 4;
-  int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0;
+  int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0, off_den = 0;
   size_t smem = 0;
   double W = 0, beta = 0, Ctot = 0;
-  DBuf rec, pos_cell, chunks, chunk_off, tqp, gring, e_scratch;
+  DBuf rec, pos_cell, chunks, chunk_off, tqp, gring, e_scratch, dinv;
   int64_t gring_stride = 0;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
@@ -186,7 +186,7 @@ struct DeviceGuard {
 };
 
 size_t device_bytes(const nbte_solver* S) {
-  const DBuf* all[] = {&S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
+  const DBuf* all[] = {&S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->dinv, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
                        &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
                        &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
@@ -378,23 +378,26 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   }
   if (o.threads_per_cell > 1) return fail(NBTE_ERR_ARG, "threads_per_cell must be 0 or 1");
   // shared memory of one CTA: barriers and chunk headers, the value ring, and
-  // the copy stages (records, (T', Qdot) pairs, imports)
-  auto stage_of = [&](int Gv, int& off_tq, int& off_imp) {
+  // the copy stages (records, (T', Qdot) pairs, imports, and with FP64 the
+  // precomputed denominators 1/(1/tau + v G) of the chunk's positions)
+  auto stage_of = [&](int Gv, int& off_tq, int& off_imp, int& off_den) {
     const int gpad = padded_group(Gv, sz);
     const int rec = (cap * RL.size + 15) / 16 * 16;
     const int tq = ((cap + 2) * 2 * sz + 15) / 16 * 16;
     const int imp = cap * K * gpad * sz;
+    const int den = prec ? 0 : ((cap + 2) * Gv * 8 + 15) / 16 * 16;
     off_tq = rec;
     off_imp = rec + tq;
-    return rec + tq + imp;
+    off_den = rec + tq + imp;
+    return rec + tq + imp + den;
   };
   // the value ring: in shared memory when it fits beside two copy stages,
   // else one global-memory region per CTA
   auto ring_of = [&](int Gv) { return (int)(((size_t)(S->max_slots + 1) * Gv * sz + 15) / 16 * 16); };
   const int head = 32 * 8;   // up to 8 stages: full + empty barriers and chunk headers
   auto smem_ring = [&](int Gv) {
-    int a, b;
-    return (int64_t)head + ring_of(Gv) + 2 * (int64_t)stage_of(Gv, a, b) <= kSweepSmemMax;
+    int a, b, c;
+    return (int64_t)head + ring_of(Gv) + 2 * (int64_t)stage_of(Gv, a, b, c) <= kSweepSmemMax;
   };
   auto ring_smem_bytes = [&](int Gv) { return smem_ring(Gv) ? ring_of(Gv) : 0; };
   const int maxG = prec ? 8 : 4;
@@ -419,16 +422,16 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
                                   " live cells in one direction)");
   const bool gr = o.ring == 2 || !smem_ring(G);
   {
-    int a, b;
-    if ((int64_t)head + 2 * (int64_t)stage_of(G, a, b) > kSweepSmemMax)
+    int a, b, c;
+    if ((int64_t)head + 2 * (int64_t)stage_of(G, a, b, c) > kSweepSmemMax)
       return fail(NBTE_ERR_ARG, "cta_threads too large for shared memory with this band group");
   }
   // stages: 2..8.  The sweep of one item is a long dependent chain of
   // levels, so co-resident CTAs are what hides its latency: aim for every
   // work item resident at once, else for as many CTAs per SM as still get
   // three stages each, then give each CTA as many stages as that allows
-  int off_tq = 0, off_imp = 0;
-  const int stage = stage_of(G, off_tq, off_imp);
+  int off_tq = 0, off_imp = 0, off_den = 0;
+  const int stage = stage_of(G, off_tq, off_imp, off_den);
   const int ng = (S->B + G - 1) / G;
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device);
@@ -448,6 +451,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     b += (size_t)ng * (S->n_exp + S->n_imp) * Gp * sz;                   // export / import rows
     if (gr) b += (size_t)D * ng * (((size_t)(S->max_slots + 1) * G + 3) / 4 * 4) * sz;   // global rings
     b += N * (4 * sz + 12 * 8 + 8 * (size_t)S->mesh->m.dim);            // per-cell fields
+    if (!prec) b += (size_t)D * Bp * N * 8;                              // FP64 denominators
     b += D * N / 8 + (size_t)S->n_dbf * Bp * 8 + (size_t)S->n_wf * 16;  // chunks, diffuse sums, wall heat
     *estimate = b;
     return NBTE_OK;
@@ -469,6 +473,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   S->stage_bytes = stage;
   S->off_tq = off_tq;
   S->off_imp = off_imp;
+  S->off_den = off_den;
   S->off_ring = head;
   S->off_stage = head + (int)ringB;
   S->gring_stride = gr ? ((int64_t)(S->max_slots + 1) * G + 3) / 4 * 4 : 0;
@@ -517,6 +522,18 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     NBTE_CK(S->gring.alloc((size_t)S->n_items * S->gring_stride * sz));
   } else {
     S->gring.release();
+  }
+  if (!prec) {
+    // FP64: the denominators 1/(1/tau + v G) of every (work item, position),
+    // iteration-independent, so the sweep reads them instead of dividing
+    // (+16 doubles: a chunk's 16-byte aligned copy may run one position past the last)
+    NBTE_CK(S->dinv.alloc(((size_t)S->n_items * N * G + 16) * 8));
+    NBTE_CK(cudaMemset(S->dinv.p, 0, S->dinv.bytes));
+    NBTE_CK(launch_fill_dinv(S->dinv.as<double>(), S->rec.as<unsigned char>(), RL.size, RL.off_G,
+                             S->band_v.as<double>(), S->band_itau.as<double>(), S->D, ng, G, N, S->stream));
+    NBTE_CK(cudaStreamSynchronize(S->stream));
+  } else {
+    S->dinv.release();
   }
   NBTE_CK(S->T.alloc(N * 8));
   NBTE_CK(S->Tprev.alloc(N * 8));
@@ -748,6 +765,8 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.off_stage = S->off_stage;
   a.off_tq = S->off_tq;
   a.off_imp = S->off_imp;
+  a.off_den = S->off_den;
+  a.dinv = S->dinv.p ? S->dinv.as<R>() : nullptr;
   a.n_exp = S->n_exp;
   a.n_imp = S->n_imp;
   a.item_dir = S->item_dir.as<int32_t>();

@@ -22,7 +22,8 @@ struct SweepArgs {
   int full;                      // also accumulate E and q (atomics)
   int Gpad;                      // padded row length of the import/export tables
   int n_stages;                  // shared-memory stages of the copy pipeline
-  int stage_bytes, off_ring, off_stage, off_tq, off_imp;   // shared-memory layout
+  int stage_bytes, off_ring, off_stage, off_tq, off_imp, off_den;   // shared-memory layout
+  const R* dinv;                 // FP64 only: [n_items*N*G] denominators 1/(1/tau + v G), else null
   int64_t n_exp, n_imp;
   const int32_t* item_dir;       // [n_items]
   const int32_t* item_grp;       // [n_items]
@@ -59,6 +60,10 @@ cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int t
 template <typename R>
 cudaError_t launch_sweep_batch(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers, int K, int G,
                                bool global_ring, int n_items, int threads, size_t smem, cudaStream_t st);
+// dinv[(item*N + pos)*G + b] = 1 / (band_inv_tau[g*G+b] + band_v[g*G+b] G_pos),
+// item = i*n_groups + g, G_pos read from the packed position records
+cudaError_t launch_fill_dinv(double* dinv, const unsigned char* rec, int rec_bytes, int off_G, const double* band_v,
+                             const double* band_inv_tau, int D, int n_groups, int G, int64_t N, cudaStream_t st);
 template <typename R>
 cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st);
 

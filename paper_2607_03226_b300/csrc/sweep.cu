@@ -240,9 +240,20 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         const unsigned tq_bytes = (unsigned)((qe - qa) * 2 * sizeof(R));
         const int nimp = m.nimp_end & 0x3fffffff;
         const unsigned imp_bytes = (unsigned)nimp * (unsigned)(a.Gpad * sizeof(R));
-        mbar_arrive_expect_tx(full + s, rec_bytes + tq_bytes + imp_bytes);
+        // FP64: the chunk's denominators, a 16-byte aligned superset
+        unsigned den_bytes = 0;
+        int64_t da = 0;
+        if constexpr (sizeof(R) == 8) {
+          constexpr int dper16 = G == 1 ? 2 : 1;   // positions per 16 bytes
+          const int64_t d0 = (int64_t)item * a.N + m.pos;
+          da = d0 / dper16 * dper16;
+          const int64_t de = (d0 + m.len + dper16 - 1) / dper16 * dper16;
+          den_bytes = (unsigned)((de - da) * G * 8);
+        }
+        mbar_arrive_expect_tx(full + s, rec_bytes + tq_bytes + imp_bytes + den_bytes);
         bulk_copy(st, a.rec + (size_t)q0 * RL.size, rec_bytes, full + s);
         bulk_copy(st + a.off_tq, a.tqp + (size_t)qa * 2, tq_bytes, full + s);
+        if (den_bytes) bulk_copy(st + a.off_den, a.dinv + (size_t)da * G, den_bytes, full + s);
         if (nimp > 0)
           bulk_copy(st + a.off_imp, a.imp + ((size_t)g * a.n_imp + a.imp_off[i] + m.imp) * a.Gpad, imp_bytes,
                     full + s);
@@ -287,6 +298,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     const R2* tqs = reinterpret_cast<const R2*>(st + a.off_tq) + tq_shift;
     const R* imps = reinterpret_cast<const R*>(st + a.off_imp);
     const int imp0 = m.imp;
+    // FP64: this chunk's precomputed denominators (superset starts d_shift early)
+    const R* dens = reinterpret_cast<const R*>(st + a.off_den);
+    const int d_shift = sizeof(R) == 8 && G == 1 ? (int)(((int64_t)item * a.N + m.pos) % 2) : 0;
     for (int j = ct; j < m.len; j += ncons) {
       uint4 w[NQ];
 #pragma unroll
@@ -318,7 +332,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       R nl = R(0);
 #pragma unroll
       for (int b = 0; b < G; ++b) {
-        const R phi = (aQ[b] * Q + vb[b] * up[b]) * recip(itau[b] + vb[b] * Gc);
+        R den;
+        if constexpr (sizeof(R) == 8) den = dens[(j + d_shift) * G + b];
+        else den = recip(itau[b] + vb[b] * Gc);
+        const R phi = (aQ[b] * Q + vb[b] * up[b]) * den;
         e[b] = e0[b] + phi;
         nl += wt[b] * phi;
       }
@@ -457,6 +474,26 @@ template <typename R>
 cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
   return a.gring ? launch_gr<R, true>(a, K, G, n_items, threads, smem, st)
                  : launch_gr<R, false>(a, K, G, n_items, threads, smem, st);
+}
+
+// FP64 denominators of every (work item, position); one thread per pair
+__global__ void fill_dinv_kernel(double* dinv, const unsigned char* rec, int rec_bytes, int off_G,
+                                 const double* band_v, const double* band_inv_tau, int D, int ng, int G, int64_t N) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)D * ng * N) return;
+  const int64_t item = t / N, pos = t - item * N;
+  const int i = (int)(item / ng), g = (int)(item - (int64_t)i * ng);
+  const double Gc = *reinterpret_cast<const double*>(rec + ((size_t)i * N + pos) * rec_bytes + off_G);
+  for (int b = 0; b < G; ++b) dinv[t * G + b] = 1.0 / (band_inv_tau[g * G + b] + band_v[g * G + b] * Gc);
+}
+
+cudaError_t launch_fill_dinv(double* dinv, const unsigned char* rec, int rec_bytes, int off_G, const double* band_v,
+                             const double* band_inv_tau, int D, int n_groups, int G, int64_t N, cudaStream_t st) {
+  const int64_t n = (int64_t)D * n_groups * N;
+  if (n == 0) return cudaSuccess;
+  fill_dinv_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dinv, rec, rec_bytes, off_G, band_v, band_inv_tau, D,
+                                                                n_groups, G, N);
+  return cudaGetLastError();
 }
 
 // (T', Qdot) of every position's cell, in each direction's level order, so
