@@ -51,9 +51,21 @@ __global__ void diffuse_kernel(const WallArgs<R> a) {
   if (t >= a.n_dbf * a.Bp) return;
   const int64_t f = t / a.Bp;
   const int b = (int)(t - f * a.Bp);
-  double s = 0.0;
-  for (int64_t k = a.dif_ptr[f]; k < a.dif_ptr[f + 1]; ++k) s += a.dif_wt[k] * exported(a, a.dif_src[k], b);
-  a.dsum[t] = s;
+  // four independent partial sums so that four directions' loads are in
+  // flight at once; combined in a fixed order
+  const int64_t k0 = a.dif_ptr[f], k1 = a.dif_ptr[f + 1];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t k = k0;
+  for (; k + 3 < k1; k += 4) {
+    const int64_t i0 = a.dif_src[k], i1 = a.dif_src[k + 1], i2 = a.dif_src[k + 2], i3 = a.dif_src[k + 3];
+    const double w0 = a.dif_wt[k], w1 = a.dif_wt[k + 1], w2 = a.dif_wt[k + 2], w3 = a.dif_wt[k + 3];
+    s0 += w0 * exported(a, i0, b);
+    s1 += w1 * exported(a, i1, b);
+    s2 += w2 * exported(a, i2, b);
+    s3 += w3 * exported(a, i3, b);
+  }
+  for (; k < k1; ++k) s0 += a.dif_wt[k] * exported(a, a.dif_src[k], b);
+  a.dsum[t] = (s0 + s1) + (s2 + s3);
 }
 
 template <typename R>
