@@ -23,9 +23,16 @@ appearance in Sec. II "Methods"):
   split over bands by heat capacity.
 * Walls (thermalizing / diffuse / specular / partially specular) with the
   reflected values taken from the previous iteration.
+* Optional second-order upwind face values (``order=2``): the gradient
+  operators the paper builds once from the mesh (Sec. II), read as a linear
+  reconstruction from the upwind cell with a least-squares gradient of the
+  previous iteration's distribution, as a right-hand-side correction of the
+  same factorised system.
 
 Points the paper leaves open are read as follows, and each function below
-names the reading it uses: first-order step upwind; wall values lagged one
+names the reading it uses: first-order step upwind by default (second order
+on interior faces only, and only from cells with at least dim + 1 face
+neighbours, when asked for); wall values lagged one
 outer iteration; the synthetic update in its DSA form (the diffusion term at
 the kinetic temperature, Eqs. (8)-(10)), with the correction's equilibrium
 part added to the lagged wall values; a TPFA cell Laplacian with the upwind
@@ -34,7 +41,9 @@ max|dT'| / max|T'|.
 
 Parity status: the transport/moment/wall arithmetic is pinned by the tests in
 ``tests/test_oracle_pins.py`` (closed forms, invariants, brute-force dense
-solves).  The synthetic *iteration path* (how fast it converges) is not pinned
+solves), the second-order reconstruction by ``tests/test_oracle_order2.py``
+(linear exactness, the per-cell energy identity, dense solves of the
+second-order system, the measured order of accuracy).  The synthetic *iteration path* (how fast it converges) is not pinned
 beyond "reaches the same fixed point as the sequential scheme"; the fixed point
 itself is.
 """

@@ -40,6 +40,13 @@ walls):
 
 At iteration 0 the "previous" distribution at the walls is the equilibrium
 ``C_l T'^0_c / W`` of the initial temperature.
+
+Second-order upwind (``order=2``) adds to step 1 the linear reconstruction of
+every interior face value from its upwind cell, with the least-squares
+gradient of the previous sweep's distribution (none before the first sweep):
+a right-hand-side correction of the same factorised system, the
+deferred-correction form of the paper's precomputed gradient operators
+(Sec. II).  Wall faces keep the cell value.
 """
 from __future__ import annotations
 
@@ -199,14 +206,73 @@ class OracleSolver:
         e_in[pm] = p * spec[pm] + (1.0 - p) * diff[pm][:, None]
         return e_in
 
-    def solve_task(self, Tdev, e_in_band, i, l):
+    def solve_task(self, Tdev, e_in_band, i, l, e_prev=None):
         """e'_{l i} over all cells: the transport solve of one (band,
         direction) task of Eq. (4) from the temperature deviation ``Tdev`` and
-        band l's incoming wall values (as returned by :meth:`incoming_band`)."""
+        band l's incoming wall values (as returned by :meth:`incoming_band`).
+        With ``e_prev`` (the task's previous distribution over all cells) the
+        face values are second order (:meth:`second_order_source`)."""
         bi, coef = self._direction(i)[1]
         rhs = self.C[l] * Tdev / (self.W * self.tau[l]) + self.source()[:, l]
         rhs += self.v[l] * np.bincount(self.bcell_of_hf[bi], weights=coef * e_in_band[bi, i], minlength=self.N)
+        if e_prev is not None:
+            rhs += self.v[l] * self.second_order_source(e_prev, i)
         return self._factor(i, l).solve(rhs)
+
+    # ------------------------------------------------------ second-order upwind
+    def lsq_operator(self):
+        """Per cell, the matrix P_c of the least-squares gradient over the
+        cell's face neighbours: grad e_c = P_c sum_m r_m (e_m - e_c) with
+        r_m = x_m - x_c.  P_c is the pseudo-inverse of M_c = sum_m r_m r_m^T
+        (eigenvalues at or below 1e-9 of the largest are dropped, so
+        neighbours spanning only a line or a plane give the gradient within
+        that subspace).  A cell with fewer than dim + 1 face neighbours (a
+        wall triangle or tetrahedron, a corner quadrilateral or hexahedron)
+        gets no gradient: its stencil would be exactly determined, and such
+        extrapolations make the lagged correction grow from one iteration to
+        the next on coarse unstructured meshes in the ballistic limit."""
+        if getattr(self, "_lsq_P", None) is not None:
+            return self._lsq_P
+        g = self.g
+        m = g.hf_nb >= 0
+        r = g.xc[g.hf_nb[m]] - g.xc[g.hf_cell[m]]
+        M = np.zeros((self.N, self.dim, self.dim))
+        np.add.at(M, g.hf_cell[m], r[:, :, None] * r[:, None, :])
+        lam, U = np.linalg.eigh(M)
+        keep = lam > 1e-9 * lam.max(axis=1, keepdims=True)
+        inv = np.where(keep, 1.0 / np.where(keep, lam, 1.0), 0.0)
+        P = np.einsum("cij,cj,ckj->cik", U, inv, U)
+        P[np.bincount(g.hf_cell[m], minlength=self.N) < self.dim + 1] = 0.0
+        self._lsq_P = P
+        return self._lsq_P
+
+    def gradient(self, e):
+        """Least-squares cell gradients (N, dim) of a cell field e."""
+        g = self.g
+        m = g.hf_nb >= 0
+        c, nb = g.hf_cell[m], g.hf_nb[m]
+        b = np.zeros((self.N, self.dim))
+        np.add.at(b, c, (g.xc[nb] - g.xc[c]) * (e[nb] - e[c])[:, None])
+        return np.einsum("cij,cj->ci", self.lsq_operator(), b)
+
+    def second_order_source(self, e, i):
+        """Extra right-hand side of the second-order upwind balance for
+        direction i, from the previous distribution e of the task.
+
+        On every interior face the upwind value is reconstructed linearly
+        from the upwind cell u: e~_f = e_u + grad e_u . (x_f - x_u), with the
+        gradient of the previous iteration (deferred correction); wall faces
+        keep the cell value, so the wall coupling and the energy balance are
+        those of the first-order scheme.  The first-order part stays in the
+        factorised operator of Eq. (13); the increment moves to the right:
+        -sum_f (s_i . An_f / V_c) grad e_u . (x_f - x_u)."""
+        g = self.g
+        m = np.where(g.hf_nb >= 0)[0]
+        a = g.hf_An[m] @ self.s[i]
+        u = np.where(a > 0, g.hf_cell[m], g.hf_nb[m])
+        grad = self.gradient(e)
+        inc = np.sum(grad[u] * (g.hf_xf[m] - g.xc[u]), axis=1)
+        return -np.bincount(g.hf_cell[m], weights=a * inc / g.V[g.hf_cell[m]], minlength=self.N)
 
     def _factor(self, i, l):
         key = (i, l)
@@ -217,12 +283,14 @@ class OracleSolver:
             self._lu[key] = lu
         return lu
 
-    def sweep(self, Tdev, eb_prev, store_e=False, tasks=None):
+    def sweep(self, Tdev, eb_prev, store_e=False, tasks=None, e_prev=None):
         """One transport pass over every (band, direction) task of Eq. (4).
 
         Returns the moments of the new distribution, its values at the wall
         cells (for the next iteration's wall coupling), the incoming wall
-        values that were used, and optionally the full distribution."""
+        values that were used, and optionally the full distribution.  With
+        ``e_prev`` (N, B, D), the previous distribution, the interior face
+        values are second order (:meth:`second_order_source`)."""
         e_in = self.incoming(eb_prev)
         S = self.source()
         NL = np.zeros(self.N)
@@ -236,6 +304,8 @@ class OracleSolver:
             rhs = self.C[l] * Tdev / (self.W * self.tau[l]) + S[:, l]
             rhs += self.v[l] * np.bincount(self.bcell_of_hf[bi], weights=coef * e_in[bi, l, i],
                                            minlength=self.N)
+            if e_prev is not None:
+                rhs += self.v[l] * self.second_order_source(e_prev[:, l, i], i)
             e = self._factor(i, l).solve(rhs)
             NL += self.w[i] * e / self.tau[l]
             E += self.w[i] * e
@@ -345,14 +415,18 @@ class OracleSolver:
 
     # ------------------------------------------------------------------ driver
     def solve(self, scheme=None, tol=None, max_iter=None, n_iter=None, T_init=None, init="tref",
-              store_e=False, verbose=False):
+              store_e=False, verbose=False, order=1):
         """Run the outer iteration.
 
         ``n_iter`` runs exactly that many sweeps (no convergence test);
         otherwise iterate until ``r = |T'^{n+1} - T'^n|_inf / |T'^{n+1}|_inf < tol``.
         ``init="fourier"`` starts from :meth:`fourier_guess` (walls at
-        equilibrium with it) instead of T_init / T_ref.  Returned temperatures
-        are absolute (K)."""
+        equilibrium with it) instead of T_init / T_ref.  ``order=2`` uses
+        second-order upwind face values, each sweep reconstructing from the
+        distribution of the sweep before it (none before the first sweep).
+        Returned temperatures are absolute (K)."""
+        if order not in (1, 2):
+            raise ValueError(order)
         scheme = scheme or self.p.scheme
         tol = self.p.tol if tol is None else tol
         max_iter = self.p.max_iter if max_iter is None else max_iter
@@ -369,8 +443,11 @@ class OracleSolver:
         limit = n_iter if n_iter is not None else max_iter
         out = None
         TL = T
+        e_prev = None
         while it < limit:
-            out = self.sweep(T, eb, store_e=store_e)
+            out = self.sweep(T, eb, store_e=store_e or order == 2, e_prev=e_prev)
+            if order == 2:
+                e_prev = out["e"]
             TL = out["NL"] / self.beta
             if scheme == "sequential":
                 Tn = TL

@@ -52,7 +52,8 @@ def _face_vector(F, dim):
 
 
 def faces_of(mesh):
-    """List of half-faces (cell, nb or None, An outward, tag or None)."""
+    """List of half-faces (cell, nb or None, An outward, tag or None, face
+    centroid)."""
     nodes = mesh.nodes
     out = []
     table = {}
@@ -73,13 +74,37 @@ def faces_of(mesh):
             others = [o for o in owners if o[0] != c]
             nb = others[0][0] if others else None
             tag = None if others else btag[key]
-            out.append((c, nb, An, tag))
+            out.append((c, nb, An, tag, xf))
     return out
 
 
-def solve_fixed_point(problem):
+def lstsq_gradients(mesh, faces):
+    """Per cell: (neighbour list, matrix G) with grad e_c = G (e_nb - e_c),
+    the minimum-norm least-squares fit of a linear field to the face
+    neighbours' values (LAPACK's least-squares solver on the offsets); none
+    (G empty) for a cell with fewer than dim + 1 face neighbours."""
+    xc = np.array([np.mean([mesh.nodes[int(k)] for k in cell], axis=0) for cell in mesh.cells])
+    nbrs = [[] for _ in range(mesh.n_cells)]
+    for (c, nb, An, tag, xf) in faces:
+        if nb is not None:
+            nbrs[c].append(nb)
+    out = []
+    for c in range(mesh.n_cells):
+        if len(nbrs[c]) < mesh.dim + 1:
+            out.append(([], np.zeros((mesh.dim, 0))))
+            continue
+        R = np.array([xc[m] - xc[c] for m in nbrs[c]])
+        G = np.linalg.lstsq(R, np.eye(len(nbrs[c])), rcond=1e-6)[0]
+        out.append((nbrs[c], G))
+    return xc, out
+
+
+def solve_fixed_point(problem, order=1):
     """Dense solve of the converged discrete problem.  Returns (T_L, q) with
-    T_L absolute in K and q of shape (N, dim)."""
+    T_L absolute in K and q of shape (N, dim).  ``order=2``: on interior
+    faces the upwind value is e_u + grad e_u . (x_f - x_u) with the
+    least-squares gradient of :func:`lstsq_gradients` (at the fixed point the
+    lagged gradient equals the current one); wall faces keep the cell value."""
     m = problem.mesh
     dim = m.dim
     N = m.n_cells
@@ -112,7 +137,10 @@ def solve_fixed_point(problem):
                     for j in range(D):
                         A[r, idx(c, l2, j)] -= Vol[c] * C[l] / (Wt * tau[l]) * w[j] / tau[l2] / beta
                 rhs[r] += Vol[c] * Qd[c] * C[l] / (Ct * Wt)
-    for (c, nb, An, tag) in faces_of(m):
+    faces = faces_of(m)
+    if order == 2:
+        xc, grads = lstsq_gradients(m, faces)
+    for (c, nb, An, tag, xf) in faces:
         nrm = An / np.linalg.norm(An)
         n3 = np.zeros(3)
         n3[:dim] = nrm
@@ -120,6 +148,14 @@ def solve_fixed_point(problem):
             a = float(np.dot(sd[i], An))
             for l in range(B):
                 r = idx(c, l, i)
+                if order == 2 and nb is not None and a != 0:
+                    # reconstruction increment grad e_u . (x_f - x_u)
+                    u = c if a > 0 else nb
+                    nbrs, G = grads[u]
+                    wts = (xf - xc[u]) @ G
+                    for mk, wk in zip(nbrs, wts):
+                        A[r, idx(mk, l, i)] += v[l] * a * wk
+                        A[r, idx(u, l, i)] -= v[l] * a * wk
                 if a > 0:
                     A[r, r] += v[l] * a
                 elif a < 0:
