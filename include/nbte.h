@@ -162,6 +162,19 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  *            flux through other walls, L the synthetic correction's TPFA
  *            operator, solved by its CG to 1e-12 (excludes T_init).  Only
  *            the starting point changes, never the converged field.
+ * order:     upwind order of the face values: 0 or 1 = first order (the
+ *            default); 2 = second order on interior faces: the upwind cell's
+ *            value plus its least-squares gradient (over its face
+ *            neighbours) times the offset to the face centroid, the gradient
+ *            taken from the previous iteration's distribution (a deferred
+ *            correction added to the sweep's right-hand side; none in the
+ *            first sweep).  Wall faces keep the cell value, so wall coupling
+ *            and energy conservation are those of the first-order scheme;
+ *            cells with fewer than dim + 1 face neighbours (wall triangles
+ *            and tetrahedra, corner quadrilaterals and hexahedra) carry no
+ *            gradient, which keeps the lagged correction contracting on
+ *            unstructured meshes.  Holds one more distribution and one
+ *            source per (work item, position) on the device.
  * cg_tol, cg_max_iter: relative residual and cap of the conjugate-gradient
  *            solve of the synthetic correction (0 = defaults 1e-2, 5000); the
  *            correction only changes the rate of convergence, not the limit.
@@ -195,6 +208,7 @@ typedef struct {
   int32_t cta_threads;
   int32_t ring;
   int32_t init;
+  int32_t order;
 } nbte_solve_opts;
 
 /* Filled on return from nbte_solve_steady (also on NOT_CONVERGED):

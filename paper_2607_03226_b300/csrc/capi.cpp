@@ -128,8 +128,14 @@ struct nbte_solver {
   // ---- band layout (depends on bands, precision and tuning)
   std::string layout_key, rec_key, chunk_key;
   int prec = 0, G = 1, Gpad = 4, n_groups = 1, Bp = 1, n_items = 0, threads = 160, n_stages = 4;
-  int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0, off_den = 0;
+  int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0, off_den = 0, off_src2 = 0;
   size_t smem = 0;
+  int order = 1;                              // upwind order of the current layout
+  // second-order upwind: previous distribution [n_items*N*G], per-position
+  // sources [n_items*N*G], reconstruction tables (mesh only; kept per precision)
+  DBuf o2_e, o2_src, rc_nb, rc_twin, rc_AnV, rc_a;
+  int rc_prec = -1;
+  int64_t rc_cells = 0;
   double W = 0, beta = 0, Ctot = 0;
   DBuf rec, pos_cell, chunks, chunk_off, tqp, gring, e_scratch, dinv;
   int64_t gring_stride = 0;
@@ -197,7 +203,8 @@ size_t device_bytes(const nbte_solver* S) {
                        &S->cg_rcx, &S->cg_scx, &S->cg_xw, &S->cg_bar, &S->cg_Ainv64,
                        &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell, &S->cg_blk_agg,
                        &S->cg_Ainv, &S->L_ecol, &S->L_eval,
-                       &S->L_diag, &S->L_dinv};
+                       &S->L_diag, &S->L_dinv, &S->o2_e, &S->o2_src, &S->rc_nb, &S->rc_twin,
+                       &S->rc_AnV, &S->rc_a};
   size_t t = 0;
   for (auto* b : all) t += b->bytes;
   return t;
@@ -380,16 +387,21 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   // shared memory of one CTA: barriers and chunk headers, the value ring, and
   // the copy stages (records, (T', Qdot) pairs, imports, and with FP64 the
   // precomputed denominators 1/(1/tau + v G) of the chunk's positions)
+  const bool order2 = o.order == 2;
+  int off_src2 = 0;
   auto stage_of = [&](int Gv, int& off_tq, int& off_imp, int& off_den) {
     const int gpad = padded_group(Gv, sz);
     const int rec = (cap * RL.size + 15) / 16 * 16;
     const int tq = ((cap + 2) * 2 * sz + 15) / 16 * 16;
     const int imp = cap * K * gpad * sz;
     const int den = prec ? 0 : ((cap + 2) * Gv * 8 + 15) / 16 * 16;
+    // second order: the chunk's reconstruction sources (superset of at most cap + 3 positions)
+    const int src2 = order2 ? ((cap + 4) * Gv * sz + 15) / 16 * 16 : 0;
     off_tq = rec;
     off_imp = rec + tq;
     off_den = rec + tq + imp;
-    return rec + tq + imp + den;
+    off_src2 = rec + tq + imp + den;
+    return rec + tq + imp + den + src2;
   };
   // the value ring: in shared memory when it fits beside two copy stages,
   // else one global-memory region per CTA
@@ -432,6 +444,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   // three stages each, then give each CTA as many stages as that allows
   int off_tq = 0, off_imp = 0, off_den = 0;
   const int stage = stage_of(G, off_tq, off_imp, off_den);
+  const int off_src2_sel = off_src2;
   const int ng = (S->B + G - 1) / G;
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S->device);
@@ -452,13 +465,17 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     if (gr) b += (size_t)D * ng * (((size_t)(S->max_slots + 1) * G + 3) / 4 * 4) * sz;   // global rings
     b += N * (4 * sz + 12 * 8 + 8 * (size_t)S->mesh->m.dim);            // per-cell fields
     if (!prec) b += (size_t)D * Bp * N * 8;                              // FP64 denominators
+    if (order2) {                                                        // previous distribution, sources, tables
+      const size_t nf = (size_t)S->mesh->m.nfc;
+      b += 2 * D * Bp * N * sz + N * nf * (8 + 3 * sz + nf * sz);
+    }
     b += D * N / 8 + (size_t)S->n_dbf * Bp * 8 + (size_t)S->n_wf * 16;  // chunks, diffuse sums, wall heat
     *estimate = b;
     return NBTE_OK;
   }
   const std::string key = std::to_string(prec) + "/" + std::to_string(G) + "/" + std::to_string(cap) + "/" +
                           std::to_string(S->version_bands) + "/" + std::to_string(S->plan_built) + "/" +
-                          std::to_string(ns) + (gr ? "/global" : "/shared");
+                          std::to_string(ns) + (gr ? "/global" : "/shared") + (order2 ? "/o2" : "/o1");
   if (key == S->layout_key) return NBTE_OK;
   DeviceGuard dg(S->device);
   drop_graph(S);
@@ -474,6 +491,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   S->off_tq = off_tq;
   S->off_imp = off_imp;
   S->off_den = off_den;
+  S->off_src2 = off_src2_sel;
+  S->order = order2 ? 2 : 1;
   S->off_ring = head;
   S->off_stage = head + (int)ringB;
   S->gring_stride = gr ? ((int64_t)(S->max_slots + 1) * G + 3) / 4 * 4 : 0;
@@ -534,6 +553,33 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     NBTE_CK(cudaStreamSynchronize(S->stream));
   } else {
     S->dinv.release();
+  }
+  if (order2) {
+    // second-order upwind: the previous sweep's distribution (zero = no
+    // reconstruction yet) and the per-position sources (+16 positions: a
+    // chunk's 16-byte aligned copy may run past the last position)
+    NBTE_CK(S->o2_e.alloc((size_t)S->n_items * N * G * sz));
+    NBTE_CK(S->o2_src.alloc(((size_t)S->n_items * N + 16) * G * sz));
+    NBTE_CK(cudaMemset(S->o2_e.p, 0, S->o2_e.bytes));
+    NBTE_CK(cudaMemset(S->o2_src.p, 0, S->o2_src.bytes));
+    if (S->rc_prec != prec || !S->rc_a.p) {
+      Reconstruction rcn;
+      build_reconstruction(S->mesh->m, rcn);
+      NBTE_CK(upload(S->rc_nb, rcn.nb));
+      NBTE_CK(upload(S->rc_twin, rcn.twin));
+      if (prec) {
+        NBTE_CK(upload(S->rc_AnV, to_float(rcn.AnV)));
+        NBTE_CK(upload(S->rc_a, to_float(rcn.a)));
+      } else {
+        NBTE_CK(upload(S->rc_AnV, rcn.AnV));
+        NBTE_CK(upload(S->rc_a, rcn.a));
+      }
+      S->rc_prec = prec;
+      S->rc_cells = rcn.cells_with_gradient;
+    }
+  } else {
+    S->o2_e.release();
+    S->o2_src.release();
   }
   NBTE_CK(S->T.alloc(N * 8));
   NBTE_CK(S->Tprev.alloc(N * 8));
@@ -766,7 +812,11 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.off_tq = S->off_tq;
   a.off_imp = S->off_imp;
   a.off_den = S->off_den;
+  a.off_src2 = S->off_src2;
   a.dinv = S->dinv.p ? S->dinv.as<R>() : nullptr;
+  a.src2 = S->order == 2 ? S->o2_src.as<R>() : nullptr;
+  a.e_out = S->order == 2 ? S->o2_e.as<R>() : nullptr;
+  a.e_out_stride = (int64_t)a.N * S->G;
   a.n_exp = S->n_exp;
   a.n_imp = S->n_imp;
   a.item_dir = S->item_dir.as<int32_t>();
@@ -892,12 +942,35 @@ CGArgs cg_args(nbte_solver* S, double tol, int max_it) {
 //         either applied (Eq. (6)) or turned into the synthetic rhs;
 //   post: the synthetic update (Eq. (12)) and the residual words to the host.
 template <typename R>
+Src2Args<R> src2_args(nbte_solver* S) {
+  Src2Args<R> a{};
+  a.N = (int)S->mesh->m.n_cells;
+  a.nfc = S->mesh->m.nfc;
+  a.G = S->G;
+  a.n_items = S->n_items;
+  a.e = S->o2_e.as<R>();
+  a.src2 = S->o2_src.as<R>();
+  a.item_dir = S->item_dir.as<int32_t>();
+  a.pos_cell = S->pos_cell.as<int32_t>();
+  a.nb = S->rc_nb.as<int32_t>();
+  a.twin = S->rc_twin.as<int32_t>();
+  a.AnV = S->rc_AnV.as<R>();
+  a.rc_a = S->rc_a.as<R>();
+  a.dir_s = S->dir_s.as<double>();
+  return a;
+}
+
+template <typename R>
 cudaError_t enqueue_pre(nbte_solver* S, cudaStream_t st) {
   launch_walls<R>(wall_args<R>(S), st);
   cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  return launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
-                             (int64_t)S->D * S->mesh->m.n_cells, st);
+  e = launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
+                          (int64_t)S->D * S->mesh->m.n_cells, st);
+  if (e != cudaSuccess) return e;
+  // second order: this sweep's reconstruction sources from the previous sweep's distribution
+  if (S->order == 2) e = launch_src2<R>(src2_args<R>(S), st);
+  return e;
 }
 
 template <typename R>
@@ -982,6 +1055,7 @@ int init_state(nbte_solver* S, const nbte_solve_opts& o) {
   }
   NBTE_CK(cudaMemsetAsync(S->Delta.p, 0, N * 8, st));
   NBTE_CK(cudaMemsetAsync(S->Tkin.p, 0, N * 8, st));
+  if (S->order == 2) NBTE_CK(cudaMemsetAsync(S->o2_e.p, 0, S->o2_e.bytes, st));   // no reconstruction in sweep 1
   launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)N, st);
   launch_init_exports<R>(S->expt.as<R>(), S->exp_cell.as<int32_t>(), S->T.as<double>(), S->band_CoW.as<double>(),
                          S->Bp, S->G, S->Gpad, S->n_exp, st);
@@ -1092,7 +1166,7 @@ struct Run {
   std::chrono::steady_clock::time_point t0, t1;
 
   int64_t kernels_per_iter() const {
-    return (S->n_dbf > 0) + (S->n_imp > 0) + 2 + (o.scheme == 0 ? 1 : 3);
+    return (S->n_dbf > 0) + (S->n_imp > 0) + 2 + (o.scheme == 0 ? 1 : 3) + (S->order == 2);
   }
   // after an iteration's residual words reached the host: true to stop
   bool check() {
@@ -1888,6 +1962,7 @@ static int check_opts(const nbte_solve_opts& o) {
   if (o.ring < 0 || o.ring > 2) return fail(NBTE_ERR_ARG, "ring must be 0, 1 or 2");
   if (o.init < 0 || o.init > 1) return fail(NBTE_ERR_ARG, "init must be 0 or 1");
   if (o.init == 1 && o.T_init) return fail(NBTE_ERR_ARG, "init = 1 (diffusion guess) excludes T_init");
+  if (o.order < 0 || o.order > 2) return fail(NBTE_ERR_ARG, "order must be 0 (= 1), 1 or 2");
   return NBTE_OK;
 }
 
@@ -2069,6 +2144,7 @@ static int distribution(nbte_solver* S, int dir, int band, double* out) {
   SweepArgs<R> a = sweep_args<R>(S, 0);
   a.item0 = dir * S->n_groups + band / G;
   a.e_out = S->e_scratch.as<R>();
+  a.e_out_stride = 0;
   NBTE_CK(launch_sweep<R>(a, S->K, G, 1, S->threads, S->smem, st));
   std::vector<R> tmp((size_t)N * G);
   NBTE_CK(cudaMemcpyAsync(tmp.data(), S->e_scratch.p, tmp.size() * sizeof(R), cudaMemcpyDeviceToHost, st));

@@ -22,8 +22,10 @@ struct SweepArgs {
   int full;                      // also accumulate E and q (atomics)
   int Gpad;                      // padded row length of the import/export tables
   int n_stages;                  // shared-memory stages of the copy pipeline
-  int stage_bytes, off_ring, off_stage, off_tq, off_imp, off_den;   // shared-memory layout
+  int stage_bytes, off_ring, off_stage, off_tq, off_imp, off_den, off_src2;   // shared-memory layout
   const R* dinv;                 // FP64 only: [n_items*N*G] denominators 1/(1/tau + v G), else null
+  const R* src2;                 // second-order upwind: [n_items*N*G] per position, the
+                                 // reconstruction's extra source (sum over faces), else null
   int64_t n_exp, n_imp;
   const int32_t* item_dir;       // [n_items]
   const int32_t* item_grp;       // [n_items]
@@ -42,7 +44,9 @@ struct SweepArgs {
   const double* dir_w;           // [D]
   const double* dir_s;           // [D*3]
   int item0;                     // first work item of the launch (block b runs item item0 + b)
-  R* e_out;                      // null, or [N*G]: every cell's outgoing values of the item's bands
+  R* e_out;                      // null, or every cell's outgoing values of the item's bands at
+                                 // e_out + item * e_out_stride + cell * G
+  int64_t e_out_stride;
   R* gring;                      // global-memory value rings, or null for the shared-memory ring
   int64_t gring_stride;          // elements per CTA's global ring
   R* part;                       // [n_items*N] collision-moment partials (of e - e0)
@@ -66,6 +70,28 @@ cudaError_t launch_fill_dinv(double* dinv, const unsigned char* rec, int rec_byt
                              const double* band_inv_tau, int D, int n_groups, int G, int64_t N, cudaStream_t st);
 template <typename R>
 cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st);
+
+// Second-order upwind source of every work item and position, from the
+// previous sweep's distribution e[(item*N + cell)*G + b]:
+//   src2 = -sum over the cell's interior faces f of (s_i . An_f / V) *
+//          sum_m rc_a[u, f_u, m] (e[nb(u, m)] - e[u]),
+// u the face's upwind cell (the cell itself on outflow faces) and f_u the
+// face's local index in u.  Written at src2[(item*N + pos)*G + b].
+template <typename R>
+struct Src2Args {
+  int N, nfc, G, n_items;
+  const R* e;
+  R* src2;
+  const int32_t* item_dir;
+  const int32_t* pos_cell;       // [D*N] cell of each position
+  const int32_t* nb;             // [N*nfc] neighbour or -1
+  const int32_t* twin;           // [N*nfc] the face's local index in the neighbour
+  const R* AnV;                  // [N*nfc*3] outward face vector / cell volume
+  const R* rc_a;                 // [N*nfc*nfc] reconstruction weights
+  const double* dir_s;           // [D*3]
+};
+template <typename R>
+cudaError_t launch_src2(const Src2Args<R>& a, cudaStream_t st);
 
 template <typename R>
 void launch_init_exports(R* exp, const int32_t* exp_cell, const double* Tdev, const double* CoW, int Bp, int G,

@@ -103,6 +103,20 @@ struct Laplacian {
 void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bulk, double k1,
                      Laplacian& L);
 
+// Second-order upwind reconstruction tables (internal cell order): per
+// half-face h = c*nfc + k the neighbour (or -1), the face's local index in the
+// neighbour, An/V (3 components, z = 0 in 2D), and per (h, m) the weight
+// a[h*nfc + m] = (P_c r_m) . (x_f - x_c) of the least-squares gradient
+// (P_c the pseudo-inverse of sum_m r_m r_m^T, r_m = x_nb(m) - x_c), so that
+// e_f - e_c = sum_m a (e_nb(m) - e_c); zero for wall faces m and for cells
+// with fewer than dim + 1 face neighbours.
+struct Reconstruction {
+  std::vector<int32_t> nb, twin;
+  std::vector<double> AnV, a;
+  int64_t cells_with_gradient = 0;
+};
+void build_reconstruction(const Mesh& m, Reconstruction& rc);
+
 // geometric aggregates (boxes of the cell-centroid bounding box); returns the
 // number of non-empty aggregates, agg[c] in [0, n)
 int build_aggregates(const Mesh& m, int target, std::vector<int32_t>& agg);

@@ -494,4 +494,99 @@ void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bul
   }
 }
 
+namespace {
+// eigenvalues lam and eigenvectors (columns of U, row-major) of a symmetric
+// n x n matrix (n <= 3) by cyclic Jacobi rotations
+void sym_eigen(int n, double A[3][3], double lam[3], double U[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) U[i][j] = i == j ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += A[i][j] * A[i][j];
+        if (i != j) off += A[i][j] * A[i][j];
+      }
+    if (off <= 1e-32 * tot) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (A[p][q] == 0.0) continue;
+        // rotation angle that zeroes A[p][q]
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {   // A <- A J
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - sn * akq;
+          A[k][q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {   // A <- J^T A
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - sn * aqk;
+          A[q][k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {   // U <- U J
+          const double ukp = U[k][p], ukq = U[k][q];
+          U[k][p] = c * ukp - sn * ukq;
+          U[k][q] = sn * ukp + c * ukq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) lam[i] = A[i][i];
+}
+}  // namespace
+
+void build_reconstruction(const Mesh& m, Reconstruction& rc) {
+  const int64_t N = m.n_cells;
+  const int nf = m.nfc, dim = m.dim;
+  rc.nb.assign((size_t)N * nf, -1);
+  rc.twin.assign((size_t)N * nf, -1);
+  rc.AnV.assign((size_t)N * nf * 3, 0.0);
+  rc.a.assign((size_t)N * nf * nf, 0.0);
+  rc.cells_with_gradient = 0;
+  for (int64_t c = 0; c < N; ++c) {
+    int n_nb = 0;
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double r[6][3] = {};
+    for (int k = 0; k < nf; ++k) {
+      const int64_t h = c * nf + k;
+      for (int d = 0; d < dim; ++d) rc.AnV[h * 3 + d] = m.An[h * dim + d] / m.V[c];
+      const int64_t nk = m.nb[h];
+      if (nk < 0) continue;
+      rc.nb[h] = (int32_t)nk;
+      rc.twin[h] = (int32_t)(m.twin[h] - nk * nf);
+      ++n_nb;
+      for (int d = 0; d < dim; ++d) r[k][d] = m.xc[nk * dim + d] - m.xc[c * dim + d];
+      for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) M[i][j] += r[k][i] * r[k][j];
+    }
+    // exactly determined stencils (fewer than dim + 1 neighbours) get no gradient
+    if (n_nb < dim + 1) continue;
+    double lam[3], U[3][3];
+    sym_eigen(dim, M, lam, U);
+    double lmax = 0.0;
+    for (int i = 0; i < dim; ++i) lmax = std::max(lmax, lam[i]);
+    // P = pseudo-inverse of M (eigenvalues at or below 1e-9 lmax dropped)
+    double P[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int e = 0; e < dim; ++e) {
+      if (!(lam[e] > 1e-9 * lmax)) continue;
+      for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) P[i][j] += U[i][e] * U[j][e] / lam[e];
+    }
+    ++rc.cells_with_gradient;
+    for (int mm = 0; mm < nf; ++mm) {
+      if (m.nb[c * nf + mm] < 0) continue;
+      double g[3] = {0, 0, 0};   // P r_m
+      for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) g[i] += P[i][j] * r[mm][j];
+      for (int k = 0; k < nf; ++k) {
+        const int64_t h = c * nf + k;
+        double w = 0.0;
+        for (int d = 0; d < dim; ++d) w += g[d] * (m.xf[h * dim + d] - m.xc[c * dim + d]);
+        rc.a[(size_t)h * nf + mm] = w;
+      }
+    }
+  }
+}
+
 }  // namespace nbte

@@ -25,8 +25,11 @@
 //
 // Per cell and band the balance is solved for the deviation from the cell's
 // own equilibrium e0 = C T'/W (Eq. (11)):
-//   e = e0 + (Qdot C/(C_tot W) + v sum_in c_k (e_up,k - e0)) / (1/tau + v G),
-//   c_k = |s.An_k|/V,  G = sum_in c_k  (= sum_out (s.An)/V for a closed cell).
+//   e = e0 + (Qdot C/(C_tot W) + v sum_in c_k (e_up,k - e0) + v src2) / (1/tau + v G),
+//   c_k = |s.An_k|/V,  G = sum_in c_k  (= sum_out (s.An)/V for a closed cell),
+// src2 = 0 for first-order upwind; with second-order face values it is the
+// reconstruction increment of every interior face taken from the previous
+// iteration's gradients (deferred correction, see launch_src2).
 // The collision-moment partial is sum_l w_i (e - e0)/tau_l; the equilibrium
 // part sums to beta T' exactly and is added back in FP64 by the update kernel.
 #include <cuda_runtime.h>
@@ -250,10 +253,21 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
           const int64_t de = (d0 + m.len + dper16 - 1) / dper16 * dper16;
           den_bytes = (unsigned)((de - da) * G * 8);
         }
-        mbar_arrive_expect_tx(full + s, rec_bytes + tq_bytes + imp_bytes + den_bytes);
+        // second order: the chunk's reconstruction sources, a 16-byte aligned superset
+        unsigned s2_bytes = 0;
+        int64_t sa = 0;
+        if (a.src2) {
+          constexpr int sper16 = (int)(16 / (G * sizeof(R))) > 1 ? (int)(16 / (G * sizeof(R))) : 1;
+          const int64_t s0 = (int64_t)item * a.N + m.pos;
+          sa = s0 / sper16 * sper16;
+          const int64_t se = (s0 + m.len + sper16 - 1) / sper16 * sper16;
+          s2_bytes = (unsigned)((se - sa) * G * sizeof(R));
+        }
+        mbar_arrive_expect_tx(full + s, rec_bytes + tq_bytes + imp_bytes + den_bytes + s2_bytes);
         bulk_copy(st, a.rec + (size_t)q0 * RL.size, rec_bytes, full + s);
         bulk_copy(st + a.off_tq, a.tqp + (size_t)qa * 2, tq_bytes, full + s);
         if (den_bytes) bulk_copy(st + a.off_den, a.dinv + (size_t)da * G, den_bytes, full + s);
+        if (s2_bytes) bulk_copy(st + a.off_src2, a.src2 + (size_t)sa * G, s2_bytes, full + s);
         if (nimp > 0)
           bulk_copy(st + a.off_imp, a.imp + ((size_t)g * a.n_imp + a.imp_off[i] + m.imp) * a.Gpad, imp_bytes,
                     full + s);
@@ -301,6 +315,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     // FP64: this chunk's precomputed denominators (superset starts d_shift early)
     const R* dens = reinterpret_cast<const R*>(st + a.off_den);
     const int d_shift = sizeof(R) == 8 && G == 1 ? (int)(((int64_t)item * a.N + m.pos) % 2) : 0;
+    // second order: this chunk's reconstruction sources (superset starts s_shift early)
+    constexpr int sper16 = (int)(16 / (G * sizeof(R))) > 1 ? (int)(16 / (G * sizeof(R))) : 1;
+    const R* s2 = reinterpret_cast<const R*>(st + a.off_src2);
+    const int s_shift = (int)(((int64_t)item * a.N + m.pos) % sper16);
+    const bool has_s2 = a.src2 != nullptr;
     for (int j = ct; j < m.len; j += ncons) {
       uint4 w[NQ];
 #pragma unroll
@@ -328,6 +347,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
 #pragma unroll
         for (int b = 0; b < G; ++b) up[b] += cf * (eu[b] - e0[b]);
       }
+      if (has_s2) {
+#pragma unroll
+        for (int b = 0; b < G; ++b) up[b] += s2[(j + s_shift) * G + b];
+      }
       R e[G];
       R nl = R(0);
 #pragma unroll
@@ -341,7 +364,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       }
       if (slot >= 0) store_vals<R, G>(ring + slot * G, e);
       if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * GP, e);
-      if (a.e_out) store_vals<R, G>(a.e_out + (size_t)cell * G, e);
+      if (a.e_out) store_vals<R, G>(a.e_out + (size_t)item * a.e_out_stride + (size_t)cell * G, e);
       part[cell] = nl;
       if (a.full) {
         R es = R(0), evs = R(0);
@@ -506,6 +529,89 @@ __global__ void gather_tq_kernel(R* tqp, const int32_t* pos_cell, const R* srcTQ
   reinterpret_cast<R2*>(tqp)[q] = __ldg(reinterpret_cast<const R2*>(srcTQ) + __ldcs(pos_cell + q));
 }
 
+// Second-order upwind sources: one thread per (work item, position), the
+// item's G bands in registers.  Reads the previous sweep's values of the
+// cell, its face neighbours and (on inflow faces) the upwind neighbour's own
+// neighbours; one direction-and-band-group slice of e is N*G values, so the
+// two-ring gathers of the blocks working on an item stay in L2.
+template <typename R, int G, int NF>
+__global__ void __launch_bounds__(256) src2_kernel(const Src2Args<R> a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)a.n_items * a.N) return;
+  const int item = (int)(t / a.N);
+  const int p = (int)(t - (int64_t)item * a.N);
+  const int i = __ldg(a.item_dir + item);
+  const int c = __ldg(a.pos_cell + (int64_t)i * a.N + p);
+  const R* e = a.e + (size_t)item * a.N * G;
+  const R sx = (R)a.dir_s[i * 3], sy = (R)a.dir_s[i * 3 + 1], sz = (R)a.dir_s[i * 3 + 2];
+  R ec[G], acc[G];
+  load_vals<R, G>(e + (size_t)c * G, ec);
+#pragma unroll
+  for (int b = 0; b < G; ++b) acc[b] = R(0);
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    const int nk = __ldg(a.nb + (int64_t)c * NF + k);
+    if (nk < 0) continue;
+    const R* An = a.AnV + ((int64_t)c * NF + k) * 3;
+    const R d = sx * An[0] + sy * An[1] + sz * An[2];
+    if (d == R(0)) continue;
+    int u = c, h = k;
+    R eu[G];
+    if (d > R(0)) {
+#pragma unroll
+      for (int b = 0; b < G; ++b) eu[b] = ec[b];
+    } else {
+      u = nk;
+      h = __ldg(a.twin + (int64_t)c * NF + k);
+      load_vals<R, G>(e + (size_t)u * G, eu);
+    }
+    const R* w = a.rc_a + ((int64_t)u * NF + h) * NF;
+    R inc[G];
+#pragma unroll
+    for (int b = 0; b < G; ++b) inc[b] = R(0);
+#pragma unroll
+    for (int m2 = 0; m2 < NF; ++m2) {
+      const R wm = __ldg(w + m2);
+      if (wm == R(0)) continue;   // wall face, or a cell without a gradient
+      const int nm = __ldg(a.nb + (int64_t)u * NF + m2);
+      R en[G];
+      load_vals<R, G>(e + (size_t)nm * G, en);
+#pragma unroll
+      for (int b = 0; b < G; ++b) inc[b] += wm * (en[b] - eu[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < G; ++b) acc[b] -= d * inc[b];
+  }
+  store_vals<R, G>(a.src2 + (size_t)t * G, acc);
+}
+
+template <typename R, int G>
+static cudaError_t launch_src2_g(const Src2Args<R>& a, cudaStream_t st) {
+  const int64_t n = (int64_t)a.n_items * a.N;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  switch (a.nfc) {
+    case 3: src2_kernel<R, G, 3><<<grid, 256, 0, st>>>(a); break;
+    case 4: src2_kernel<R, G, 4><<<grid, 256, 0, st>>>(a); break;
+    case 6: src2_kernel<R, G, 6><<<grid, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_src2(const Src2Args<R>& a, cudaStream_t st) {
+  if ((int64_t)a.n_items * a.N == 0) return cudaSuccess;
+  switch (a.G) {
+    case 1: return launch_src2_g<R, 1>(a, st);
+    case 2: return launch_src2_g<R, 2>(a, st);
+    case 4: return launch_src2_g<R, 4>(a, st);
+    case 8:
+      if constexpr (sizeof(R) == 4) return launch_src2_g<R, 8>(a, st);
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename R>
 cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
@@ -519,6 +625,8 @@ template cudaError_t launch_sweep_batch<float>(const SweepArgs<float>*, const in
 template cudaError_t launch_sweep_batch<double>(const SweepArgs<double>*, const int32_t*, int, int, int, bool, int,
                                                 int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_src2<float>(const Src2Args<float>&, cudaStream_t);
+template cudaError_t launch_src2<double>(const Src2Args<double>&, cudaStream_t);
 template cudaError_t launch_gather_tq<float>(float*, const int32_t*, const float*, int64_t, cudaStream_t);
 template cudaError_t launch_gather_tq<double>(double*, const int32_t*, const double*, int64_t, cudaStream_t);
 

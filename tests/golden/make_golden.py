@@ -4,7 +4,8 @@ Calls only ``oracle/`` and the seeded generators in ``workloads/``.  Each
 output file records the command, the problem parameters and the oracle's
 iteration count; values are absolute temperatures (K) and heat fluxes (W/m^2).
 
-Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_converged ...]
+Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_converged|
+                                            finfet2d_order2_steps ...]
 
 * ``square``              - the 40x40 in-plane square, sequential to 1e-12
                             (all 1600 cells).
@@ -13,6 +14,10 @@ Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_conve
                             1 and 2 from T_ref, on 4096 seeded sample cells.
 * ``finfet2d_converged``  - the same problem converged (sequential, 1e-10),
                             T_L and q on the sample cells.
+* ``finfet2d_order2_steps`` - the same fin with second-order upwind face
+                            values: T_L after sequential iterations 2 and 3
+                            from T_ref (the first iteration has no
+                            reconstruction yet), on the sample cells.
 * ``cube3d_tasks`` / ``finfet3d_tasks`` - the 64^3 cube and the 1.14M-tet
                             FinFET at full size: the distribution e'_{l i} of
                             a few (direction, band) tasks in the first
@@ -87,6 +92,22 @@ def finfet2d_converged():
         converged=r["converged"], seconds=time.time() - t, sample_seed=SAMPLE_SEED,
         cells=idx.tolist(), T=r["T"][idx].tolist(), q=r["q"][idx].tolist(),
         T_max=float(r["T"].max()), energy_imbalance=r["energy_imbalance"]))
+
+
+def finfet2d_order2_steps():
+    p = W.problems.finfet2d()
+    o = OracleSolver(p)
+    idx = _sample(p.n_cells)
+    out = dict(problem="finfet2d()", scheme="sequential", order=2, sample_seed=SAMPLE_SEED,
+               cells=idx.tolist())
+    for n in (2, 3):
+        t = time.time()
+        r = o.solve(scheme="sequential", n_iter=n, order=2)
+        out[f"T_iter{n}"] = r["T"][idx].tolist()
+        out[f"T_iter{n}_max_dev"] = float(np.abs(r["T"] - p.T_ref).max())
+        out[f"seconds_iter{n}"] = time.time() - t
+        print("iter", n, "done", time.time() - t, flush=True)
+    _write("finfet2d_order2_steps.json", out)
 
 
 def _tasks(name, p, tasks):

@@ -129,6 +129,9 @@ def test_setup_argument_errors(lib):
     with pytest.raises(nbte.NbteError) as e:
         nbte.nbte_solve_steady(s, nbte.make_opts(tol=-1.0))
     assert e.value.code == nbte.NBTE_ERR_ARG
+    with pytest.raises(nbte.NbteError) as e:
+        nbte.nbte_solve_steady(s, nbte.make_opts(order=3))
+    assert e.value.code == nbte.NBTE_ERR_ARG
     nbte.nbte_solver_destroy(s)
     nbte.nbte_mesh_destroy(h)
 
