@@ -118,7 +118,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def sweep_algorithmic_bytes(st, n_cells, n_dirs, prec_bytes, Bp):
+def sweep_algorithmic_bytes(st, n_cells, n_dirs, prec_bytes, Bp, order=1):
     """Bytes one sweep launch must move to or from HBM at minimum:
     * each direction's position records once (cell, ring slot, export index,
       diagonal G, and K inflow references and coefficients; the 16-byte
@@ -128,11 +128,16 @@ def sweep_algorithmic_bytes(st, n_cells, n_dirs, prec_bytes, Bp):
     * the (T', Qdot) pair of every cell once;
     * the wall/lag import values read and the export values written
       (boundary cells only), all bands.
-    Upwind values live in the shared-memory ring and cost no HBM traffic."""
+    Upwind values live in the shared-memory ring and cost no HBM traffic.
+    Second order adds, per (direction, cell, band), the reconstruction source
+    read and the outgoing value kept for the next iteration's gradients."""
     K = st["K"]
     rec = 3 * 4 + prec_bytes + K * (4 + prec_bytes)
-    return (n_dirs * n_cells * rec + st["items"] * n_cells * prec_bytes + n_cells * 2 * prec_bytes
-            + (st["exports"] + st["imports"]) * Bp * prec_bytes)
+    b = (n_dirs * n_cells * rec + st["items"] * n_cells * prec_bytes + n_cells * 2 * prec_bytes
+         + (st["exports"] + st["imports"]) * Bp * prec_bytes)
+    if order == 2:
+        b += 2 * n_dirs * n_cells * Bp * prec_bytes
+    return b
 
 
 def _sweep_traffic(G, threads):
@@ -180,7 +185,7 @@ def run_gpu(args):
     solver = nbte.Solver(p, stream=stream.cuda_stream)
     kw = dict(scheme=args.scheme, precision=args.precision, cg_tol=args.cg_tol, cg_max_iter=args.cg_max_iter,
               band_group=args.band_group, cta_threads=args.cta_threads, use_graph=True,
-              skip_outputs=True)
+              skip_outputs=True, order=args.order)
     stats = solver.plan_stats(**kw)
     upd = p.updates_per_iteration
     # warm-up (includes planning, upload and graph capture) then the timed steps
@@ -212,7 +217,7 @@ def run_gpu(args):
     G = stats["band_group"]
     n_items = stats["items"]
     Bp = n_items // p.n_dirs * G
-    bytes_launch = sweep_algorithmic_bytes(stats, p.n_cells, p.n_dirs, prec_b, Bp)
+    bytes_launch = sweep_algorithmic_bytes(stats, p.n_cells, p.n_dirs, prec_b, Bp, args.order)
     peak, peak_kind = _peaks()
     achieved = bytes_launch / (sweep_ms * 1e-3) / 1e9
 
@@ -239,6 +244,32 @@ def run_gpu(args):
         ttc[sch] = {"seconds": e0.elapsed_time(e1) * 1e-3, "iterations": ic["iterations"],
                     "residual": ic["residual"], "status": ic["status"]}
 
+    # the other upwind order: its step (the second-order step adds the
+    # reconstruction-source gather and the sweep's extra input), its sweep,
+    # and its time to a converged field
+    order_o = 2 if args.order == 1 else 1
+    kw_r = dict(kw, order=order_o)
+    solver.solve(n_iter=3, **kw_r)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    solver.solve(n_iter=args.steps, warm=True, **kw_r)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1) / args.steps
+    prof_r = solver.solve(n_iter=args.steps, warm=True, profile=True,
+                          **{k: v for k, v in kw_r.items() if k != "use_graph"})
+    kw_rc = dict(kw_r, tol=tol_c, max_iter=20000)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ic = solver.solve(**kw_rc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    order_step = {"ms_per_step": ms_r, "updates_per_s": upd / (ms_r * 1e-3),
+                  "sweep_ms": prof_r["sweep_seconds"] * 1e3 / max(1, prof_r["sweep_launches"]),
+                  "time_to_converged": {"scheme": args.scheme, "seconds": e0.elapsed_time(e1) * 1e-3,
+                                        "iterations": ic["iterations"], "residual": ic["residual"],
+                                        "status": ic["status"]}}
+
     # end to end through the public API with host buffers: per step the heat
     # source goes host->device, one iteration runs, the temperature comes back
     Qh = np.ascontiguousarray(p.Q, dtype=np.float64)
@@ -262,6 +293,7 @@ def run_gpu(args):
         "data": "synthetic (seeded mesh, spectrum and hot spot)",
         "config": {"workload": WORKLOAD, "n_cells": p.n_cells, "bands": p.n_bands, "directions": p.n_dirs,
                    "updates_per_step": upd, "scheme": args.scheme, "precision": args.precision, "cg_tol": args.cg_tol,
+                   "upwind_order": args.order,
                    "band_group": G, "cta_threads": stats["cta_threads"], "items": n_items, "levels_max": stats["max_levels"],
                    "ring_slots_max": stats["max_slots"], "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2: per-step device footprint %.0f MB > 126 MB" % (
@@ -272,10 +304,11 @@ def run_gpu(args):
         other + "_step": {"ms_per_step": ms_o, "updates_per_s": upd / (ms_o * 1e-3),
                           "cg_iterations_per_step": info_o["cg_iterations"] / max(1, args.steps)},
         "time_to_converged": dict(ttc, tol=tol_c, start="T_ref"),
+        "upwind_order_%d_step" % order_o: order_step,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": (_sweep_traffic(G, stats["cta_threads"])
-                                 if args.precision == "fp32" else None),
+                                 if args.precision == "fp32" and args.order == 1 else None),
                      "kernel": "sweep_kernel", "sweep_ms": sweep_ms,
                      "algorithmic_bytes_per_launch": bytes_launch},
         "clocks": clocks,
@@ -518,6 +551,8 @@ def main():
     ap.add_argument("--band-group", type=int, default=0)
     ap.add_argument("--cta-threads", type=int, default=0)
     ap.add_argument("--cg-tol", type=float, default=1e-2)
+    ap.add_argument("--order", type=int, default=1, choices=[1, 2],
+                    help="upwind order of the face values (2: deferred least-squares reconstruction)")
     ap.add_argument("--cg-max-iter", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -816,7 +816,10 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.dinv = S->dinv.p ? S->dinv.as<R>() : nullptr;
   a.src2 = S->order == 2 ? S->o2_src.as<R>() : nullptr;
   a.e_out = S->order == 2 ? S->o2_e.as<R>() : nullptr;
-  a.e_out_stride = (int64_t)a.N * S->G;
+  // second order keeps the distribution as [direction][cell][band]
+  a.e_out_dstride = (int64_t)a.N * S->Bp;
+  a.e_out_gstride = S->G;
+  a.e_out_cstride = S->Bp;
   a.n_exp = S->n_exp;
   a.n_imp = S->n_imp;
   a.item_dir = S->item_dir.as<int32_t>();
@@ -948,9 +951,11 @@ Src2Args<R> src2_args(nbte_solver* S) {
   a.nfc = S->mesh->m.nfc;
   a.G = S->G;
   a.n_items = S->n_items;
+  a.n_groups = S->n_groups;
+  a.Bp = S->Bp;
+  a.D = S->D;
   a.e = S->o2_e.as<R>();
   a.src2 = S->o2_src.as<R>();
-  a.item_dir = S->item_dir.as<int32_t>();
   a.pos_cell = S->pos_cell.as<int32_t>();
   a.nb = S->rc_nb.as<int32_t>();
   a.twin = S->rc_twin.as<int32_t>();
@@ -2144,7 +2149,9 @@ static int distribution(nbte_solver* S, int dir, int band, double* out) {
   SweepArgs<R> a = sweep_args<R>(S, 0);
   a.item0 = dir * S->n_groups + band / G;
   a.e_out = S->e_scratch.as<R>();
-  a.e_out_stride = 0;
+  a.e_out_dstride = 0;
+  a.e_out_gstride = 0;
+  a.e_out_cstride = G;
   NBTE_CK(launch_sweep<R>(a, S->K, G, 1, S->threads, S->smem, st));
   std::vector<R> tmp((size_t)N * G);
   NBTE_CK(cudaMemcpyAsync(tmp.data(), S->e_scratch.p, tmp.size() * sizeof(R), cudaMemcpyDeviceToHost, st));

@@ -45,8 +45,8 @@ struct SweepArgs {
   const double* dir_s;           // [D*3]
   int item0;                     // first work item of the launch (block b runs item item0 + b)
   R* e_out;                      // null, or every cell's outgoing values of the item's bands at
-                                 // e_out + item * e_out_stride + cell * G
-  int64_t e_out_stride;
+                                 // e_out + i * e_out_dstride + g * e_out_gstride + cell * e_out_cstride
+  int64_t e_out_dstride, e_out_gstride, e_out_cstride;   // (direction i, band group g)
   R* gring;                      // global-memory value rings, or null for the shared-memory ring
   int64_t gring_stride;          // elements per CTA's global ring
   R* part;                       // [n_items*N] collision-moment partials (of e - e0)
@@ -72,17 +72,18 @@ template <typename R>
 cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st);
 
 // Second-order upwind source of every work item and position, from the
-// previous sweep's distribution e[(item*N + cell)*G + b]:
+// previous sweep's distribution e[(i*N + cell)*Bp + band] (direction i, all
+// bands of a cell contiguous):
 //   src2 = -sum over the cell's interior faces f of (s_i . An_f / V) *
 //          sum_m rc_a[u, f_u, m] (e[nb(u, m)] - e[u]),
 // u the face's upwind cell (the cell itself on outflow faces) and f_u the
-// face's local index in u.  Written at src2[(item*N + pos)*G + b].
+// face's local index in u.  Written at src2[(item*N + pos)*G + b], item =
+// i*n_groups + g, the layout the sweep's chunks copy.
 template <typename R>
 struct Src2Args {
-  int N, nfc, G, n_items;
+  int N, nfc, G, n_items, n_groups, Bp, D;
   const R* e;
   R* src2;
-  const int32_t* item_dir;
   const int32_t* pos_cell;       // [D*N] cell of each position
   const int32_t* nb;             // [N*nfc] neighbour or -1
   const int32_t* twin;           // [N*nfc] the face's local index in the neighbour

@@ -364,7 +364,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       }
       if (slot >= 0) store_vals<R, G>(ring + slot * G, e);
       if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * GP, e);
-      if (a.e_out) store_vals<R, G>(a.e_out + (size_t)item * a.e_out_stride + (size_t)cell * G, e);
+      if (a.e_out)
+        store_vals<R, G>(a.e_out + (size_t)i * a.e_out_dstride + (size_t)g * a.e_out_gstride +
+                             (size_t)cell * a.e_out_cstride,
+                         e);
       part[cell] = nl;
       if (a.full) {
         R es = R(0), evs = R(0);
@@ -529,66 +532,90 @@ __global__ void gather_tq_kernel(R* tqp, const int32_t* pos_cell, const R* srcTQ
   reinterpret_cast<R2*>(tqp)[q] = __ldg(reinterpret_cast<const R2*>(srcTQ) + __ldcs(pos_cell + q));
 }
 
-// Second-order upwind sources: one thread per (work item, position), the
-// item's G bands in registers.  Reads the previous sweep's values of the
-// cell, its face neighbours and (on inflow faces) the upwind neighbour's own
-// neighbours; one direction-and-band-group slice of e is N*G values, so the
-// two-ring gathers of the blocks working on an item stay in L2.
+// Second-order upwind sources.  One thread per (direction, position): it
+// resolves the cell's faces once -- upwind cell, its neighbours and the
+// reconstruction weights toward the face -- and keeps them in registers
+// while it walks the band groups along each needed row of the direction's
+// distribution (N*Bp values, L2-resident while the direction's blocks run).
+// Consecutive threads take consecutive positions, so each band group's
+// results are stored as one contiguous run of the [item][position][G]
+// layout the sweep copies.  Wall faces get d = 0 and read the cell itself;
+// a wall neighbour of the upwind cell reads the upwind cell (zero difference,
+// zero weight): no branches between the loads.
 template <typename R, int G, int NF>
-__global__ void __launch_bounds__(256) src2_kernel(const Src2Args<R> a) {
+__global__ void __launch_bounds__(256, NF > 4 ? 3 : 1) src2_kernel(const Src2Args<R> a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)a.n_items * a.N) return;
-  const int item = (int)(t / a.N);
-  const int p = (int)(t - (int64_t)item * a.N);
-  const int i = __ldg(a.item_dir + item);
-  const int c = __ldg(a.pos_cell + (int64_t)i * a.N + p);
-  const R* e = a.e + (size_t)item * a.N * G;
+  if (t >= (int64_t)a.D * a.N) return;
+  const int i = (int)(t / a.N);
+  const int p = (int)(t - (int64_t)i * a.N);
+  const int c = __ldg(a.pos_cell + t);
   const R sx = (R)a.dir_s[i * 3], sy = (R)a.dir_s[i * 3 + 1], sz = (R)a.dir_s[i * 3 + 2];
-  R ec[G], acc[G];
-  load_vals<R, G>(e + (size_t)c * G, ec);
-#pragma unroll
-  for (int b = 0; b < G; ++b) acc[b] = R(0);
+  // hexahedra (36 weights and neighbours) re-read the tables from L1 per band
+  // group instead of holding them in registers
+  constexpr bool kHold = NF <= 4;
+  constexpr int NH = kHold ? NF : 1;
+  R d[NF], w[NH][NH];
+  int u[NF], h[NF], nbu[NH][NH];
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     const int nk = __ldg(a.nb + (int64_t)c * NF + k);
-    if (nk < 0) continue;
+    const int tw = __ldg(a.twin + (int64_t)c * NF + k);
     const R* An = a.AnV + ((int64_t)c * NF + k) * 3;
-    const R d = sx * An[0] + sy * An[1] + sz * An[2];
-    if (d == R(0)) continue;
-    int u = c, h = k;
-    R eu[G];
-    if (d > R(0)) {
+    R dk = sx * __ldg(An) + sy * __ldg(An + 1) + sz * __ldg(An + 2);
+    if (nk < 0) dk = R(0);
+    const bool in = dk < R(0);
+    d[k] = dk;
+    u[k] = in ? nk : c;
+    h[k] = in ? tw : k;
+    if constexpr (kHold) {
 #pragma unroll
-      for (int b = 0; b < G; ++b) eu[b] = ec[b];
-    } else {
-      u = nk;
-      h = __ldg(a.twin + (int64_t)c * NF + k);
-      load_vals<R, G>(e + (size_t)u * G, eu);
+      for (int m2 = 0; m2 < NF; ++m2) {
+        const int nm = __ldg(a.nb + (int64_t)u[k] * NF + m2);
+        nbu[k][m2] = nm >= 0 ? nm : u[k];
+        w[k][m2] = __ldg(a.rc_a + ((int64_t)u[k] * NF + h[k]) * NF + m2);
+      }
     }
-    const R* w = a.rc_a + ((int64_t)u * NF + h) * NF;
-    R inc[G];
-#pragma unroll
-    for (int b = 0; b < G; ++b) inc[b] = R(0);
-#pragma unroll
-    for (int m2 = 0; m2 < NF; ++m2) {
-      const R wm = __ldg(w + m2);
-      if (wm == R(0)) continue;   // wall face, or a cell without a gradient
-      const int nm = __ldg(a.nb + (int64_t)u * NF + m2);
-      R en[G];
-      load_vals<R, G>(e + (size_t)nm * G, en);
-#pragma unroll
-      for (int b = 0; b < G; ++b) inc[b] += wm * (en[b] - eu[b]);
-    }
-#pragma unroll
-    for (int b = 0; b < G; ++b) acc[b] -= d * inc[b];
   }
-  store_vals<R, G>(a.src2 + (size_t)t * G, acc);
+  const R* e = a.e + (size_t)i * a.N * a.Bp;
+  R* out = a.src2 + ((size_t)i * a.n_groups * a.N + p) * G;
+  for (int g = 0; g < a.n_groups; ++g) {
+    const R* eg = e + g * G;
+    R acc[G];
+#pragma unroll
+    for (int b = 0; b < G; ++b) acc[b] = R(0);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      R eu[G], inc[G];
+      load_vals<R, G>(eg + (size_t)u[k] * a.Bp, eu);
+#pragma unroll
+      for (int b = 0; b < G; ++b) inc[b] = R(0);
+#pragma unroll
+      for (int m2 = 0; m2 < NF; ++m2) {
+        int nm;
+        R wm;
+        if constexpr (kHold) {
+          nm = nbu[k][m2];
+          wm = w[k][m2];
+        } else {
+          nm = __ldg(a.nb + (int64_t)u[k] * NF + m2);
+          nm = nm >= 0 ? nm : u[k];
+          wm = __ldg(a.rc_a + ((int64_t)u[k] * NF + h[k]) * NF + m2);
+        }
+        R en[G];
+        load_vals<R, G>(eg + (size_t)nm * a.Bp, en);
+#pragma unroll
+        for (int b = 0; b < G; ++b) inc[b] += wm * (en[b] - eu[b]);
+      }
+#pragma unroll
+      for (int b = 0; b < G; ++b) acc[b] -= d[k] * inc[b];
+    }
+    store_vals<R, G>(out + (size_t)g * a.N * G, acc);
+  }
 }
 
 template <typename R, int G>
 static cudaError_t launch_src2_g(const Src2Args<R>& a, cudaStream_t st) {
-  const int64_t n = (int64_t)a.n_items * a.N;
-  const unsigned grid = (unsigned)((n + 255) / 256);
+  const unsigned grid = (unsigned)(((int64_t)a.D * a.N + 255) / 256);
   switch (a.nfc) {
     case 3: src2_kernel<R, G, 3><<<grid, 256, 0, st>>>(a); break;
     case 4: src2_kernel<R, G, 4><<<grid, 256, 0, st>>>(a); break;
@@ -601,6 +628,7 @@ static cudaError_t launch_src2_g(const Src2Args<R>& a, cudaStream_t st) {
 template <typename R>
 cudaError_t launch_src2(const Src2Args<R>& a, cudaStream_t st) {
   if ((int64_t)a.n_items * a.N == 0) return cudaSuccess;
+  if (a.Bp != a.n_groups * a.G) return cudaErrorInvalidValue;
   switch (a.G) {
     case 1: return launch_src2_g<R, 1>(a, st);
     case 2: return launch_src2_g<R, 2>(a, st);
