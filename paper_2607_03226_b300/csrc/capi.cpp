@@ -1384,6 +1384,7 @@ struct BatchTables {
   struct SweepGroup {
     int K = 0, G = 0, threads = 0, items = 0;
     bool gr = false;
+    bool o2 = false;
     size_t smem = 0;
     std::vector<int> members;
     DBuf args, start;
@@ -1405,15 +1406,17 @@ int batch_build(BatchTables<R>& bt, const std::vector<Run*>& act) {
   for (int k = 0; k < (int)act.size(); ++k) {
     nbte_solver* S = act[k]->S;
     const bool gr = S->gring_stride > 0;
+    const bool o2 = S->order == 2;
     typename BatchTables<R>::SweepGroup* grp = nullptr;
     for (auto& g : bt.groups)
-      if (g.K == S->K && g.G == S->G && g.gr == gr) grp = &g;
+      if (g.K == S->K && g.G == S->G && g.gr == gr && g.o2 == o2) grp = &g;
     if (!grp) {
       bt.groups.emplace_back();
       grp = &bt.groups.back();
       grp->K = S->K;
       grp->G = S->G;
       grp->gr = gr;
+      grp->o2 = o2;
     }
     grp->members.push_back(k);
   }
@@ -1498,7 +1501,7 @@ cudaError_t batch_enqueue(BatchTables<R>& bt, const std::vector<Run*>& act, cuda
     if ((e = enqueue_pre<R>(run->S, st)) != cudaSuccess) return e;
   for (auto& g : bt.groups) {
     e = launch_sweep_batch<R>(g.args.template as<SweepArgs<R>>(), g.start.template as<int32_t>(), (int)g.members.size(), g.K, g.G,
-                              g.gr, g.items, g.threads, g.smem, st);
+                              g.gr, g.o2, g.items, g.threads, g.smem, st);
     if (e != cudaSuccess) return e;
   }
   for (Run* run : act)

@@ -58,12 +58,13 @@ struct SweepArgs {
 template <typename R>
 cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem,
                          cudaStream_t st);
-// work items of several solvers sharing (R, K, G, ring placement) in one
+// work items of several solvers sharing (R, K, G, ring placement, upwind order) in one
 // launch; args[s] and item_start[s] (prefix sums, n_solvers+1 entries) are
 // device arrays
 template <typename R>
 cudaError_t launch_sweep_batch(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers, int K, int G,
-                               bool global_ring, int n_items, int threads, size_t smem, cudaStream_t st);
+                               bool global_ring, bool order2, int n_items, int threads, size_t smem,
+                               cudaStream_t st);
 // dinv[(item*N + pos)*G + b] = 1 / (band_inv_tau[g*G+b] + band_v[g*G+b] G_pos),
 // item = i*n_groups + g, G_pos read from the packed position records
 cudaError_t launch_fill_dinv(double* dinv, const unsigned char* rec, int rec_bytes, int off_G, const double* band_v,

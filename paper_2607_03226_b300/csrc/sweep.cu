@@ -170,7 +170,7 @@ struct RecField<double> {
 }  // namespace
 
 // One work item (direction i, band group g) of one solver; the whole CTA.
-template <typename R, int K, int G, bool GR>
+template <typename R, int K, int G, bool GR, bool O2>
 __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item, unsigned char* smem) {
   const int NS = a.n_stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -256,7 +256,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         // second order: the chunk's reconstruction sources, a 16-byte aligned superset
         unsigned s2_bytes = 0;
         int64_t sa = 0;
-        if (a.src2) {
+        if constexpr (O2) {
           constexpr int sper16 = (int)(16 / (G * sizeof(R))) > 1 ? (int)(16 / (G * sizeof(R))) : 1;
           const int64_t s0 = (int64_t)item * a.N + m.pos;
           sa = s0 / sper16 * sper16;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         bulk_copy(st, a.rec + (size_t)q0 * RL.size, rec_bytes, full + s);
         bulk_copy(st + a.off_tq, a.tqp + (size_t)qa * 2, tq_bytes, full + s);
         if (den_bytes) bulk_copy(st + a.off_den, a.dinv + (size_t)da * G, den_bytes, full + s);
-        if (s2_bytes) bulk_copy(st + a.off_src2, a.src2 + (size_t)sa * G, s2_bytes, full + s);
+        if constexpr (O2) bulk_copy(st + a.off_src2, a.src2 + (size_t)sa * G, s2_bytes, full + s);
         if (nimp > 0)
           bulk_copy(st + a.off_imp, a.imp + ((size_t)g * a.n_imp + a.imp_off[i] + m.imp) * a.Gpad, imp_bytes,
                     full + s);
@@ -318,8 +318,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     // second order: this chunk's reconstruction sources (superset starts s_shift early)
     constexpr int sper16 = (int)(16 / (G * sizeof(R))) > 1 ? (int)(16 / (G * sizeof(R))) : 1;
     const R* s2 = reinterpret_cast<const R*>(st + a.off_src2);
-    const int s_shift = (int)(((int64_t)item * a.N + m.pos) % sper16);
-    const bool has_s2 = a.src2 != nullptr;
+    const int s_shift = O2 ? (int)(((int64_t)item * a.N + m.pos) % sper16) : 0;
     for (int j = ct; j < m.len; j += ncons) {
       uint4 w[NQ];
 #pragma unroll
@@ -347,7 +346,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
 #pragma unroll
         for (int b = 0; b < G; ++b) up[b] += cf * (eu[b] - e0[b]);
       }
-      if (has_s2) {
+      if constexpr (O2) {
 #pragma unroll
         for (int b = 0; b < G; ++b) up[b] += s2[(j + s_shift) * G + b];
       }
@@ -387,17 +386,17 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
   }
 }
 
-template <typename R, int K, int G, bool GR>
+template <typename R, int K, int G, bool GR, bool O2>
 __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  sweep_item<R, K, G, GR>(a, blockIdx.x + a.item0, smem);
+  sweep_item<R, K, G, GR, O2>(a, blockIdx.x + a.item0, smem);
 }
 
 // Work items of several solvers in one launch: block b runs item
 // b - item_start[s] of solver s, item_start[s] <= b < item_start[s+1].  The
 // solvers share (R, K, G, ring placement); each brings its own tables, value
 // rings and shared-memory layout (the launch takes the largest).
-template <typename R, int K, int G, bool GR>
+template <typename R, int K, int G, bool GR, bool O2>
 __global__ void __launch_bounds__(544) sweep_batch_kernel(const SweepArgs<R>* args, const int32_t* item_start,
                                                           int n_solvers) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -414,65 +413,65 @@ __global__ void __launch_bounds__(544) sweep_batch_kernel(const SweepArgs<R>* ar
     s_item = (int)blockIdx.x - item_start[lo];
   }
   __syncthreads();
-  sweep_item<R, K, G, GR>(sa, s_item, smem);
+  sweep_item<R, K, G, GR, O2>(sa, s_item, smem);
 }
 
-template <typename R, int K, int G, bool GR>
+template <typename R, int K, int G, bool GR, bool O2>
 static cudaError_t launch_one(const SweepArgs<R>& a, int n_items, int threads, size_t smem, cudaStream_t st) {
-  auto kern = sweep_kernel<R, K, G, GR>;
+  auto kern = sweep_kernel<R, K, G, GR, O2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<n_items, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <typename R, int K, bool GR>
+template <typename R, int K, bool GR, bool O2>
 static cudaError_t launch_k(const SweepArgs<R>& a, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
   switch (G) {
-    case 1: return launch_one<R, K, 1, GR>(a, n_items, threads, smem, st);
-    case 2: return launch_one<R, K, 2, GR>(a, n_items, threads, smem, st);
-    case 4: return launch_one<R, K, 4, GR>(a, n_items, threads, smem, st);
+    case 1: return launch_one<R, K, 1, GR, O2>(a, n_items, threads, smem, st);
+    case 2: return launch_one<R, K, 2, GR, O2>(a, n_items, threads, smem, st);
+    case 4: return launch_one<R, K, 4, GR, O2>(a, n_items, threads, smem, st);
     case 8:
-      if constexpr (sizeof(R) == 4) return launch_one<R, K, 8, GR>(a, n_items, threads, smem, st);
+      if constexpr (sizeof(R) == 4) return launch_one<R, K, 8, GR, O2>(a, n_items, threads, smem, st);
       return cudaErrorInvalidConfiguration;
     default:
       return cudaErrorInvalidConfiguration;
   }
 }
 
-template <typename R, bool GR>
+template <typename R, bool GR, bool O2>
 static cudaError_t launch_gr(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem,
                              cudaStream_t st) {
   switch (K) {
-    case 1: return launch_k<R, 1, GR>(a, G, n_items, threads, smem, st);
-    case 2: return launch_k<R, 2, GR>(a, G, n_items, threads, smem, st);
-    case 3: return launch_k<R, 3, GR>(a, G, n_items, threads, smem, st);
-    case 4: return launch_k<R, 4, GR>(a, G, n_items, threads, smem, st);
-    case 5: return launch_k<R, 5, GR>(a, G, n_items, threads, smem, st);
+    case 1: return launch_k<R, 1, GR, O2>(a, G, n_items, threads, smem, st);
+    case 2: return launch_k<R, 2, GR, O2>(a, G, n_items, threads, smem, st);
+    case 3: return launch_k<R, 3, GR, O2>(a, G, n_items, threads, smem, st);
+    case 4: return launch_k<R, 4, GR, O2>(a, G, n_items, threads, smem, st);
+    case 5: return launch_k<R, 5, GR, O2>(a, G, n_items, threads, smem, st);
     default: return cudaErrorInvalidConfiguration;
   }
 }
 
-template <typename R, int K, int G, bool GR>
+template <typename R, int K, int G, bool GR, bool O2>
 static cudaError_t launch_batch_one(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers,
                                     int n_items, int threads, size_t smem, cudaStream_t st) {
-  auto kern = sweep_batch_kernel<R, K, G, GR>;
+  auto kern = sweep_batch_kernel<R, K, G, GR, O2>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<n_items, threads, smem, st>>>(args, item_start, n_solvers);
   return cudaGetLastError();
 }
 
-template <typename R, int K, bool GR>
+template <typename R, int K, bool GR, bool O2>
 static cudaError_t launch_batch_k(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers, int G,
                                   int n_items, int threads, size_t smem, cudaStream_t st) {
   switch (G) {
-    case 1: return launch_batch_one<R, K, 1, GR>(args, item_start, n_solvers, n_items, threads, smem, st);
-    case 2: return launch_batch_one<R, K, 2, GR>(args, item_start, n_solvers, n_items, threads, smem, st);
-    case 4: return launch_batch_one<R, K, 4, GR>(args, item_start, n_solvers, n_items, threads, smem, st);
+    case 1: return launch_batch_one<R, K, 1, GR, O2>(args, item_start, n_solvers, n_items, threads, smem, st);
+    case 2: return launch_batch_one<R, K, 2, GR, O2>(args, item_start, n_solvers, n_items, threads, smem, st);
+    case 4: return launch_batch_one<R, K, 4, GR, O2>(args, item_start, n_solvers, n_items, threads, smem, st);
     case 8:
       if constexpr (sizeof(R) == 4)
-        return launch_batch_one<R, K, 8, GR>(args, item_start, n_solvers, n_items, threads, smem, st);
+        return launch_batch_one<R, K, 8, GR, O2>(args, item_start, n_solvers, n_items, threads, smem, st);
       return cudaErrorInvalidConfiguration;
     default:
       return cudaErrorInvalidConfiguration;
@@ -481,13 +480,18 @@ static cudaError_t launch_batch_k(const SweepArgs<R>* args, const int32_t* item_
 
 template <typename R>
 cudaError_t launch_sweep_batch(const SweepArgs<R>* args, const int32_t* item_start, int n_solvers, int K, int G,
-                               bool global_ring, int n_items, int threads, size_t smem, cudaStream_t st) {
+                               bool global_ring, bool order2, int n_items, int threads, size_t smem,
+                               cudaStream_t st) {
   if (n_solvers < 1 || n_items < 1) return cudaSuccess;
-#define NBTE_BK(Kv)                                                                                            \
-  case Kv:                                                                                                     \
-    return global_ring                                                                                         \
-               ? launch_batch_k<R, Kv, true>(args, item_start, n_solvers, G, n_items, threads, smem, st)      \
-               : launch_batch_k<R, Kv, false>(args, item_start, n_solvers, G, n_items, threads, smem, st);
+#define NBTE_BK(Kv)                                                                                               \
+  case Kv:                                                                                                        \
+    if (order2)                                                                                                   \
+      return global_ring                                                                                          \
+                 ? launch_batch_k<R, Kv, true, true>(args, item_start, n_solvers, G, n_items, threads, smem, st)  \
+                 : launch_batch_k<R, Kv, false, true>(args, item_start, n_solvers, G, n_items, threads, smem, st); \
+    return global_ring                                                                                            \
+               ? launch_batch_k<R, Kv, true, false>(args, item_start, n_solvers, G, n_items, threads, smem, st)   \
+               : launch_batch_k<R, Kv, false, false>(args, item_start, n_solvers, G, n_items, threads, smem, st);
   switch (K) {
     NBTE_BK(1) NBTE_BK(2) NBTE_BK(3) NBTE_BK(4) NBTE_BK(5)
     default:
@@ -498,8 +502,13 @@ cudaError_t launch_sweep_batch(const SweepArgs<R>* args, const int32_t* item_sta
 
 template <typename R>
 cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem, cudaStream_t st) {
-  return a.gring ? launch_gr<R, true>(a, K, G, n_items, threads, smem, st)
-                 : launch_gr<R, false>(a, K, G, n_items, threads, smem, st);
+  // second-order sources (src2) select their own kernel variant, so the
+  // first-order sweep carries none of their per-chunk work
+  if (a.src2)
+    return a.gring ? launch_gr<R, true, true>(a, K, G, n_items, threads, smem, st)
+                   : launch_gr<R, false, true>(a, K, G, n_items, threads, smem, st);
+  return a.gring ? launch_gr<R, true, false>(a, K, G, n_items, threads, smem, st)
+                 : launch_gr<R, false, false>(a, K, G, n_items, threads, smem, st);
 }
 
 // FP64 denominators of every (work item, position); one thread per pair
@@ -648,10 +657,10 @@ cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, in
 }
 
 template cudaError_t launch_sweep<float>(const SweepArgs<float>&, int, int, int, int, size_t, cudaStream_t);
-template cudaError_t launch_sweep_batch<float>(const SweepArgs<float>*, const int32_t*, int, int, int, bool, int, int,
-                                               size_t, cudaStream_t);
-template cudaError_t launch_sweep_batch<double>(const SweepArgs<double>*, const int32_t*, int, int, int, bool, int,
-                                                int, size_t, cudaStream_t);
+template cudaError_t launch_sweep_batch<float>(const SweepArgs<float>*, const int32_t*, int, int, int, bool, bool, int,
+                                               int, size_t, cudaStream_t);
+template cudaError_t launch_sweep_batch<double>(const SweepArgs<double>*, const int32_t*, int, int, int, bool, bool,
+                                                int, int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, int, int, size_t, cudaStream_t);
 template cudaError_t launch_src2<float>(const Src2Args<float>&, cudaStream_t);
 template cudaError_t launch_src2<double>(const Src2Args<double>&, cudaStream_t);
