@@ -71,11 +71,23 @@ struct DBuf {
   T* as() const { return static_cast<T*>(p); }
 };
 
+// A plain cudaMemcpy from pageable memory may return before its DMA lands,
+// and it runs on the legacy stream, which the solvers' non-blocking streams
+// do not wait for: wait for it here, so that every later launch sees the data.
 template <typename T>
 cudaError_t upload(DBuf& b, const std::vector<T>& v) {
   cudaError_t e = b.alloc(v.size() * sizeof(T));
   if (e != cudaSuccess) return e;
   if (!v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
+  return e;
+}
+
+// Zero device memory in the order of `st` and wait for it (device error
+// words and set-up buffers that the next launches on `st` read).
+inline cudaError_t zero_now(void* p, size_t n, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(p, 0, n, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
 }
 
@@ -136,6 +148,9 @@ struct nbte_solver {
   DBuf o2_e, o2_src, rc_nb, rc_twin, rc_AnV, rc_a;
   int rc_prec = -1;
   int64_t rc_cells = 0;
+  // most wall/lag imports in one chunk, per chunk length (sizes the stages' import region)
+  int64_t cimp_plan = -1;
+  std::map<int, int> cimp_max;
   double W = 0, beta = 0, Ctot = 0;
   DBuf rec, pos_cell, chunks, chunk_off, tqp, gring, e_scratch, dinv;
   int64_t gring_stride = 0;
@@ -354,6 +369,35 @@ int ensure_chunks(nbte_solver* S, int cap) {
   return NBTE_OK;
 }
 
+// the most imports any chunk of length <= cap holds (chunks as ensure_chunks
+// cuts them): the size of a copy stage's import region
+int max_chunk_imports(nbte_solver* S, int cap) {
+  if (S->cimp_plan != S->plan_built) {
+    S->cimp_max.clear();
+    S->cimp_plan = S->plan_built;
+  }
+  auto it = S->cimp_max.find(cap);
+  if (it != S->cimp_max.end()) return it->second;
+  const Plan& P = S->plan;
+  int best = 0;
+  for (int i = 0; i < P.D; ++i) {
+    const int32_t* lp = P.level_ptr.data() + P.lvl_off[i];
+    const int L = (int)(P.lvl_off[i + 1] - P.lvl_off[i]) - 1;
+    for (int l = 0; l < L; ++l)
+      for (int32_t p0 = lp[l]; p0 < lp[l + 1]; p0 += cap) {
+        const int32_t p1 = std::min(lp[l + 1], p0 + cap);
+        int nimp = 0;
+        for (int k = 0; k < P.K; ++k) {
+          const int32_t* ref = P.pos_ref.data() + ((size_t)i * P.K + k) * P.N;
+          for (int32_t p = p0; p < p1; ++p) nimp += ref[p] < 0;
+        }
+        best = std::max(best, nimp);
+      }
+  }
+  S->cimp_max[cap] = best;
+  return best;
+}
+
 bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 int64_t tune_key(const nbte_solver* S) { return S->plan_built * 1000003 + S->version_bands; }
@@ -389,11 +433,13 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   // precomputed denominators 1/(1/tau + v G) of the chunk's positions)
   const bool order2 = o.order == 2;
   int off_src2 = 0;
+  // import rows of a chunk: sized by the fullest chunk, not by cap * K
+  const int cimp = max_chunk_imports(S, cap);
   auto stage_of = [&](int Gv, int& off_tq, int& off_imp, int& off_den) {
     const int gpad = padded_group(Gv, sz);
     const int rec = (cap * RL.size + 15) / 16 * 16;
     const int tq = ((cap + 2) * 2 * sz + 15) / 16 * 16;
-    const int imp = cap * K * gpad * sz;
+    const int imp = cimp * gpad * sz;
     const int den = prec ? 0 : ((cap + 2) * Gv * 8 + 15) / 16 * 16;
     // second order: the chunk's reconstruction sources (superset of at most cap + 3 positions)
     const int src2 = order2 ? ((cap + 4) * Gv * sz + 15) / 16 * 16 : 0;
@@ -533,7 +579,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   NBTE_CK(S->expt.alloc((size_t)ng * S->n_exp * S->Gpad * sz));
   NBTE_CK(S->impt.alloc((size_t)ng * S->n_imp * S->Gpad * sz));
   NBTE_CK(S->tqp.alloc(((size_t)S->D * N + 2) * 2 * sz));
-  NBTE_CK(cudaMemset(S->tqp.p, 0, S->tqp.bytes));
+  NBTE_CK(cudaMemsetAsync(S->tqp.p, 0, S->tqp.bytes, S->stream));
   NBTE_CK(S->srcTQ.alloc((size_t)2 * N * sz));
   NBTE_CK(S->srcTQ_fin.alloc((size_t)2 * N * sz));
   NBTE_CK(S->part.alloc((size_t)S->n_items * N * sz));
@@ -547,7 +593,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     // iteration-independent, so the sweep reads them instead of dividing
     // (+16 doubles: a chunk's 16-byte aligned copy may run one position past the last)
     NBTE_CK(S->dinv.alloc(((size_t)S->n_items * N * G + 16) * 8));
-    NBTE_CK(cudaMemset(S->dinv.p, 0, S->dinv.bytes));
+    NBTE_CK(cudaMemsetAsync(S->dinv.p, 0, S->dinv.bytes, S->stream));
     NBTE_CK(launch_fill_dinv(S->dinv.as<double>(), S->rec.as<unsigned char>(), RL.size, RL.off_G,
                              S->band_v.as<double>(), S->band_itau.as<double>(), S->D, ng, G, N, S->stream));
     NBTE_CK(cudaStreamSynchronize(S->stream));
@@ -560,8 +606,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     // chunk's 16-byte aligned copy may run past the last position)
     NBTE_CK(S->o2_e.alloc((size_t)S->n_items * N * G * sz));
     NBTE_CK(S->o2_src.alloc(((size_t)S->n_items * N + 16) * G * sz));
-    NBTE_CK(cudaMemset(S->o2_e.p, 0, S->o2_e.bytes));
-    NBTE_CK(cudaMemset(S->o2_src.p, 0, S->o2_src.bytes));
+    NBTE_CK(cudaMemsetAsync(S->o2_e.p, 0, S->o2_e.bytes, S->stream));
+    NBTE_CK(cudaMemsetAsync(S->o2_src.p, 0, S->o2_src.bytes, S->stream));
     if (S->rc_prec != prec || !S->rc_a.p) {
       Reconstruction rcn;
       build_reconstruction(S->mesh->m, rcn);
@@ -593,9 +639,10 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   NBTE_CK(S->accE.alloc(N * 8));
   NBTE_CK(S->accQ.alloc((size_t)N * S->mesh->m.dim * 8));
   NBTE_CK(S->res.alloc(32));   // [0,1] residual words, [2] sweep error word (sticky)
-  NBTE_CK(cudaMemset(S->res.p, 0, 32));
+  NBTE_CK(cudaMemsetAsync(S->res.p, 0, 32, S->stream));
   NBTE_CK(S->heat.alloc((size_t)S->n_wf * 8));
-  NBTE_CK(cudaMemcpy(S->Vd.p, S->mesh->m.V.data(), N * 8, cudaMemcpyHostToDevice));
+  NBTE_CK(cudaMemcpyAsync(S->Vd.p, S->mesh->m.V.data(), N * 8, cudaMemcpyHostToDevice, S->stream));
+  NBTE_CK(cudaStreamSynchronize(S->stream));
   S->version_q = -1;   // force heat-source upload
   S->layout_key = key;
   S->have_state = false;
@@ -704,12 +751,12 @@ int ensure_laplacian(nbte_solver* S) {
   NBTE_CK(S->cg_rw.alloc((size_t)Nc * 8));
   NBTE_CK(S->cg_rcx.alloc((size_t)Nc * 8));
   NBTE_CK(S->cg_scx.alloc((size_t)Nc * 8));
-  NBTE_CK(cudaMemset(S->cg_x.p, 0, N * 8));   // no previous correction yet
+  NBTE_CK(zero_now(S->cg_x.p, N * 8, S->stream));   // no previous correction yet
   NBTE_CK(S->cg_bar.alloc(16));
   NBTE_CK(S->cg_err.alloc(16));
   NBTE_CK(S->cg_it.alloc(16));
   NBTE_CK(S->cg_res.alloc(16));
-  NBTE_CK(cudaMemset(S->cg_err.p, 0, 16));
+  NBTE_CK(zero_now(S->cg_err.p, 16, S->stream));
   S->cg_part_key = -1;
   S->lap_built = want;
   drop_graph(S);
@@ -771,8 +818,8 @@ int cg_partition(nbte_solver* S, int grid, int threads_min) {
   NBTE_CK(S->cg_s.alloc(work));
   NBTE_CK(S->cg_w.alloc(work));
   NBTE_CK(S->cg_slots.alloc((size_t)grid * sizeof(CGSlot)));
-  NBTE_CK(cudaMemset(S->cg_slots.p, 0, S->cg_slots.bytes));
-  NBTE_CK(cudaMemset(S->cg_bar.p, 0, 16));   // arrivals must start at a multiple of the block count
+  NBTE_CK(zero_now(S->cg_slots.p, S->cg_slots.bytes, S->stream));
+  NBTE_CK(zero_now(S->cg_bar.p, 16, S->stream));   // arrivals must start at a multiple of the block count
   S->cg_max_rows = max_rows;
   S->cg_max_na = max_na;
   S->cg_smem_vec = vec;
@@ -1052,9 +1099,9 @@ int init_state(nbte_solver* S, const nbte_solve_opts& o) {
     NBTE_CK(cudaMemcpyAsync(&err, S->cg_err.p, 4, cudaMemcpyDeviceToHost, st));
     NBTE_CK(cudaStreamSynchronize(st));
     if (err != 0) {
-      cudaMemset(S->cg_err.p, 0, 16);
-      cudaMemset(S->cg_slots.p, 0, S->cg_slots.bytes);
-      cudaMemset(S->cg_bar.p, 0, 16);
+      zero_now(S->cg_err.p, 16, S->stream);
+      zero_now(S->cg_slots.p, S->cg_slots.bytes, S->stream);
+      zero_now(S->cg_bar.p, 16, S->stream);
       return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the initial diffusion solve gave up");
     }
   }
@@ -1094,7 +1141,7 @@ int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
   unsigned long long err = 0;
   NBTE_CK(cudaMemcpy(&err, S->res.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost));
   if (err) {
-    cudaMemset(S->res.p, 0, 32);
+    zero_now(S->res.p, 32, S->stream);
     return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
   }
   *ms = t / 2;
@@ -1177,14 +1224,14 @@ struct Run {
   bool check() {
     if (S->h_res[2] != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
-      cudaMemset(S->res.p, 0, 32);
+      zero_now(S->res.p, 32, S->stream);
       return true;
     }
     if (S->h_misc[0] != 0 && o.scheme != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded device wait in the CG correction gave up");
-      cudaMemset(S->cg_err.p, 0, 16);
-      cudaMemset(S->cg_slots.p, 0, S->cg_slots.bytes);
-      cudaMemset(S->cg_bar.p, 0, 16);
+      zero_now(S->cg_err.p, 16, S->stream);
+      zero_now(S->cg_slots.p, S->cg_slots.bytes, S->stream);
+      zero_now(S->cg_bar.p, 16, S->stream);
       return true;
     }
     double dmax, tmax;
@@ -1433,6 +1480,7 @@ int batch_build(BatchTables<R>& bt, const std::vector<Run*>& act) {
     g.items = start.back();
     NBTE_CK(g.args.alloc(args.size() * sizeof(SweepArgs<R>)));
     NBTE_CK(cudaMemcpy(g.args.p, args.data(), args.size() * sizeof(SweepArgs<R>), cudaMemcpyHostToDevice));
+    NBTE_CK(cudaStreamSynchronize(cudaStreamLegacy));
     NBTE_CK(upload(g.start, start));
   }
   // CG: every synthetic solver gets blocks in proportion to its cells (at
@@ -1484,6 +1532,7 @@ int batch_build(BatchTables<R>& bt, const std::vector<Run*>& act) {
     bt.cg_threads = T;
     NBTE_CK(bt.cg_args_d.alloc(args.size() * sizeof(CGArgs)));
     NBTE_CK(cudaMemcpy(bt.cg_args_d.p, args.data(), args.size() * sizeof(CGArgs), cudaMemcpyHostToDevice));
+    NBTE_CK(cudaStreamSynchronize(cudaStreamLegacy));
     NBTE_CK(upload(bt.cg_start_d, start));
   }
   if (bt.graph) {
@@ -2162,7 +2211,7 @@ static int distribution(nbte_solver* S, int dir, int band, double* out) {
   NBTE_CK(cudaMemcpyAsync(&err, S->res.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost, st));
   NBTE_CK(cudaStreamSynchronize(st));
   if (err) {
-    cudaMemset(S->res.p, 0, 32);
+    zero_now(S->res.p, 32, S->stream);
     return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
   }
   const int b = band % G;

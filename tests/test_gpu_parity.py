@@ -191,6 +191,36 @@ def test_finfet2d_full_size_steps(nbte_mod, precision, tol):
     s.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-6)])
+def test_finfet2d_full_size_every_layout(nbte_mod, precision, tol):
+    """Every sweep layout the autotuner may pick (band group x chunk length)
+    on the full-size 2D fin: T after one and two sequential iterations on the
+    stored oracle sample cells.  Layouts that do not fit shared memory are
+    refused with NBTE_ERR_ARG and skipped."""
+    g = _fin2d_golden("finfet2d_steps.json")
+    p = W.problems.finfet2d()
+    idx = np.array(g["cells"])
+    s = nbte_mod.Solver(p)
+    groups = (1, 2, 4) if precision == "fp64" else (1, 2, 4, 8)
+    bad, ran = [], 0
+    for G in groups:
+        for cap in (64, 128, 256, 512):
+            for n in (1, 2):
+                try:
+                    s.solve(scheme="sequential", precision=precision, n_iter=n, band_group=G,
+                            cta_threads=cap + 32)
+                except nbte_mod.NbteError as e:
+                    assert e.code == nbte_mod.NBTE_ERR_ARG
+                    break
+                ran += 1
+                err = np.abs(s.temperature(0)[idx] - np.array(g[f"T_iter{n}"])).max() / g[f"T_iter{n}_max_dev"]
+                if not err < tol:
+                    bad.append((G, cap, n, float(err)))
+    s.close()
+    print(f"{precision}: {ran} layout runs, failing: {bad}")
+    assert ran >= 8 and not bad
+
+
 def test_finfet2d_full_size_converged(nbte_mod):
     """The full-size 2D fin converged with the benchmark's scheme (synthetic,
     FP32 sweep) and in FP64: T and q on the stored oracle sample cells."""
