@@ -152,7 +152,10 @@ struct nbte_solver {
   int64_t cimp_plan = -1;
   std::map<int, int> cimp_max;
   double W = 0, beta = 0, Ctot = 0;
-  DBuf rec, pos_cell, chunks, chunk_off, tqp, gring, e_scratch, dinv;
+  DBuf rec_pos, rec, pos_cell, chunks, chunk_off, chunk_doff, chunk_dir, tq_dst, gring, e_scratch, dinv;
+  std::string blk_key;
+  std::vector<Chunk> h_chunks;                // host copy of the chunks of the current chunk length
+  std::vector<int64_t> h_chunk_off;           // [D+1] first chunk of each direction
   int64_t gring_stride = 0;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
@@ -207,7 +210,8 @@ struct DeviceGuard {
 };
 
 size_t device_bytes(const nbte_solver* S) {
-  const DBuf* all[] = {&S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->dinv, &S->chunks, &S->chunk_off, &S->tqp, &S->exp_off, &S->imp_off,
+  const DBuf* all[] = {&S->rec_pos, &S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->dinv, &S->chunks,
+                       &S->chunk_off, &S->chunk_doff, &S->chunk_dir, &S->tq_dst, &S->exp_off, &S->imp_off,
                        &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
                        &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
@@ -268,6 +272,7 @@ int ensure_plan(nbte_solver* S) {
   S->rec.release();
   S->rec_key.clear();
   S->chunk_key.clear();
+  S->blk_key.clear();
   NBTE_CK(upload(S->exp_off, P.exp_off));
   NBTE_CK(upload(S->imp_off, P.imp_off));
   NBTE_CK(upload(S->exp_cell, P.exp_cell));
@@ -302,11 +307,13 @@ int ensure_plan(nbte_solver* S) {
   return NBTE_OK;
 }
 
-// Packed position records of precision R (see layout.h), direction-major.
+// Packed position records of precision R (see layout.h), direction-major,
+// uploaded once per plan and precision; ensure_blocks rearranges them per
+// chunk length.
 template <typename R>
 int ensure_records(nbte_solver* S) {
   const std::string key = std::to_string(sizeof(R)) + "/" + std::to_string(S->plan_built);
-  if (key == S->rec_key && S->rec.p) return NBTE_OK;
+  if (key == S->rec_key && S->rec_pos.p) return NBTE_OK;
   const Plan& P = S->plan;
   const int K = P.K;
   const RecLayout L = rec_layout((int)sizeof(R), K);
@@ -328,9 +335,46 @@ int ensure_records(nbte_solver* S) {
         std::memcpy(r + L.off_coef + sizeof(R) * k, &c, sizeof(R));
       }
     }
-  NBTE_CK(upload(S->rec, buf));
+  NBTE_CK(upload(S->rec_pos, buf));
   NBTE_CK(upload(S->pos_cell, P.pos_cell));
   S->rec_key = key;
+  S->blk_key.clear();
+  return NBTE_OK;
+}
+
+// The sweep's chunk blocks for the current chunks: each chunk's records,
+// then room for its (T', Qdot) pairs, so that one bulk copy brings both.
+// chunk_doff holds each block's byte offset; tq_dst, per position
+// (direction-major), the index of its pair in units of pairs.  Packed on the
+// device from the position-ordered records.
+template <typename R>
+int ensure_blocks(nbte_solver* S, int cap) {
+  const std::string key = S->rec_key + "/" + S->chunk_key;
+  if (key == S->blk_key && S->rec.p) return NBTE_OK;
+  const Plan& P = S->plan;
+  const RecLayout L = rec_layout((int)sizeof(R), P.K);
+  const int pair = 2 * (int)sizeof(R);
+  const size_t nch = S->h_chunks.size();
+  std::vector<int64_t> doff(nch);
+  std::vector<int32_t> cdir(nch);
+  size_t total = 0;
+  for (int i = 0; i < P.D; ++i)
+    for (int64_t c = S->h_chunk_off[i]; c < S->h_chunk_off[i + 1]; ++c) {
+      doff[c] = (int64_t)total;
+      cdir[c] = i;
+      total += (size_t)S->h_chunks[c].len * L.size + chunk_tq_bytes(S->h_chunks[c].len, (int)sizeof(R));
+    }
+  if (total / pair > 0xffffffffull) return fail(NBTE_ERR_OOM, "position records exceed the 32-bit pair index");
+  NBTE_CK(upload(S->chunk_doff, doff));
+  NBTE_CK(upload(S->chunk_dir, cdir));
+  NBTE_CK(S->rec.alloc(total));
+  NBTE_CK(S->tq_dst.alloc((size_t)P.D * P.N * 4));
+  NBTE_CK(cudaMemsetAsync(S->rec.p, 0, S->rec.bytes, S->stream));
+  NBTE_CK(launch_pack_blocks(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->rec_pos.as<unsigned char>(),
+                             S->chunks.as<Chunk>(), S->chunk_doff.as<int64_t>(), S->chunk_dir.as<int32_t>(),
+                             (int64_t)nch, P.N, L.size, pair, cap, S->stream));
+  NBTE_CK(cudaStreamSynchronize(S->stream));
+  S->blk_key = key;
   return NBTE_OK;
 }
 
@@ -365,6 +409,8 @@ int ensure_chunks(nbte_solver* S, int cap) {
   }
   NBTE_CK(upload(S->chunks, ch));
   NBTE_CK(upload(S->chunk_off, off));
+  S->h_chunks = std::move(ch);
+  S->h_chunk_off = std::move(off);
   S->chunk_key = key;
   return NBTE_OK;
 }
@@ -505,7 +551,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   const int threads = cap + 32;
   if (estimate) {
     const size_t N = (size_t)S->mesh->m.n_cells, D = (size_t)S->D, Gp = (size_t)padded_group(G, sz);
-    size_t b = D * N * (RL.size + 4 + 2 * sz);                          // records, position cells, (T', Qdot)
+    size_t b = D * N * (2 * RL.size + 8 + 2 * sz);                      // records (by position and in chunk
+                                                                         // blocks), cells, pair index, (T', Qdot)
     b += (size_t)D * ng * N * sz;                                        // collision partials
     b += (size_t)ng * (S->n_exp + S->n_imp) * Gp * sz;                   // export / import rows
     if (gr) b += (size_t)D * ng * (((size_t)(S->max_slots + 1) * G + 3) / 4 * 4) * sz;   // global rings
@@ -528,6 +575,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   int rc = prec ? ensure_records<float>(S) : ensure_records<double>(S);
   if (rc) return rc;
   rc = ensure_chunks(S, cap);
+  if (rc) return rc;
+  rc = prec ? ensure_blocks<float>(S, cap) : ensure_blocks<double>(S, cap);
   if (rc) return rc;
   S->prec = prec; S->G = G; S->Gpad = padded_group(G, sz); S->n_groups = ng; S->Bp = Bp;
   S->n_items = S->D * ng;
@@ -578,8 +627,6 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   NBTE_CK(upload(S->item_grp, igrp));
   NBTE_CK(S->expt.alloc((size_t)ng * S->n_exp * S->Gpad * sz));
   NBTE_CK(S->impt.alloc((size_t)ng * S->n_imp * S->Gpad * sz));
-  NBTE_CK(S->tqp.alloc(((size_t)S->D * N + 2) * 2 * sz));
-  NBTE_CK(cudaMemsetAsync(S->tqp.p, 0, S->tqp.bytes, S->stream));
   NBTE_CK(S->srcTQ.alloc((size_t)2 * N * sz));
   NBTE_CK(S->srcTQ_fin.alloc((size_t)2 * N * sz));
   NBTE_CK(S->part.alloc((size_t)S->n_items * N * sz));
@@ -594,8 +641,10 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     // (+16 doubles: a chunk's 16-byte aligned copy may run one position past the last)
     NBTE_CK(S->dinv.alloc(((size_t)S->n_items * N * G + 16) * 8));
     NBTE_CK(cudaMemsetAsync(S->dinv.p, 0, S->dinv.bytes, S->stream));
-    NBTE_CK(launch_fill_dinv(S->dinv.as<double>(), S->rec.as<unsigned char>(), RL.size, RL.off_G,
-                             S->band_v.as<double>(), S->band_itau.as<double>(), S->D, ng, G, N, S->stream));
+    DBuf posG;
+    NBTE_CK(upload(posG, S->plan.pos_G));
+    NBTE_CK(launch_fill_dinv(S->dinv.as<double>(), posG.as<double>(), S->band_v.as<double>(),
+                             S->band_itau.as<double>(), S->D, ng, G, N, S->stream));
     NBTE_CK(cudaStreamSynchronize(S->stream));
   } else {
     S->dinv.release();
@@ -856,7 +905,6 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.stage_bytes = S->stage_bytes;
   a.off_ring = S->off_ring;
   a.off_stage = S->off_stage;
-  a.off_tq = S->off_tq;
   a.off_imp = S->off_imp;
   a.off_den = S->off_den;
   a.off_src2 = S->off_src2;
@@ -874,7 +922,7 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.chunk_off = S->chunk_off.as<int64_t>();
   a.chunks = S->chunks.as<Chunk>();
   a.rec = S->rec.as<unsigned char>();
-  a.tqp = S->tqp.as<R>();
+  a.chunk_doff = S->chunk_doff.as<int64_t>();
   a.exp_off = S->exp_off.as<int64_t>();
   a.imp_off = S->imp_off.as<int64_t>();
   a.imp = S->impt.as<R>();
@@ -1017,7 +1065,7 @@ cudaError_t enqueue_pre(nbte_solver* S, cudaStream_t st) {
   launch_walls<R>(wall_args<R>(S), st);
   cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  e = launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
+  e = launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
                           (int64_t)S->D * S->mesh->m.n_cells, st);
   if (e != cudaSuccess) return e;
   // second order: this sweep's reconstruction sources from the previous sweep's distribution
@@ -1123,7 +1171,7 @@ int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
   if (rc) return rc;
   cudaStream_t st = S->stream;
   launch_walls<R>(wall_args<R>(S), st);
-  NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
+  NBTE_CK(launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
                               (int64_t)S->D * S->mesh->m.n_cells, st));
   NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 0), S->K, S->G, S->n_items, S->threads, S->smem, st));
   cudaEvent_t e0, e1;
@@ -1303,7 +1351,7 @@ int run_finish(Run& run, nbte_solve_info* info) {
     NBTE_CK(cudaMemsetAsync(S->accE.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
     launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
-    NBTE_CK(launch_gather_tq<R>(S->tqp.as<R>(), S->pos_cell.as<int32_t>(), S->srcTQ_fin.as<R>(), (int64_t)S->D * N,
+    NBTE_CK(launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->pos_cell.as<int32_t>(), S->srcTQ_fin.as<R>(), (int64_t)S->D * N,
                                 st));
     NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 1), S->K, S->G, S->n_items, S->threads, S->smem, st));
     WallHeatArgs<R> wh{};
@@ -1653,7 +1701,8 @@ size_t estimate_cg_bytes(const nbte_solver* S) {
 void shrink(nbte_solver* S) {
   DeviceGuard g(S->device);
   drop_graph(S);
-  DBuf* big[] = {&S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->chunks, &S->chunk_off, &S->tqp,
+  DBuf* big[] = {&S->rec_pos, &S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->chunks, &S->chunk_off,
+                 &S->chunk_doff, &S->chunk_dir, &S->tq_dst,
                  &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part, &S->Tprev, &S->Delta, &S->rhs,
                  &S->delta, &S->dsum, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s, &S->cg_w, &S->cg_x, &S->cg_xw,
                  &S->cg_rw, &S->cg_rcx, &S->cg_scx, &S->cg_Ainv, &S->cg_Ainv64, &S->L_ecol, &S->L_eval,
@@ -1663,6 +1712,7 @@ void shrink(nbte_solver* S) {
   S->layout_key.clear();
   S->rec_key.clear();
   S->chunk_key.clear();
+  S->blk_key.clear();
   S->lap_built = -1;
   S->cg_part_key = -1;
   S->have_state = false;

@@ -22,7 +22,7 @@ struct SweepArgs {
   int full;                      // also accumulate E and q (atomics)
   int Gpad;                      // padded row length of the import/export tables
   int n_stages;                  // shared-memory stages of the copy pipeline
-  int stage_bytes, off_ring, off_stage, off_tq, off_imp, off_den, off_src2;   // shared-memory layout
+  int stage_bytes, off_ring, off_stage, off_imp, off_den, off_src2;   // shared-memory layout
   const R* dinv;                 // FP64 only: [n_items*N*G] denominators 1/(1/tau + v G), else null
   const R* src2;                 // second-order upwind: [n_items*N*G] per position, the
                                  // reconstruction's extra source (sum over faces), else null
@@ -31,8 +31,8 @@ struct SweepArgs {
   const int32_t* item_grp;       // [n_items]
   const int64_t* chunk_off;      // [D+1]
   const Chunk* chunks;
-  const unsigned char* rec;      // packed position records [D*N]
-  const R* tqp;                  // [2*(D*N+2)] (T', Qdot) per position
+  const unsigned char* rec;      // per chunk: its packed position records, then its (T', Qdot) pairs
+  const int64_t* chunk_doff;     // [chunks] byte offset of each chunk's block in rec
   const int64_t* exp_off;        // [D+1]
   const int64_t* imp_off;
   const R* imp;                  // band-group-major import rows
@@ -66,11 +66,19 @@ cudaError_t launch_sweep_batch(const SweepArgs<R>* args, const int32_t* item_sta
                                bool global_ring, bool order2, int n_items, int threads, size_t smem,
                                cudaStream_t st);
 // dinv[(item*N + pos)*G + b] = 1 / (band_inv_tau[g*G+b] + band_v[g*G+b] G_pos),
-// item = i*n_groups + g, G_pos read from the packed position records
-cudaError_t launch_fill_dinv(double* dinv, const unsigned char* rec, int rec_bytes, int off_G, const double* band_v,
-                             const double* band_inv_tau, int D, int n_groups, int G, int64_t N, cudaStream_t st);
+// item = i*n_groups + g, G_pos = pos_G[i*N + pos]
+cudaError_t launch_fill_dinv(double* dinv, const double* pos_G, const double* band_v, const double* band_inv_tau,
+                             int D, int n_groups, int G, int64_t N, cudaStream_t st);
+// Rearrange position-ordered records into chunk blocks (records, then room
+// for the chunk's (T', Qdot) pairs) and set tq_dst: one block per chunk.
+cudaError_t launch_pack_blocks(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
+                               const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
+                               int64_t n_chunks, int64_t N, int rec_size, int pair_bytes, int cap, cudaStream_t st);
+// (T', Qdot) of every position's cell into its chunk's block:
+// ((R2*)data)[tq_dst[q]] = ((R2*)srcTQ)[pos_cell[q]], q = i*N + position
 template <typename R>
-cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st);
+cudaError_t launch_gather_tq(unsigned char* data, const uint32_t* tq_dst, const int32_t* pos_cell, const R* srcTQ,
+                             int64_t n, cudaStream_t st);
 
 // Second-order upwind source of every work item and position, from the
 // previous sweep's distribution e[(i*N + cell)*Bp + band] (direction i, all

@@ -52,6 +52,12 @@ NBTE_HD constexpr RecLayout rec_layout(int elem_bytes, int K) {
   return L;
 }
 
+// Bytes of a chunk's (T', Qdot) pairs behind its records, padded to 16 (the
+// next chunk's block starts 16-byte aligned; records are multiples of 16).
+NBTE_HD constexpr unsigned chunk_tq_bytes(int len, int elem_bytes) {
+  return (unsigned)((len * 2 * elem_bytes + 15) / 16 * 16);
+}
+
 // A chunk: up to CAP consecutive positions of one direction inside one level.
 struct Chunk {
   int32_t pos;       // first position (relative to the direction)

@@ -187,7 +187,6 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
   const int ncons = blockDim.x - 32;
   const int64_t ch0 = a.chunk_off[i];
   const int nch = (int)(a.chunk_off[i + 1] - ch0);
-  const int64_t dbase = (int64_t)i * a.N;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -208,14 +207,21 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       if (base + lane < nch) v = *reinterpret_cast<const int4*>(a.chunks + ch0 + base + lane);
       return v;
     };
+    auto fetch_off = [&](int base) {
+      return base + lane < nch ? a.chunk_doff[ch0 + base + lane] : (int64_t)0;
+    };
     int4 cur = fetch(0), nxt = fetch(32);
+    int64_t cur_off = fetch_off(0), nxt_off = fetch_off(32);
     int issued = 0;
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
       if (c > 0 && (c & 31) == 0) {
         cur = nxt;
         nxt = fetch(c + 32);
+        cur_off = nxt_off;
+        nxt_off = fetch_off(c + 32);
       }
+      const int64_t doff = __shfl_sync(0xffffffffu, cur_off, c & 31);
       Chunk m;
       m.pos = __shfl_sync(0xffffffffu, cur.x, c & 31);
       m.len = __shfl_sync(0xffffffffu, cur.y, c & 31);
@@ -234,13 +240,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         const int s = c % NS;
         meta[s] = m;
         unsigned char* st = stages + (size_t)s * a.stage_bytes;
-        const unsigned rec_bytes = (unsigned)(m.len * RL.size);
-        // (T', Qdot) pairs: copy a 16-byte aligned superset
-        const int64_t q0 = dbase + m.pos;
-        const int per16 = 16 / (int)(2 * sizeof(R));   // pairs per 16 bytes (2 for FP32, 1 for FP64)
-        const int64_t qa = q0 / per16 * per16;
-        const int64_t qe = (q0 + m.len + per16 - 1) / per16 * per16;
-        const unsigned tq_bytes = (unsigned)((qe - qa) * 2 * sizeof(R));
+        // the chunk's records and, right behind them, its (T', Qdot) pairs:
+        // one contiguous block, one copy
+        const unsigned rec_bytes = (unsigned)(m.len * RL.size) + chunk_tq_bytes(m.len, (int)sizeof(R));
         const int nimp = m.nimp_end & 0x3fffffff;
         const unsigned imp_bytes = (unsigned)nimp * (unsigned)(a.Gpad * sizeof(R));
         // FP64: the chunk's denominators, a 16-byte aligned superset
@@ -263,9 +265,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
           const int64_t se = (s0 + m.len + sper16 - 1) / sper16 * sper16;
           s2_bytes = (unsigned)((se - sa) * G * sizeof(R));
         }
-        mbar_arrive_expect_tx(full + s, rec_bytes + tq_bytes + imp_bytes + den_bytes + s2_bytes);
-        bulk_copy(st, a.rec + (size_t)q0 * RL.size, rec_bytes, full + s);
-        bulk_copy(st + a.off_tq, a.tqp + (size_t)qa * 2, tq_bytes, full + s);
+        mbar_arrive_expect_tx(full + s, rec_bytes + imp_bytes + den_bytes + s2_bytes);
+        bulk_copy(st, a.rec + doff, rec_bytes, full + s);
         if (den_bytes) bulk_copy(st + a.off_den, a.dinv + (size_t)da * G, den_bytes, full + s);
         if constexpr (O2) bulk_copy(st + a.off_src2, a.src2 + (size_t)sa * G, s2_bytes, full + s);
         if (nimp > 0)
@@ -306,10 +307,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     }
     const Chunk m = meta[s];
     const unsigned char* st = stages + (size_t)s * a.stage_bytes;
-    const int per16 = 16 / (int)(2 * sizeof(R));
-    const int tq_shift = (int)((dbase + m.pos) % per16);
     using R2 = typename Vec2<R>::T;
-    const R2* tqs = reinterpret_cast<const R2*>(st + a.off_tq) + tq_shift;
+    const R2* tqs = reinterpret_cast<const R2*>(st + (size_t)m.len * RL.size);   // behind the records
     const R* imps = reinterpret_cast<const R*>(st + a.off_imp);
     const int imp0 = m.imp;
     // FP64: this chunk's precomputed denominators (superset starts d_shift early)
@@ -511,34 +510,63 @@ cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int t
                  : launch_gr<R, false, false>(a, K, G, n_items, threads, smem, st);
 }
 
+// One block per chunk: its positions' records (multiples of 16 bytes, copied
+// as 16-byte words) to the chunk's block, and each position's pair index
+__global__ void pack_blocks_kernel(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
+                                   const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
+                                   int64_t N, int rec_size, int pair_bytes) {
+  const int64_t c = blockIdx.x;
+  const Chunk ch = chunks[c];
+  const int64_t doff = chunk_doff[c];
+  const int64_t q0 = (int64_t)chunk_dir[c] * N + ch.pos;
+  const int w16 = rec_size / 16;
+  const uint4* src = reinterpret_cast<const uint4*>(rec_pos + (size_t)q0 * rec_size);
+  uint4* dst = reinterpret_cast<uint4*>(blk + doff);
+  for (int t = threadIdx.x; t < ch.len * w16; t += blockDim.x) dst[t] = src[t];
+  const uint32_t tq0 = (uint32_t)((doff + (int64_t)ch.len * rec_size) / pair_bytes);
+  for (int j = threadIdx.x; j < ch.len; j += blockDim.x) tq_dst[q0 + j] = tq0 + (uint32_t)j;
+}
+
+cudaError_t launch_pack_blocks(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
+                               const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
+                               int64_t n_chunks, int64_t N, int rec_size, int pair_bytes, int cap, cudaStream_t st) {
+  if (n_chunks == 0) return cudaSuccess;
+  if (rec_size % 16 != 0 || n_chunks > 0x7fffffff) return cudaErrorInvalidValue;
+  (void)cap;
+  pack_blocks_kernel<<<(unsigned)n_chunks, 128, 0, st>>>(blk, tq_dst, rec_pos, chunks, chunk_doff, chunk_dir, N,
+                                                         rec_size, pair_bytes);
+  return cudaGetLastError();
+}
+
 // FP64 denominators of every (work item, position); one thread per pair
-__global__ void fill_dinv_kernel(double* dinv, const unsigned char* rec, int rec_bytes, int off_G,
-                                 const double* band_v, const double* band_inv_tau, int D, int ng, int G, int64_t N) {
+__global__ void fill_dinv_kernel(double* dinv, const double* pos_G, const double* band_v, const double* band_inv_tau,
+                                 int D, int ng, int G, int64_t N) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)D * ng * N) return;
   const int64_t item = t / N, pos = t - item * N;
   const int i = (int)(item / ng), g = (int)(item - (int64_t)i * ng);
-  const double Gc = *reinterpret_cast<const double*>(rec + ((size_t)i * N + pos) * rec_bytes + off_G);
+  const double Gc = pos_G[(size_t)i * N + pos];
   for (int b = 0; b < G; ++b) dinv[t * G + b] = 1.0 / (band_inv_tau[g * G + b] + band_v[g * G + b] * Gc);
 }
 
-cudaError_t launch_fill_dinv(double* dinv, const unsigned char* rec, int rec_bytes, int off_G, const double* band_v,
-                             const double* band_inv_tau, int D, int n_groups, int G, int64_t N, cudaStream_t st) {
+cudaError_t launch_fill_dinv(double* dinv, const double* pos_G, const double* band_v, const double* band_inv_tau,
+                             int D, int n_groups, int G, int64_t N, cudaStream_t st) {
   const int64_t n = (int64_t)D * n_groups * N;
   if (n == 0) return cudaSuccess;
-  fill_dinv_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dinv, rec, rec_bytes, off_G, band_v, band_inv_tau, D,
-                                                                n_groups, G, N);
+  fill_dinv_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dinv, pos_G, band_v, band_inv_tau, D, n_groups, G,
+                                                                N);
   return cudaGetLastError();
 }
 
 // (T', Qdot) of every position's cell, in each direction's level order, so
 // the sweep's producer can bulk-copy them with the position records
 template <typename R>
-__global__ void gather_tq_kernel(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n) {
+__global__ void gather_tq_kernel(R* data, const uint32_t* tq_dst, const int32_t* pos_cell, const R* srcTQ,
+                                 int64_t n) {
   using R2 = typename Vec2<R>::T;
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  reinterpret_cast<R2*>(tqp)[q] = __ldg(reinterpret_cast<const R2*>(srcTQ) + __ldcs(pos_cell + q));
+  reinterpret_cast<R2*>(data)[__ldcs(tq_dst + q)] = __ldg(reinterpret_cast<const R2*>(srcTQ) + __ldcs(pos_cell + q));
 }
 
 // Second-order upwind sources.  One thread per (direction, position): it
@@ -650,9 +678,11 @@ cudaError_t launch_src2(const Src2Args<R>& a, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_gather_tq(R* tqp, const int32_t* pos_cell, const R* srcTQ, int64_t n, cudaStream_t st) {
+cudaError_t launch_gather_tq(unsigned char* data, const uint32_t* tq_dst, const int32_t* pos_cell, const R* srcTQ,
+                             int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  gather_tq_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tqp, pos_cell, srcTQ, n);
+  gather_tq_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<R*>(data), tq_dst, pos_cell,
+                                                                    srcTQ, n);
   return cudaGetLastError();
 }
 
@@ -664,7 +694,9 @@ template cudaError_t launch_sweep_batch<double>(const SweepArgs<double>*, const 
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, int, int, int, int, size_t, cudaStream_t);
 template cudaError_t launch_src2<float>(const Src2Args<float>&, cudaStream_t);
 template cudaError_t launch_src2<double>(const Src2Args<double>&, cudaStream_t);
-template cudaError_t launch_gather_tq<float>(float*, const int32_t*, const float*, int64_t, cudaStream_t);
-template cudaError_t launch_gather_tq<double>(double*, const int32_t*, const double*, int64_t, cudaStream_t);
+template cudaError_t launch_gather_tq<float>(unsigned char*, const uint32_t*, const int32_t*, const float*, int64_t,
+                                             cudaStream_t);
+template cudaError_t launch_gather_tq<double>(unsigned char*, const uint32_t*, const int32_t*, const double*, int64_t,
+                                              cudaStream_t);
 
 }  // namespace nbte
