@@ -150,12 +150,15 @@ struct nbte_solver {
   int64_t rc_cells = 0;
   // most wall/lag imports in one chunk, per chunk length (sizes the stages' import region)
   int64_t cimp_plan = -1;
-  std::map<int, int> cimp_max;
+  std::map<int, int> cimp_max, csub_max;
   double W = 0, beta = 0, Ctot = 0;
-  DBuf rec_pos, rec, pos_cell, chunks, chunk_off, chunk_doff, chunk_dir, tq_dst, gring, e_scratch, dinv;
+  DBuf rec_pos, rec, pos_cell, chunks, chunk_off, chunk_doff, chunk_dir, chunk_sub_ptr, chunk_sub_end, tq_dst, gring,
+      e_scratch, dinv;
   std::string blk_key;
   std::vector<Chunk> h_chunks;                // host copy of the chunks of the current chunk length
   std::vector<int64_t> h_chunk_off;           // [D+1] first chunk of each direction
+  std::vector<int64_t> h_sub_ptr;             // [chunks+1] CSR of the chunks' level ends
+  std::vector<int32_t> h_sub_end;
   int64_t gring_stride = 0;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
@@ -211,7 +214,8 @@ struct DeviceGuard {
 
 size_t device_bytes(const nbte_solver* S) {
   const DBuf* all[] = {&S->rec_pos, &S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->dinv, &S->chunks,
-                       &S->chunk_off, &S->chunk_doff, &S->chunk_dir, &S->tq_dst, &S->exp_off, &S->imp_off,
+                       &S->chunk_off, &S->chunk_doff, &S->chunk_dir, &S->chunk_sub_ptr, &S->chunk_sub_end,
+                       &S->tq_dst, &S->exp_off, &S->imp_off,
                        &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
                        &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
@@ -342,8 +346,9 @@ int ensure_records(nbte_solver* S) {
   return NBTE_OK;
 }
 
-// The sweep's chunk blocks for the current chunks: each chunk's records,
-// then room for its (T', Qdot) pairs, so that one bulk copy brings both.
+// The sweep's chunk blocks for the current chunks: each chunk's header (its
+// level count and level ends), its records, then room for its (T', Qdot)
+// pairs, so that one bulk copy brings all three.
 // chunk_doff holds each block's byte offset; tq_dst, per position
 // (direction-major), the index of its pair in units of pairs.  Packed on the
 // device from the position-ordered records.
@@ -362,89 +367,139 @@ int ensure_blocks(nbte_solver* S, int cap) {
     for (int64_t c = S->h_chunk_off[i]; c < S->h_chunk_off[i + 1]; ++c) {
       doff[c] = (int64_t)total;
       cdir[c] = i;
-      total += (size_t)S->h_chunks[c].len * L.size + chunk_tq_bytes(S->h_chunks[c].len, (int)sizeof(R));
+      const Chunk& ch = S->h_chunks[c];
+      total += chunk_header_bytes(chunk_levels(ch.nimp_end)) + (size_t)ch.len * L.size +
+               chunk_tq_bytes(ch.len, (int)sizeof(R));
     }
   if (total / pair > 0xffffffffull) return fail(NBTE_ERR_OOM, "position records exceed the 32-bit pair index");
   NBTE_CK(upload(S->chunk_doff, doff));
   NBTE_CK(upload(S->chunk_dir, cdir));
+  NBTE_CK(upload(S->chunk_sub_ptr, S->h_sub_ptr));
+  NBTE_CK(upload(S->chunk_sub_end, S->h_sub_end));
   NBTE_CK(S->rec.alloc(total));
   NBTE_CK(S->tq_dst.alloc((size_t)P.D * P.N * 4));
   NBTE_CK(cudaMemsetAsync(S->rec.p, 0, S->rec.bytes, S->stream));
   NBTE_CK(launch_pack_blocks(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->rec_pos.as<unsigned char>(),
                              S->chunks.as<Chunk>(), S->chunk_doff.as<int64_t>(), S->chunk_dir.as<int32_t>(),
-                             (int64_t)nch, P.N, L.size, pair, cap, S->stream));
+                             S->chunk_sub_ptr.as<int64_t>(), S->chunk_sub_end.as<int32_t>(), (int64_t)nch, P.N,
+                             L.size, pair, S->stream));
   NBTE_CK(cudaStreamSynchronize(S->stream));
   S->blk_key = key;
   return NBTE_OK;
 }
 
-// Chunks of at most cap positions inside one level, with each chunk's slice
-// of the direction's imports (imports are numbered in position order).
-int ensure_chunks(nbte_solver* S, int cap) {
-  const std::string key = std::to_string(cap) + "/" + std::to_string(S->plan_built);
-  if (key == S->chunk_key && S->chunks.p) return NBTE_OK;
-  const Plan& P = S->plan;
+// Chunks of one sweep: consecutive whole levels of a direction are packed
+// into one chunk while they total at most cap positions (the consumers
+// separate them with a named barrier, the copy and stage hand-off are
+// shared); a level wider than cap is split into chunks of its own.
+// sub_end lists, per chunk, where each of its levels ends (relative to the
+// chunk's first position).  Imports are numbered in position order, so each
+// chunk's imports are one contiguous slice.
+struct ChunkList {
   std::vector<Chunk> ch;
-  std::vector<int64_t> off(P.D + 1, 0);
+  std::vector<int64_t> off;        // [D+1] first chunk of each direction
+  std::vector<int64_t> sub_ptr;    // [chunks+1]
+  std::vector<int32_t> sub_end;
+  int max_imp = 0, max_sub = 0;
+};
+
+int build_chunks(const Plan& P, int cap, ChunkList& out) {
+  out = ChunkList{};
+  out.off.assign(P.D + 1, 0);
+  out.sub_ptr.push_back(0);
   for (int i = 0; i < P.D; ++i) {
     int32_t imp = 0;
     const int32_t* lp = P.level_ptr.data() + P.lvl_off[i];
     const int L = (int)(P.lvl_off[i + 1] - P.lvl_off[i]) - 1;
-    for (int l = 0; l < L; ++l)
-      for (int32_t p0 = lp[l]; p0 < lp[l + 1]; p0 += cap) {
-        const int32_t p1 = std::min(lp[l + 1], p0 + cap);
-        int32_t nimp = 0;
-        for (int32_t p = p0; p < p1; ++p)
-          for (int k = 0; k < P.K; ++k) nimp += P.pos_ref[((size_t)i * P.K + k) * P.N + p] < 0;
-        Chunk c;
-        c.pos = p0;
-        c.len = p1 - p0;
-        c.imp = imp;
-        c.nimp_end = nimp | (p1 == lp[l + 1] ? (1 << 30) : 0);
-        ch.push_back(c);
-        imp += nimp;
+    auto n_imports = [&](int32_t p0, int32_t p1) {
+      int32_t n = 0;
+      for (int k = 0; k < P.K; ++k) {
+        const int32_t* ref = P.pos_ref.data() + ((size_t)i * P.K + k) * P.N;
+        for (int32_t p = p0; p < p1; ++p) n += ref[p] < 0;
       }
+      return n;
+    };
+    auto emit = [&](int32_t p0, int32_t p1, bool level_end, const std::vector<int32_t>& ends) {
+      const int32_t nimp = n_imports(p0, p1);
+      Chunk c;
+      c.pos = p0;
+      c.len = p1 - p0;
+      c.imp = imp;
+      c.nimp_end = chunk_flags(nimp, (int)ends.size(), level_end);
+      out.ch.push_back(c);
+      for (int32_t e : ends) out.sub_end.push_back(e);
+      out.sub_ptr.push_back((int64_t)out.sub_end.size());
+      out.max_imp = std::max(out.max_imp, (int)nimp);
+      out.max_sub = std::max(out.max_sub, (int)ends.size());
+      imp += nimp;
+    };
+    int32_t b0 = -1;                 // first position of the chunk being filled
+    std::vector<int32_t> ends;       // its level ends, relative to b0
+    for (int l = 0; l < L; ++l) {
+      const int32_t w = lp[l + 1] - lp[l];
+      if (w > cap) {
+        if (b0 >= 0) emit(b0, lp[l], true, ends);
+        b0 = -1;
+        ends.clear();
+        for (int32_t p0 = lp[l]; p0 < lp[l + 1]; p0 += cap) {
+          const int32_t p1 = std::min(lp[l + 1], p0 + cap);
+          emit(p0, p1, p1 == lp[l + 1], {p1 - p0});
+        }
+        continue;
+      }
+      if (b0 >= 0 && lp[l + 1] - b0 > cap) {
+        emit(b0, lp[l], true, ends);
+        b0 = -1;
+        ends.clear();
+      }
+      if (b0 < 0) b0 = lp[l];
+      ends.push_back(lp[l + 1] - b0);
+    }
+    if (b0 >= 0) emit(b0, lp[L], true, ends);
     if (imp != P.imp_off[i + 1] - P.imp_off[i]) return fail(NBTE_ERR_MESH, "internal: import numbering");
-    off[i + 1] = (int64_t)ch.size();
+    out.off[i + 1] = (int64_t)out.ch.size();
   }
-  NBTE_CK(upload(S->chunks, ch));
-  NBTE_CK(upload(S->chunk_off, off));
-  S->h_chunks = std::move(ch);
-  S->h_chunk_off = std::move(off);
-  S->chunk_key = key;
+  if (out.max_imp > kChunkMaxImports || out.max_sub > kChunkMaxLevels)
+    return fail(NBTE_ERR_MESH, "internal: chunk descriptor field overflow");
   return NBTE_OK;
 }
 
-// the most imports any chunk of length <= cap holds (chunks as ensure_chunks
-// cuts them): the size of a copy stage's import region
-int max_chunk_imports(nbte_solver* S, int cap) {
+// the most imports and levels any chunk of length <= cap holds (they size a
+// copy stage's import region and block header)
+int chunk_extents(nbte_solver* S, int cap, int* max_imp, int* max_sub) {
   if (S->cimp_plan != S->plan_built) {
     S->cimp_max.clear();
+    S->csub_max.clear();
     S->cimp_plan = S->plan_built;
   }
   auto it = S->cimp_max.find(cap);
-  if (it != S->cimp_max.end()) return it->second;
-  const Plan& P = S->plan;
-  int best = 0;
-  for (int i = 0; i < P.D; ++i) {
-    const int32_t* lp = P.level_ptr.data() + P.lvl_off[i];
-    const int L = (int)(P.lvl_off[i + 1] - P.lvl_off[i]) - 1;
-    for (int l = 0; l < L; ++l)
-      for (int32_t p0 = lp[l]; p0 < lp[l + 1]; p0 += cap) {
-        const int32_t p1 = std::min(lp[l + 1], p0 + cap);
-        int nimp = 0;
-        for (int k = 0; k < P.K; ++k) {
-          const int32_t* ref = P.pos_ref.data() + ((size_t)i * P.K + k) * P.N;
-          for (int32_t p = p0; p < p1; ++p) nimp += ref[p] < 0;
-        }
-        best = std::max(best, nimp);
-      }
+  if (it == S->cimp_max.end()) {
+    ChunkList cl;
+    int rc = build_chunks(S->plan, cap, cl);
+    if (rc) return rc;
+    S->cimp_max[cap] = cl.max_imp;
+    S->csub_max[cap] = cl.max_sub;
   }
-  S->cimp_max[cap] = best;
-  return best;
+  *max_imp = S->cimp_max[cap];
+  *max_sub = S->csub_max[cap];
+  return NBTE_OK;
 }
 
-bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+int ensure_chunks(nbte_solver* S, int cap) {
+  const std::string key = std::to_string(cap) + "/" + std::to_string(S->plan_built);
+  if (key == S->chunk_key && S->chunks.p) return NBTE_OK;
+  ChunkList cl;
+  int rc = build_chunks(S->plan, cap, cl);
+  if (rc) return rc;
+  NBTE_CK(upload(S->chunks, cl.ch));
+  NBTE_CK(upload(S->chunk_off, cl.off));
+  S->h_chunks = std::move(cl.ch);
+  S->h_chunk_off = std::move(cl.off);
+  S->h_sub_ptr = std::move(cl.sub_ptr);
+  S->h_sub_end = std::move(cl.sub_end);
+  S->chunk_key = key;
+  return NBTE_OK;
+}
 
 int64_t tune_key(const nbte_solver* S) { return S->plan_built * 1000003 + S->version_bands; }
 
@@ -479,11 +534,16 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   // precomputed denominators 1/(1/tau + v G) of the chunk's positions)
   const bool order2 = o.order == 2;
   int off_src2 = 0;
-  // import rows of a chunk: sized by the fullest chunk, not by cap * K
-  const int cimp = max_chunk_imports(S, cap);
+  // import rows of a chunk: sized by the fullest chunk, not by cap * K; the
+  // block header by the chunk with the most levels
+  int cimp = 0, csub = 0;
+  {
+    const int rc0 = chunk_extents(S, cap, &cimp, &csub);
+    if (rc0) return rc0;
+  }
   auto stage_of = [&](int Gv, int& off_tq, int& off_imp, int& off_den) {
     const int gpad = padded_group(Gv, sz);
-    const int rec = (cap * RL.size + 15) / 16 * 16;
+    const int rec = (int)chunk_header_bytes(csub) + cap * RL.size;
     const int tq = ((cap + 2) * 2 * sz + 15) / 16 * 16;
     const int imp = cimp * gpad * sz;
     const int den = prec ? 0 : ((cap + 2) * Gv * 8 + 15) / 16 * 16;
@@ -1702,7 +1762,7 @@ void shrink(nbte_solver* S) {
   DeviceGuard g(S->device);
   drop_graph(S);
   DBuf* big[] = {&S->rec_pos, &S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->chunks, &S->chunk_off,
-                 &S->chunk_doff, &S->chunk_dir, &S->tq_dst,
+                 &S->chunk_doff, &S->chunk_dir, &S->chunk_sub_ptr, &S->chunk_sub_end, &S->tq_dst,
                  &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part, &S->Tprev, &S->Delta, &S->rhs,
                  &S->delta, &S->dsum, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s, &S->cg_w, &S->cg_x, &S->cg_xw,
                  &S->cg_rw, &S->cg_rcx, &S->cg_scx, &S->cg_Ainv, &S->cg_Ainv64, &S->L_ecol, &S->L_eval,

@@ -69,11 +69,13 @@ cudaError_t launch_sweep_batch(const SweepArgs<R>* args, const int32_t* item_sta
 // item = i*n_groups + g, G_pos = pos_G[i*N + pos]
 cudaError_t launch_fill_dinv(double* dinv, const double* pos_G, const double* band_v, const double* band_inv_tau,
                              int D, int n_groups, int G, int64_t N, cudaStream_t st);
-// Rearrange position-ordered records into chunk blocks (records, then room
-// for the chunk's (T', Qdot) pairs) and set tq_dst: one block per chunk.
+// Rearrange position-ordered records into chunk blocks (header with the
+// chunk's level ends, records, then room for the chunk's (T', Qdot) pairs)
+// and set tq_dst: one block per chunk.
 cudaError_t launch_pack_blocks(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
                                const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
-                               int64_t n_chunks, int64_t N, int rec_size, int pair_bytes, int cap, cudaStream_t st);
+                               const int64_t* sub_ptr, const int32_t* sub_end, int64_t n_chunks, int64_t N,
+                               int rec_size, int pair_bytes, cudaStream_t st);
 // (T', Qdot) of every position's cell into its chunk's block:
 // ((R2*)data)[tq_dst[q]] = ((R2*)srcTQ)[pos_cell[q]], q = i*N + position
 template <typename R>

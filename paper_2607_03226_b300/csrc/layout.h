@@ -58,12 +58,27 @@ NBTE_HD constexpr unsigned chunk_tq_bytes(int len, int elem_bytes) {
   return (unsigned)((len * 2 * elem_bytes + 15) / 16 * 16);
 }
 
-// A chunk: up to CAP consecutive positions of one direction inside one level.
+// A chunk: up to CAP consecutive positions of one direction, either whole
+// consecutive levels or a piece of one level wider than CAP.
 struct Chunk {
   int32_t pos;       // first position (relative to the direction)
   int32_t len;       // positions
   int32_t imp;       // first import (relative to the direction)
-  int32_t nimp_end;  // number of imports in the chunk (low 30 bits); bit 30: last chunk of its level
+  int32_t nimp_end;  // bits 0-15: imports in the chunk; bits 16-29: levels in the
+                     // chunk; bit 30: the chunk ends a level
 };
+constexpr int kChunkMaxImports = 0xffff;
+constexpr int kChunkMaxLevels = 0x3fff;
+NBTE_HD constexpr int32_t chunk_flags(int n_imports, int n_levels, bool level_end) {
+  return (int32_t)(n_imports | (n_levels << 16) | (level_end ? (1 << 30) : 0));
+}
+NBTE_HD constexpr int chunk_imports(int32_t f) { return f & 0xffff; }
+NBTE_HD constexpr int chunk_levels(int32_t f) { return (f >> 16) & 0x3fff; }
+NBTE_HD constexpr bool chunk_level_end(int32_t f) { return (f & (1 << 30)) != 0; }
+// A chunk block starts with a header: int32 level count, then each level's
+// end (relative to the chunk's first position), padded to 16 bytes.
+NBTE_HD constexpr unsigned chunk_header_bytes(int n_levels) {
+  return (unsigned)(((n_levels + 1) * 4 + 15) / 16 * 16);
+}
 
 }  // namespace nbte

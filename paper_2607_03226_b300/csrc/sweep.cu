@@ -240,10 +240,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         const int s = c % NS;
         meta[s] = m;
         unsigned char* st = stages + (size_t)s * a.stage_bytes;
-        // the chunk's records and, right behind them, its (T', Qdot) pairs:
-        // one contiguous block, one copy
-        const unsigned rec_bytes = (unsigned)(m.len * RL.size) + chunk_tq_bytes(m.len, (int)sizeof(R));
-        const int nimp = m.nimp_end & 0x3fffffff;
+        // the chunk's header, records and (T', Qdot) pairs: one contiguous
+        // block, one copy
+        const unsigned rec_bytes = chunk_header_bytes(chunk_levels(m.nimp_end)) + (unsigned)(m.len * RL.size) +
+                                   chunk_tq_bytes(m.len, (int)sizeof(R));
+        const int nimp = chunk_imports(m.nimp_end);
         const unsigned imp_bytes = (unsigned)nimp * (unsigned)(a.Gpad * sizeof(R));
         // FP64: the chunk's denominators, a 16-byte aligned superset
         unsigned den_bytes = 0;
@@ -307,8 +308,12 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     }
     const Chunk m = meta[s];
     const unsigned char* st = stages + (size_t)s * a.stage_bytes;
+    // the block: header (level count, level ends), records, (T', Qdot) pairs
+    const int n_lev = chunk_levels(m.nimp_end);
+    const int32_t* lev_end = reinterpret_cast<const int32_t*>(st) + 1;
+    const unsigned char* recs = st + chunk_header_bytes(n_lev);
     using R2 = typename Vec2<R>::T;
-    const R2* tqs = reinterpret_cast<const R2*>(st + (size_t)m.len * RL.size);   // behind the records
+    const R2* tqs = reinterpret_cast<const R2*>(recs + (size_t)m.len * RL.size);
     const R* imps = reinterpret_cast<const R*>(st + a.off_imp);
     const int imp0 = m.imp;
     // FP64: this chunk's precomputed denominators (superset starts d_shift early)
@@ -318,70 +323,78 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     constexpr int sper16 = (int)(16 / (G * sizeof(R))) > 1 ? (int)(16 / (G * sizeof(R))) : 1;
     const R* s2 = reinterpret_cast<const R*>(st + a.off_src2);
     const int s_shift = O2 ? (int)(((int64_t)item * a.N + m.pos) % sper16) : 0;
-    for (int j = ct; j < m.len; j += ncons) {
-      uint4 w[NQ];
+    // the chunk's levels in order, a named barrier between them (each sees
+    // the ring values the previous one wrote)
+    int lb = 0;
+    for (int lv = 0; lv < n_lev; ++lv) {
+      const int le = lev_end[lv];
+      for (int j = lb + ct; j < le; j += ncons) {
+        uint4 w[NQ];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) w[q] = reinterpret_cast<const uint4*>(st)[j * NQ + q];
-      const int cell = (int)rec_word(w, 0);
-      const int slot = (int)rec_word(w, 1);
-      const int ex = (int)rec_word(w, 2);
-      const R Gc = RecField<R>::get(w, RL.off_G);
-      const R2 tq = tqs[j];
-      const R T = tq.x;
-      const R Q = tq.y;
-      R e0[G], up[G];
-#pragma unroll
-      for (int b = 0; b < G; ++b) {
-        e0[b] = cw[b] * T;
-        up[b] = R(0);
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int ref = (int)rec_word(w, RL.off_ref / 4 + k);
-        const R cf = RecField<R>::get(w, RL.off_coef + k * (int)sizeof(R));
-        const R* src = ref >= 0 ? ring + ref * G : imps + ((-1 - ref) - imp0) * GP;
-        R eu[G];
-        load_vals<R, G>(src, eu);
-#pragma unroll
-        for (int b = 0; b < G; ++b) up[b] += cf * (eu[b] - e0[b]);
-      }
-      if constexpr (O2) {
-#pragma unroll
-        for (int b = 0; b < G; ++b) up[b] += s2[(j + s_shift) * G + b];
-      }
-      R e[G];
-      R nl = R(0);
-#pragma unroll
-      for (int b = 0; b < G; ++b) {
-        R den;
-        if constexpr (sizeof(R) == 8) den = dens[(j + d_shift) * G + b];
-        else den = recip(itau[b] + vb[b] * Gc);
-        const R phi = (aQ[b] * Q + vb[b] * up[b]) * den;
-        e[b] = e0[b] + phi;
-        nl += wt[b] * phi;
-      }
-      if (slot >= 0) store_vals<R, G>(ring + slot * G, e);
-      if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * GP, e);
-      if (a.e_out)
-        store_vals<R, G>(a.e_out + (size_t)i * a.e_out_dstride + (size_t)g * a.e_out_gstride +
-                             (size_t)cell * a.e_out_cstride,
-                         e);
-      part[cell] = nl;
-      if (a.full) {
-        R es = R(0), evs = R(0);
+        for (int q = 0; q < NQ; ++q) w[q] = reinterpret_cast<const uint4*>(recs)[j * NQ + q];
+        const int cell = (int)rec_word(w, 0);
+        const int slot = (int)rec_word(w, 1);
+        const int ex = (int)rec_word(w, 2);
+        const R Gc = RecField<R>::get(w, RL.off_G);
+        const R2 tq = tqs[j];
+        const R T = tq.x;
+        const R Q = tq.y;
+        R e0[G], up[G];
 #pragma unroll
         for (int b = 0; b < G; ++b) {
-          es += e[b];
-          evs += vb[b] * e[b];
+          e0[b] = cw[b] * T;
+          up[b] = R(0);
         }
-        atomicAdd(a.accE + cell, wi * (double)es);
-        for (int d = 0; d < a.dim; ++d)
-          atomicAdd(a.accQ + (int64_t)cell * a.dim + d, wi * a.dir_s[i * 3 + d] * (double)evs);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int ref = (int)rec_word(w, RL.off_ref / 4 + k);
+          const R cf = RecField<R>::get(w, RL.off_coef + k * (int)sizeof(R));
+          const R* src = ref >= 0 ? ring + ref * G : imps + ((-1 - ref) - imp0) * GP;
+          R eu[G];
+          load_vals<R, G>(src, eu);
+#pragma unroll
+          for (int b = 0; b < G; ++b) up[b] += cf * (eu[b] - e0[b]);
+        }
+        if constexpr (O2) {
+#pragma unroll
+          for (int b = 0; b < G; ++b) up[b] += s2[(j + s_shift) * G + b];
+        }
+        R e[G];
+        R nl = R(0);
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+          R den;
+          if constexpr (sizeof(R) == 8) den = dens[(j + d_shift) * G + b];
+          else den = recip(itau[b] + vb[b] * Gc);
+          const R phi = (aQ[b] * Q + vb[b] * up[b]) * den;
+          e[b] = e0[b] + phi;
+          nl += wt[b] * phi;
+        }
+        if (slot >= 0) store_vals<R, G>(ring + slot * G, e);
+        if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * GP, e);
+        if (a.e_out)
+          store_vals<R, G>(a.e_out + (size_t)i * a.e_out_dstride + (size_t)g * a.e_out_gstride +
+                               (size_t)cell * a.e_out_cstride,
+                           e);
+        part[cell] = nl;
+        if (a.full) {
+          R es = R(0), evs = R(0);
+#pragma unroll
+          for (int b = 0; b < G; ++b) {
+            es += e[b];
+            evs += vb[b] * e[b];
+          }
+          atomicAdd(a.accE + cell, wi * (double)es);
+          for (int d = 0; d < a.dim; ++d)
+            atomicAdd(a.accQ + (int64_t)cell * a.dim + d, wi * a.dir_s[i * 3 + d] * (double)evs);
+        }
       }
+      if (lv + 1 < n_lev) consumer_barrier(ncons);
+      lb = le;
     }
     __syncwarp();
     if ((ct & 31) == 0) mbar_arrive(empty + s);
-    if (m.nimp_end & (1 << 30)) consumer_barrier(ncons);
+    if (chunk_level_end(m.nimp_end)) consumer_barrier(ncons);
   }
 }
 
@@ -514,27 +527,32 @@ cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int t
 // as 16-byte words) to the chunk's block, and each position's pair index
 __global__ void pack_blocks_kernel(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
                                    const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
-                                   int64_t N, int rec_size, int pair_bytes) {
+                                   const int64_t* sub_ptr, const int32_t* sub_end, int64_t N, int rec_size,
+                                   int pair_bytes) {
   const int64_t c = blockIdx.x;
   const Chunk ch = chunks[c];
   const int64_t doff = chunk_doff[c];
   const int64_t q0 = (int64_t)chunk_dir[c] * N + ch.pos;
+  const int n_lev = chunk_levels(ch.nimp_end);
+  int32_t* hdr = reinterpret_cast<int32_t*>(blk + doff);
+  for (int t = threadIdx.x; t <= n_lev; t += blockDim.x) hdr[t] = t == 0 ? n_lev : sub_end[sub_ptr[c] + t - 1];
+  const int64_t roff = doff + chunk_header_bytes(n_lev);
   const int w16 = rec_size / 16;
   const uint4* src = reinterpret_cast<const uint4*>(rec_pos + (size_t)q0 * rec_size);
-  uint4* dst = reinterpret_cast<uint4*>(blk + doff);
+  uint4* dst = reinterpret_cast<uint4*>(blk + roff);
   for (int t = threadIdx.x; t < ch.len * w16; t += blockDim.x) dst[t] = src[t];
-  const uint32_t tq0 = (uint32_t)((doff + (int64_t)ch.len * rec_size) / pair_bytes);
+  const uint32_t tq0 = (uint32_t)((roff + (int64_t)ch.len * rec_size) / pair_bytes);
   for (int j = threadIdx.x; j < ch.len; j += blockDim.x) tq_dst[q0 + j] = tq0 + (uint32_t)j;
 }
 
 cudaError_t launch_pack_blocks(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
                                const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
-                               int64_t n_chunks, int64_t N, int rec_size, int pair_bytes, int cap, cudaStream_t st) {
+                               const int64_t* sub_ptr, const int32_t* sub_end, int64_t n_chunks, int64_t N,
+                               int rec_size, int pair_bytes, cudaStream_t st) {
   if (n_chunks == 0) return cudaSuccess;
   if (rec_size % 16 != 0 || n_chunks > 0x7fffffff) return cudaErrorInvalidValue;
-  (void)cap;
-  pack_blocks_kernel<<<(unsigned)n_chunks, 128, 0, st>>>(blk, tq_dst, rec_pos, chunks, chunk_doff, chunk_dir, N,
-                                                         rec_size, pair_bytes);
+  pack_blocks_kernel<<<(unsigned)n_chunks, 128, 0, st>>>(blk, tq_dst, rec_pos, chunks, chunk_doff, chunk_dir,
+                                                         sub_ptr, sub_end, N, rec_size, pair_bytes);
   return cudaGetLastError();
 }
 
