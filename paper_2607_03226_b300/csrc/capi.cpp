@@ -125,7 +125,11 @@ struct nbte_solver {
   std::vector<double> s, w;
   std::vector<BC> bcs;
   bool bcs_set = false;
-  std::vector<double> Q;   // internal order
+  // heat source: caller order in pinned host memory (what the caller set),
+  // internal order on the host on demand (Q) and on the device (Qd)
+  double* h_qc = nullptr;
+  int64_t q_dev_version = -1, q_host_version = -1;
+  std::vector<double> Q;   // internal order, valid for q_host_version
   int64_t version_plan = 0, version_bands = 0, version_q = 0;
 
   // ---- plan (depends on quadrature and walls)
@@ -162,6 +166,7 @@ struct nbte_solver {
   int64_t gring_stride = 0;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
   DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
+  DBuf perm_d, io_d;   // caller index of each internal cell; caller-order staging on the device
   DBuf cg_r, cg_u, cg_w, cg_p, cg_s, cg_xw, cg_slots, cg_bar, cg_err, cg_it, cg_res;
   DBuf cg_Ainv64;
   DBuf cg_x, cg_rw, cg_rcx, cg_scx, cg_perm, cg_agg_rel, cg_agg_cell, cg_blk_cell, cg_blk_agg, cg_Ainv;
@@ -190,6 +195,7 @@ struct nbte_solver {
 
   ~nbte_solver() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (h_qc) cudaFreeHost(h_qc);
     if (h_res) cudaFreeHost(h_res);
     if (h_misc) cudaFreeHost(h_misc);
     if (h_stage) cudaFreeHost(h_stage);
@@ -221,6 +227,7 @@ size_t device_bytes(const nbte_solver* S) {
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
                        &S->band_CoW, &S->band_v64, &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part,
                        &S->T, &S->Tprev, &S->Tkin, &S->Delta, &S->rhs, &S->delta, &S->Qd, &S->Vd, &S->dsum,
+                       &S->perm_d, &S->io_d,
                        &S->accE, &S->accQ, &S->res, &S->heat, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s,
                        &S->cg_w, &S->cg_slots, &S->cg_err, &S->cg_it, &S->cg_res, &S->cg_x, &S->cg_rw,
                        &S->cg_rcx, &S->cg_scx, &S->cg_xw, &S->cg_bar, &S->cg_Ainv64,
@@ -752,18 +759,51 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   NBTE_CK(S->heat.alloc((size_t)S->n_wf * 8));
   NBTE_CK(cudaMemcpyAsync(S->Vd.p, S->mesh->m.V.data(), N * 8, cudaMemcpyHostToDevice, S->stream));
   NBTE_CK(cudaStreamSynchronize(S->stream));
-  S->version_q = -1;   // force heat-source upload
+  S->q_dev_version = -2;   // Qd was reallocated: upload the heat source again
   S->layout_key = key;
   S->have_state = false;
   return NBTE_OK;
 }
 
-int ensure_q(nbte_solver* S) {
-  static_cast<void>(S);
+// the caller's cell index of every internal cell, on the device
+int ensure_perm(nbte_solver* S) {
   const int64_t N = S->mesh->m.n_cells;
-  if (S->Q.empty()) S->Q.assign(N, 0.0);
-  NBTE_CK(cudaMemcpyAsync(S->Qd.p, S->Q.data(), N * 8, cudaMemcpyHostToDevice, S->stream));
+  if (S->perm_d.p && S->perm_d.bytes == (size_t)N * 4) return NBTE_OK;
+  std::vector<int32_t> p(N);
+  for (int64_t c = 0; c < N; ++c) p[c] = (int32_t)S->mesh->m.perm[c];
+  NBTE_CK(upload(S->perm_d, p));
   return NBTE_OK;
+}
+
+// device heat source (internal order) for the caller's last setting: the
+// pinned caller-order copy goes up once and is reordered on the device
+int ensure_q(nbte_solver* S) {
+  const int64_t N = S->mesh->m.n_cells;
+  if (S->q_dev_version == S->version_q && S->Qd.p) return NBTE_OK;
+  if (!S->h_qc) {
+    NBTE_CK(cudaMemsetAsync(S->Qd.p, 0, N * 8, S->stream));
+  } else {
+    int rc = ensure_perm(S);
+    if (rc) return rc;
+    NBTE_CK(S->io_d.alloc(std::max<size_t>(S->io_d.bytes, (size_t)N * 8 * S->mesh->m.dim)));
+    NBTE_CK(cudaMemcpyAsync(S->io_d.p, S->h_qc, N * 8, cudaMemcpyHostToDevice, S->stream));
+    NBTE_CK(launch_from_caller(S->Qd.as<double>(), S->io_d.as<double>(), S->perm_d.as<int32_t>(), (int)N,
+                               S->stream));
+  }
+  S->q_dev_version = S->version_q;
+  return NBTE_OK;
+}
+
+// host heat source in internal order (energy balance, diffusion guess)
+const std::vector<double>& host_q(nbte_solver* S) {
+  const int64_t N = S->mesh->m.n_cells;
+  if (S->q_host_version != S->version_q || (int64_t)S->Q.size() != N) {
+    S->Q.assign(N, 0.0);
+    if (S->h_qc)
+      for (int64_t c = 0; c < N; ++c) S->Q[c] = S->h_qc[S->mesh->m.perm[c]];
+    S->q_host_version = S->version_q;
+  }
+  return S->Q;
 }
 
 int ensure_laplacian(nbte_solver* S) {
@@ -1196,7 +1236,8 @@ int init_state(nbte_solver* S, const nbte_solve_opts& o) {
     // the synthetic correction's operator with the wall temperatures as
     // Dirichlet data, solved with the same CG to FP64 accuracy
     std::vector<double> rhs(N);
-    for (int64_t c = 0; c < N; ++c) rhs[c] = S->Q[c] * m.V[c] + S->h_fourier_bc[c];
+    const std::vector<double>& Qh = host_q(S);
+    for (int64_t c = 0; c < N; ++c) rhs[c] = Qh[c] * m.V[c] + S->h_fourier_bc[c];
     NBTE_CK(cudaMemcpyAsync(S->rhs.p, rhs.data(), N * 8, cudaMemcpyHostToDevice, st));
     NBTE_CK(cudaMemsetAsync(S->cg_x.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->cg_err.p, 0, 4, st));
@@ -1442,9 +1483,10 @@ int run_finish(Run& run, nbte_solve_info* info) {
       absall += std::fabs(S->wall_heat_by_face[f]);
       if (type[S->wf_tag_h[f]] == NBTE_THERMALIZING) therm += S->wall_heat_by_face[f];
     }
+    const std::vector<double>& Qh = host_q(S);
     for (int64_t c = 0; c < N; ++c) {
-      qtot += S->Q[c] * m.V[c];
-      qabs += std::fabs(S->Q[c] * m.V[c]);
+      qtot += Qh[c] * m.V[c];
+      qabs += std::fabs(Qh[c] * m.V[c]);
     }
     S->last_energy_imbalance = std::fabs(therm - qtot) / std::max(std::max(qabs, absall), 1e-300);
   }
@@ -2095,16 +2137,19 @@ int nbte_set_boundaries(nbte_solver* S, int n, const nbte_boundary* bcs) {
 
 int nbte_set_heat_source(nbte_solver* S, const double* Qdot) {
   if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
-  const Mesh& m = S->mesh->m;
-  std::vector<double> q(m.n_cells, 0.0);
+  const int64_t N = S->mesh->m.n_cells;
   if (Qdot) {
-    for (int64_t c = 0; c < m.n_cells; ++c) {
-      const double x = Qdot[m.perm[c]];
-      if (!std::isfinite(x)) return fail(NBTE_ERR_ARG, "non-finite heat source");
-      q[c] = x;
+    for (int64_t k = 0; k < N; ++k)
+      if (!std::isfinite(Qdot[k])) return fail(NBTE_ERR_ARG, "non-finite heat source");
+    // the caller's order, in pinned memory: reordered on the device
+    if (!S->h_qc && cudaMallocHost(&S->h_qc, (size_t)std::max<int64_t>(N, 1) * 8) != cudaSuccess) {
+      S->h_qc = nullptr;
+      return fail(NBTE_ERR_OOM, "pinned host allocation failed");
     }
+    std::memcpy(S->h_qc, Qdot, (size_t)N * 8);
+  } else if (S->h_qc) {
+    std::memset(S->h_qc, 0, (size_t)N * 8);
   }
-  S->Q.swap(q);
   S->version_q++;
   S->have_results = false;
   return NBTE_OK;
@@ -2271,12 +2316,15 @@ int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
   double* tmp = host_stage(S, (size_t)N);
   if (!tmp) return fail(NBTE_ERR_OOM, "pinned host allocation failed");
   const DBuf& src = kind == 0 ? S->T : (kind == 1 ? S->accE : S->Tkin);
-  NBTE_CK(cudaMemcpyAsync(tmp, src.p, N * 8, cudaMemcpyDeviceToHost, S->stream));
+  nbte_solver* Sm = const_cast<nbte_solver*>(S);   // device staging only
+  int rc = ensure_perm(Sm);
+  if (rc) return rc;
+  NBTE_CK(Sm->io_d.alloc(std::max<size_t>(Sm->io_d.bytes, (size_t)N * 8 * m.dim)));
+  NBTE_CK(launch_to_caller(Sm->io_d.as<double>(), src.as<double>(), Sm->perm_d.as<int32_t>(), (int)N, 1,
+                           kind == 1 ? 1.0 / S->Ctot : 1.0, S->T_ref, S->stream));
+  NBTE_CK(cudaMemcpyAsync(tmp, Sm->io_d.p, N * 8, cudaMemcpyDeviceToHost, S->stream));
   NBTE_CK(cudaStreamSynchronize(S->stream));
-  for (int64_t c = 0; c < N; ++c) {
-    const double t = kind == 1 ? tmp[c] / S->Ctot : tmp[c];
-    out[m.perm[c]] = t + S->T_ref;
-  }
+  std::memcpy(out, tmp, (size_t)N * 8);
   return NBTE_OK;
 }
 
@@ -2289,10 +2337,15 @@ int nbte_get_heat_flux(const nbte_solver* S, double* out) {
   const int64_t N = m.n_cells;
   double* tmp = host_stage(S, (size_t)N * m.dim);
   if (!tmp) return fail(NBTE_ERR_OOM, "pinned host allocation failed");
-  NBTE_CK(cudaMemcpyAsync(tmp, S->accQ.p, (size_t)N * m.dim * 8, cudaMemcpyDeviceToHost, S->stream));
+  nbte_solver* Sm = const_cast<nbte_solver*>(S);   // device staging only
+  int rc = ensure_perm(Sm);
+  if (rc) return rc;
+  NBTE_CK(Sm->io_d.alloc(std::max<size_t>(Sm->io_d.bytes, (size_t)N * 8 * m.dim)));
+  NBTE_CK(launch_to_caller(Sm->io_d.as<double>(), S->accQ.as<double>(), Sm->perm_d.as<int32_t>(), (int)N, m.dim,
+                           1.0, 0.0, S->stream));
+  NBTE_CK(cudaMemcpyAsync(tmp, Sm->io_d.p, (size_t)N * m.dim * 8, cudaMemcpyDeviceToHost, S->stream));
   NBTE_CK(cudaStreamSynchronize(S->stream));
-  for (int64_t c = 0; c < N; ++c)
-    for (int d = 0; d < m.dim; ++d) out[m.perm[c] * m.dim + d] = tmp[c * m.dim + d];
+  std::memcpy(out, tmp, (size_t)N * m.dim * 8);
   return NBTE_OK;
 }
 

@@ -245,6 +245,32 @@ void launch_fill_srcTQ(R* srcTQ, const double* T, const double* Q, int N, cudaSt
   fill_srcTQ_kernel<R><<<(N + 255) / 256, 256, 0, st>>>(srcTQ, T, Q, N);
 }
 
+// Between the caller's cell order and the library's: perm[c] is the caller
+// index of internal cell c.
+__global__ void from_caller_kernel(double* dst, const double* src, const int32_t* perm, int N) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < N) dst[c] = __ldg(src + __ldg(perm + c));
+}
+__global__ void to_caller_kernel(double* dst, const double* src, const int32_t* perm, int N, int dim,
+                                 double scale, double offset) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * dim) return;
+  const int c = (int)(t / dim), d = (int)(t - (int64_t)c * dim);
+  dst[(int64_t)__ldg(perm + c) * dim + d] = src[t] * scale + offset;
+}
+cudaError_t launch_from_caller(double* dst, const double* src, const int32_t* perm, int N, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  from_caller_kernel<<<(N + 255) / 256, 256, 0, st>>>(dst, src, perm, N);
+  return cudaGetLastError();
+}
+cudaError_t launch_to_caller(double* dst, const double* src, const int32_t* perm, int N, int dim, double scale,
+                             double offset, cudaStream_t st) {
+  const int64_t n = (int64_t)N * dim;
+  if (n <= 0) return cudaSuccess;
+  to_caller_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, src, perm, N, dim, scale, offset);
+  return cudaGetLastError();
+}
+
 // ============================================================================ CG
 // FP64 arithmetic is scarce on this part (a warp-wide FP64 instruction holds
 // its scheduler's FP64 pipe for tens of cycles), so the kernel below spends

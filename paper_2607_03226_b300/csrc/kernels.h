@@ -257,5 +257,10 @@ void launch_wall_heat(const WallHeatArgs<R>& a, cudaStream_t st);
 
 template <typename R>
 void launch_fill_srcTQ(R* srcTQ, const double* T, const double* Q, int N, cudaStream_t st);
+// dst[c] = src[perm[c]] (caller order -> internal order)
+cudaError_t launch_from_caller(double* dst, const double* src, const int32_t* perm, int N, cudaStream_t st);
+// dst[perm[c]*dim + d] = src[c*dim + d] * scale + offset (internal -> caller order)
+cudaError_t launch_to_caller(double* dst, const double* src, const int32_t* perm, int N, int dim, double scale,
+                             double offset, cudaStream_t st);
 
 }  // namespace nbte
