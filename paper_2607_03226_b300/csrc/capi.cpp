@@ -1299,7 +1299,8 @@ int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
 
 // Autotuner: with band_group and cta_threads left at 0, time every feasible
 // (band group, chunk length) layout once per (mesh plan, band table,
-// precision) and keep the fastest.
+// precision) -- chunk lengths 64, 128, 256, 512, then a few multiples of 32
+// around the best -- and keep the fastest.
 int autotune(nbte_solver* S, const nbte_solve_opts& o) {
   if (o.band_group != 0 || o.cta_threads != 0 || o.ring != 0) return NBTE_OK;
   Tuned& tu = S->tuned[o.precision];
@@ -1315,25 +1316,39 @@ int autotune(nbte_solver* S, const nbte_solve_opts& o) {
   }
   double best = 1e300;
   int bG = 0, bcap = 0;
+  auto try_layout = [&](int G, int cap) -> int {
+    nbte_solve_opts c = o;
+    c.band_group = G;
+    c.cta_threads = cap + 32;
+    c.warm = 0;
+    c.init = 0;
+    if (ensure_layout(S, c) != NBTE_OK) return NBTE_OK;   // does not fit this mesh
+    int rc = ensure_q(S);
+    if (rc) return rc;
+    float ms = 0.f;
+    rc = o.precision ? time_sweep<float>(S, c, &ms) : time_sweep<double>(S, c, &ms);
+    if (rc) return rc;
+    if (ms < best) {
+      best = ms;
+      bG = G;
+      bcap = cap;
+    }
+    return NBTE_OK;
+  };
+  // coarse: powers of two; then chunk lengths around the best, in steps of a warp
   for (int G : Gs)
     for (int cap : {64, 128, 256, 512}) {
-      nbte_solve_opts c = o;
-      c.band_group = G;
-      c.cta_threads = cap + 32;
-      c.warm = 0;
-      c.init = 0;
-      if (ensure_layout(S, c) != NBTE_OK) continue;   // does not fit this mesh
-      int rc = ensure_q(S);
+      const int rc = try_layout(G, cap);
       if (rc) return rc;
-      float ms = 0.f;
-      rc = o.precision ? time_sweep<float>(S, c, &ms) : time_sweep<double>(S, c, &ms);
-      if (rc) return rc;
-      if (ms < best) {
-        best = ms;
-        bG = G;
-        bcap = cap;
-      }
     }
+  if (bG != 0) {
+    const int G = bG, c0 = bcap;
+    for (int cap : {c0 - 32, c0 + 32, c0 + 64, c0 + c0 / 2}) {
+      if (cap < 64 || cap > 512 || cap % 32 != 0 || cap == c0 || cap == 2 * c0) continue;
+      const int rc = try_layout(G, cap);
+      if (rc) return rc;
+    }
+  }
   if (bG == 0) return fail(NBTE_ERR_ARG, "no sweep layout fits shared memory for this mesh");
   tu.valid = true;
   tu.G = bG;

@@ -193,7 +193,8 @@ def test_finfet2d_full_size_steps(nbte_mod, precision, tol):
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-6)])
 def test_finfet2d_full_size_every_layout(nbte_mod, precision, tol):
-    """Every sweep layout the autotuner may pick (band group x chunk length)
+    """Sweep layouts the autotuner may pick (band group x chunk length: the
+    powers of two and the multiples of 32 it refines around the best)
     on the full-size 2D fin: T after one and two sequential iterations on the
     stored oracle sample cells.  Layouts that do not fit shared memory are
     refused with NBTE_ERR_ARG and skipped."""
@@ -204,7 +205,7 @@ def test_finfet2d_full_size_every_layout(nbte_mod, precision, tol):
     groups = (1, 2, 4) if precision == "fp64" else (1, 2, 4, 8)
     bad, ran = [], 0
     for G in groups:
-        for cap in (64, 128, 256, 512):
+        for cap in (64, 128, 160, 192, 256, 512):
             for n in (1, 2):
                 try:
                     s.solve(scheme="sequential", precision=precision, n_iter=n, band_group=G,
