@@ -612,8 +612,13 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   auto budget = [&](int t) { return (int64_t)(228 * 1024) / t - 1024; };
   int per_sm = std::max(1, (S->D * ng + nsm - 1) / nsm);
   while (per_sm > 1 && total(3) > budget(per_sm)) --per_sm;
+  // a global-memory value ring is served by L1, which shares the SM's 256 KB
+  // with shared memory: past about 96 KB of copy stages per CTA the ring's
+  // loads fall through to L2 (1.14M-tet FinFET, band group 8: 57 ms per sweep
+  // at 96 KB, 70 ms at 225 KB)
+  const int64_t smem_cap = gr ? std::min<int64_t>(kSweepSmemMax, 96 * 1024) : kSweepSmemMax;
   int ns = 8;
-  while (ns > 2 && total(ns) > std::min<int64_t>(budget(per_sm), kSweepSmemMax)) --ns;
+  while (ns > 2 && total(ns) > std::min<int64_t>(budget(per_sm), smem_cap)) --ns;
   const int Bp = ng * G;
   const int threads = cap + 32;
   if (estimate) {
