@@ -44,28 +44,32 @@ __device__ __forceinline__ double exported(const WallArgs<R>& a, int64_t x, int 
   return (double)a.exp[io_index(x, b, a.n_exp, a.G, a.Gpad)] + a.CoW[b] * a.Delta[a.exp_cell[x]];
 }
 
-// diffuse re-emission: one value per (diffuse face, band)
+// diffuse re-emission: one value per (diffuse face, band).  One block per
+// face; thread (band, slice) sums every kDifSlices-th outgoing direction of
+// the face, and the slice sums are combined in a fixed order (so results do
+// not depend on scheduling).  FP64 sums, as the wall balance needs.
+constexpr int kDifSlices = 8;
+
+constexpr int kDifBands = 64;   // bands per block (blockIdx.y covers the rest)
+
 template <typename R>
 __global__ void diffuse_kernel(const WallArgs<R> a) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= a.n_dbf * a.Bp) return;
-  const int64_t f = t / a.Bp;
-  const int b = (int)(t - f * a.Bp);
-  // four independent partial sums so that four directions' loads are in
-  // flight at once; combined in a fixed order
+  __shared__ double dif_red[kDifSlices][kDifBands];
+  const int64_t f = blockIdx.x;
+  const int b = blockIdx.y * kDifBands + threadIdx.x;
+  const int j = threadIdx.y;
   const int64_t k0 = a.dif_ptr[f], k1 = a.dif_ptr[f + 1];
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int64_t k = k0;
-  for (; k + 3 < k1; k += 4) {
-    const int64_t i0 = a.dif_src[k], i1 = a.dif_src[k + 1], i2 = a.dif_src[k + 2], i3 = a.dif_src[k + 3];
-    const double w0 = a.dif_wt[k], w1 = a.dif_wt[k + 1], w2 = a.dif_wt[k + 2], w3 = a.dif_wt[k + 3];
-    s0 += w0 * exported(a, i0, b);
-    s1 += w1 * exported(a, i1, b);
-    s2 += w2 * exported(a, i2, b);
-    s3 += w3 * exported(a, i3, b);
+  double s = 0.0;
+  if (b < a.Bp)
+    for (int64_t k = k0 + j; k < k1; k += kDifSlices) s += a.dif_wt[k] * exported(a, a.dif_src[k], b);
+  dif_red[j][threadIdx.x] = s;
+  __syncthreads();
+  if (j == 0 && b < a.Bp) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kDifSlices; ++q) t += dif_red[q][threadIdx.x];
+    a.dsum[f * a.Bp + b] = t;
   }
-  for (; k < k1; ++k) s0 += a.dif_wt[k] * exported(a, a.dif_src[k], b);
-  a.dsum[t] = (s0 + s1) + (s2 + s3);
 }
 
 template <typename R>
@@ -100,8 +104,9 @@ __global__ void imports_kernel(const WallArgs<R> a) {
 template <typename R>
 void launch_walls(const WallArgs<R>& a, cudaStream_t st) {
   if (a.n_dbf > 0) {
-    const int64_t n = a.n_dbf * a.Bp;
-    diffuse_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+    const int bx = a.Bp < kDifBands ? a.Bp : kDifBands;
+    diffuse_kernel<R><<<dim3((unsigned)a.n_dbf, (unsigned)((a.Bp + kDifBands - 1) / kDifBands)),
+                        dim3(bx, kDifSlices), 0, st>>>(a);
   }
   if (a.n_imp > 0) {
     const int64_t n = a.n_imp * a.Bp;
