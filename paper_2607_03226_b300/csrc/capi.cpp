@@ -1829,8 +1829,10 @@ void shrink(nbte_solver* S) {
                  &S->delta, &S->dsum, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s, &S->cg_w, &S->cg_x, &S->cg_xw,
                  &S->cg_rw, &S->cg_rcx, &S->cg_scx, &S->cg_Ainv, &S->cg_Ainv64, &S->L_ecol, &S->L_eval,
                  &S->L_diag, &S->L_dinv, &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell,
-                 &S->cg_blk_agg, &S->cg_slots};
+                 &S->cg_blk_agg, &S->cg_slots, &S->dinv, &S->o2_e, &S->o2_src, &S->rc_nb, &S->rc_twin,
+                 &S->rc_AnV, &S->rc_a};
   for (DBuf* b : big) b->release();
+  S->rc_prec = -1;
   S->layout_key.clear();
   S->rec_key.clear();
   S->chunk_key.clear();

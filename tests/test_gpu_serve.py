@@ -61,3 +61,29 @@ def test_served_results_equal_alone(nbte_mod, alone, budget):
     srv.close()
     for s in ss:
         s.close()
+
+
+def test_served_second_order_equals_alone(nbte_mod):
+    """Second-order solves through the server (its options carry order=2)
+    converge to the same fields as alone."""
+    probs = _problems()[:3]
+    opts = dict(OPTS, order=2)
+    ref = []
+    for p in probs:
+        s = nbte_mod.Solver(p)
+        assert s.solve(**opts)["status"] == 0
+        ref.append(s.temperature(0))
+        s.close()
+    srv = nbte_mod.Server(max_active=8, n_planners=2, **opts)
+    ss = [nbte_mod.Solver(p) for p in probs]
+    ids = [srv.submit(s) for s in ss]
+    srv.drain(timeout_s=600)
+    for p, s, rid, T in zip(probs, ss, ids, ref):
+        info, _, _ = srv.poll(rid)
+        assert info["status"] == 0
+        err = rel_T(s.temperature(0), T, p.T_ref)
+        print(f"{p.name}: served second order, {info['iterations']} iterations, difference {err:.2e}")
+        assert err < 1e-9
+    srv.close()
+    for s in ss:
+        s.close()
