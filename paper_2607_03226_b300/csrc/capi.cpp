@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 #include <deque>
+#include <cstdlib>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -127,7 +128,8 @@ struct nbte_solver {
   bool bcs_set = false;
   // heat source: caller order in pinned host memory (what the caller set),
   // internal order on the host on demand (Q) and on the device (Qd)
-  double* h_qc = nullptr;
+  double* h_qc = nullptr;   // pinned, or ordinary memory where pinning is unavailable
+  bool h_qc_pinned = false;
   int64_t q_dev_version = -1, q_host_version = -1;
   std::vector<double> Q;   // internal order, valid for q_host_version
   int64_t version_plan = 0, version_bands = 0, version_q = 0;
@@ -195,7 +197,8 @@ struct nbte_solver {
 
   ~nbte_solver() {
     if (graph) cudaGraphExecDestroy(graph);
-    if (h_qc) cudaFreeHost(h_qc);
+    if (h_qc && h_qc_pinned) cudaFreeHost(h_qc);
+    if (h_qc && !h_qc_pinned) std::free(h_qc);
     if (h_res) cudaFreeHost(h_res);
     if (h_misc) cudaFreeHost(h_misc);
     if (h_stage) cudaFreeHost(h_stage);
@@ -2161,12 +2164,24 @@ int nbte_set_heat_source(nbte_solver* S, const double* Qdot) {
   if (!S) return fail(NBTE_ERR_ARG, "solver is NULL");
   const int64_t N = S->mesh->m.n_cells;
   if (Qdot) {
-    for (int64_t k = 0; k < N; ++k)
-      if (!std::isfinite(Qdot[k])) return fail(NBTE_ERR_ARG, "non-finite heat source");
-    // the caller's order, in pinned memory: reordered on the device
-    if (!S->h_qc && cudaMallocHost(&S->h_qc, (size_t)std::max<int64_t>(N, 1) * 8) != cudaSuccess) {
-      S->h_qc = nullptr;
-      return fail(NBTE_ERR_OOM, "pinned host allocation failed");
+    // non-finite <=> all exponent bits set; an integer OR-reduction that
+    // vectorises, then one copy into pinned memory in the caller's order
+    // (reordered on the device).  A rejected array leaves the old source.
+    uint64_t bad = 0;
+    for (int64_t k = 0; k < N; ++k) {
+      uint64_t u;
+      std::memcpy(&u, Qdot + k, 8);
+      bad |= (uint64_t)((u & 0x7ff0000000000000ull) == 0x7ff0000000000000ull);
+    }
+    if (bad) return fail(NBTE_ERR_ARG, "non-finite heat source");
+    if (!S->h_qc) {
+      const size_t bytes = (size_t)std::max<int64_t>(N, 1) * 8;
+      S->h_qc_pinned = cudaMallocHost(&S->h_qc, bytes) == cudaSuccess;
+      if (!S->h_qc_pinned) {   // no device yet: plain memory, copied synchronously later
+        cudaGetLastError();
+        S->h_qc = static_cast<double*>(std::malloc(bytes));
+        if (!S->h_qc) return fail(NBTE_ERR_OOM, "host allocation failed");
+      }
     }
     std::memcpy(S->h_qc, Qdot, (size_t)N * 8);
   } else if (S->h_qc) {

@@ -105,9 +105,12 @@ def test_setup_argument_errors(lib):
     assert code(nbte.nbte_set_boundaries, s, [Boundary(t, 1) for t in (1, 2, 3, 4)]) == nbte.NBTE_ERR_ARG
     assert code(nbte.nbte_set_boundaries, s, [Boundary(1, 0, 300.0), Boundary(2, 3, 0, 1.5),
                                               Boundary(3, 1), Boundary(4, 1)]) == nbte.NBTE_ERR_ARG
-    q = np.zeros(p.n_cells)
-    q[2] = np.inf
-    assert code(nbte.nbte_set_heat_source, s, q) == nbte.NBTE_ERR_ARG
+    for bad in (np.inf, -np.inf, np.nan):
+        for at in (0, 2, p.n_cells - 1):
+            q = np.zeros(p.n_cells)
+            q[at] = bad
+            assert code(nbte.nbte_set_heat_source, s, q) == nbte.NBTE_ERR_ARG
+    nbte.nbte_set_heat_source(s, np.full(p.n_cells, 1e300))   # large but finite: accepted
     # solve before the set-up is complete
     st, _ = None, None
     with pytest.raises(nbte.NbteError) as e:
