@@ -55,3 +55,42 @@ def test_full_size_first_iteration_tasks(nbte_mod, name, precision, tol):
         err = np.abs(e - np.array(t["e"])).max() / t["max_abs"]
         print(f"{name} {precision} task ({t['direction']}, {t['band']}): rel err {err:.2e}")
         assert err < tol
+
+
+def _stream_problems():
+    """The smallest request of each mesh kind in the benchmark's 24-request
+    stream (same seed): a 2D triangle fin, a 3D hex box and a 3D tet fin with
+    random wall mixes and a heat box."""
+    reqs = W.stream.requests(24, 1.0)
+    out = []
+    for kind in ("tri2d", "hex3d", "tet3d"):
+        r = min((r for r in reqs if r.kind == kind), key=lambda r: r.n_cells_target)
+        out.append(W.stream.build(r))
+    return out
+
+
+@pytest.mark.parametrize("k", range(3))
+def test_stream_requests_first_iteration_tasks(nbte_mod, k):
+    """Stream requests at their full size: the first sequential iteration's
+    distribution of three (direction, band) tasks against the oracle's
+    sparse solve of the same tasks (walls at equilibrium with T_ref), every
+    cell, relative to max|e'| of the task.  FP64 1e-11 (rounding order).
+    FP32 4e-6: the 1e-6 target is for the temperature, an average over all
+    tasks; one task's distribution carries the FP32 rounding of its own level
+    chain, up to about a thousand dependent updates of relative error 2^-24
+    each (a random walk of ~2e-6 at that length), with a factor 2 margin."""
+    from oracle import OracleSolver
+    p = _stream_problems()[k]
+    o = OracleSolver(p)
+    T0 = np.zeros(o.N)
+    eb0 = np.zeros((o.bcells.size, o.D))
+    tasks = [(0, 0), (p.n_dirs // 2, p.n_bands // 2), (p.n_dirs - 1, p.n_bands - 1)]
+    ref = {(i, l): o.solve_task(T0, o.incoming_band(eb0, l), i, l) for (i, l) in tasks}
+    s = nbte_mod.Solver(p)
+    for precision, tol in (("fp64", 1e-11), ("fp32", 4e-6)):
+        s.solve(scheme="sequential", precision=precision, n_iter=1, skip_outputs=True)
+        for (i, l), e in ref.items():
+            err = np.abs(s.distribution(i, l) - e).max() / np.abs(e).max()
+            print(f"{p.name} ({p.n_cells} cells) {precision} task ({i}, {l}): rel err {err:.2e}")
+            assert err < tol
+    s.close()
