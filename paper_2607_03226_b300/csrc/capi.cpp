@@ -146,7 +146,7 @@ struct nbte_solver {
   // ---- band layout (depends on bands, precision and tuning)
   std::string layout_key, rec_key, chunk_key;
   int prec = 0, G = 1, Gpad = 4, n_groups = 1, Bp = 1, n_items = 0, threads = 160, n_stages = 4;
-  int stage_bytes = 0, off_ring = 0, off_stage = 0, off_tq = 0, off_imp = 0, off_den = 0, off_src2 = 0;
+  int stage_bytes = 0, off_ring = 0, off_stage = 0, off_imp = 0, off_den = 0, off_src2 = 0;
   size_t smem = 0;
   int order = 1;                              // upwind order of the current layout
   // second-order upwind: previous distribution [n_items*N*G], per-position
@@ -551,7 +551,9 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     const int rc0 = chunk_extents(S, cap, &cimp, &csub);
     if (rc0) return rc0;
   }
-  auto stage_of = [&](int Gv, int& off_tq, int& off_imp, int& off_den) {
+  // a stage: the chunk block (header, records, (T', Qdot) pairs), the
+  // chunk's import rows, FP64 denominators, second-order sources
+  auto stage_of = [&](int Gv, int& off_imp, int& off_den) {
     const int gpad = padded_group(Gv, sz);
     const int rec = (int)chunk_header_bytes(csub) + cap * RL.size;
     const int tq = ((cap + 2) * 2 * sz + 15) / 16 * 16;
@@ -559,7 +561,6 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     const int den = prec ? 0 : ((cap + 2) * Gv * 8 + 15) / 16 * 16;
     // second order: the chunk's reconstruction sources (superset of at most cap + 3 positions)
     const int src2 = order2 ? ((cap + 4) * Gv * sz + 15) / 16 * 16 : 0;
-    off_tq = rec;
     off_imp = rec + tq;
     off_den = rec + tq + imp;
     off_src2 = rec + tq + imp + den;
@@ -570,8 +571,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   auto ring_of = [&](int Gv) { return (int)(((size_t)(S->max_slots + 1) * Gv * sz + 15) / 16 * 16); };
   const int head = 32 * 8;   // up to 8 stages: full + empty barriers and chunk headers
   auto smem_ring = [&](int Gv) {
-    int a, b, c;
-    return (int64_t)head + ring_of(Gv) + 2 * (int64_t)stage_of(Gv, a, b, c) <= kSweepSmemMax;
+    int a, b;
+    return (int64_t)head + ring_of(Gv) + 2 * (int64_t)stage_of(Gv, a, b) <= kSweepSmemMax;
   };
   auto ring_smem_bytes = [&](int Gv) { return smem_ring(Gv) ? ring_of(Gv) : 0; };
   const int maxG = prec ? 8 : 4;
@@ -596,16 +597,16 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
                                   " live cells in one direction)");
   const bool gr = o.ring == 2 || !smem_ring(G);
   {
-    int a, b, c;
-    if ((int64_t)head + 2 * (int64_t)stage_of(G, a, b, c) > kSweepSmemMax)
+    int a, b;
+    if ((int64_t)head + 2 * (int64_t)stage_of(G, a, b) > kSweepSmemMax)
       return fail(NBTE_ERR_ARG, "cta_threads too large for shared memory with this band group");
   }
   // stages: 2..8.  The sweep of one item is a long dependent chain of
   // levels, so co-resident CTAs are what hides its latency: aim for every
   // work item resident at once, else for as many CTAs per SM as still get
   // three stages each, then give each CTA as many stages as that allows
-  int off_tq = 0, off_imp = 0, off_den = 0;
-  const int stage = stage_of(G, off_tq, off_imp, off_den);
+  int off_imp = 0, off_den = 0;
+  const int stage = stage_of(G, off_imp, off_den);
   const int off_src2_sel = off_src2;
   const int ng = (S->B + G - 1) / G;
   int nsm = 148;
@@ -658,7 +659,6 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   S->threads = threads;
   S->n_stages = ns;
   S->stage_bytes = stage;
-  S->off_tq = off_tq;
   S->off_imp = off_imp;
   S->off_den = off_den;
   S->off_src2 = off_src2_sel;
