@@ -214,6 +214,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     int64_t cur_off = fetch_off(0), nxt_off = fetch_off(32);
     int issued = 0;
     bool ok = true;
+    // stage of chunk c and the parity of its round, kept incrementally (the
+    // stage count is not a compile-time constant, so c % NS would divide)
+    int sp = 0;
+    unsigned php = 0;
     for (int c = 0; c < nch; ++c) {
       if (c > 0 && (c & 31) == 0) {
         cur = nxt;
@@ -228,8 +232,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       m.imp = __shfl_sync(0xffffffffu, cur.z, c & 31);
       m.nimp_end = __shfl_sync(0xffffffffu, cur.w, c & 31);
       if (lane == 0) {
-        const int s = c % NS;
-        if (c >= NS && !mbar_wait(empty + s, ((c / NS) - 1) & 1)) {
+        const int s = sp;
+        if (c >= NS && !mbar_wait(empty + s, php ^ 1u)) {
           atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
           ok = false;
         }
@@ -237,7 +241,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       if (!ok) break;
       if (lane == 0) {
-        const int s = c % NS;
+        const int s = sp;
         meta[s] = m;
         unsigned char* st = stages + (size_t)s * a.stage_bytes;
         // the chunk's header, records and (T', Qdot) pairs: one contiguous
@@ -275,6 +279,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
                     full + s);
       }
       ++issued;
+      if (++sp == NS) {
+        sp = 0;
+        php ^= 1u;
+      }
     }
     // every copy issued must land before the CTA leaves
     if (lane == 0)
@@ -300,9 +308,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
   R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * GP;
   consumer_barrier(ncons);
 
+  int sc = 0;          // stage of chunk c, and the parity of its round
+  unsigned phc = 0;
   for (int c = 0; c < nch; ++c) {
-    const int s = c % NS;
-    if (!mbar_wait(full + s, (c / NS) & 1)) {
+    const int s = sc;
+    if (!mbar_wait(full + s, phc)) {
       atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
       break;
     }
@@ -395,6 +405,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     __syncwarp();
     if ((ct & 31) == 0) mbar_arrive(empty + s);
     if (chunk_level_end(m.nimp_end)) consumer_barrier(ncons);
+    if (++sc == NS) {
+      sc = 0;
+      phc ^= 1u;
+    }
   }
 }
 
