@@ -613,11 +613,10 @@ __global__ void gather_tq_kernel(R* data, const uint32_t* tq_dst, const int32_t*
 // zero weight): no branches between the loads.
 template <typename R, int G, int NF>
 __global__ void __launch_bounds__(256, NF > 4 ? 3 : 1) src2_kernel(const Src2Args<R> a) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)a.D * a.N) return;
-  const int i = (int)(t / a.N);
-  const int p = (int)(t - (int64_t)i * a.N);
-  const int c = __ldg(a.pos_cell + t);
+  const int i = blockIdx.y;   // direction (a 2D grid: no division by N)
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.N) return;
+  const int c = __ldg(a.pos_cell + (int64_t)i * a.N + p);
   const R sx = (R)a.dir_s[i * 3], sy = (R)a.dir_s[i * 3 + 1], sz = (R)a.dir_s[i * 3 + 2];
   // hexahedra (36 weights and neighbours) re-read the tables from L1 per band
   // group instead of holding them in registers
@@ -684,7 +683,7 @@ __global__ void __launch_bounds__(256, NF > 4 ? 3 : 1) src2_kernel(const Src2Arg
 
 template <typename R, int G>
 static cudaError_t launch_src2_g(const Src2Args<R>& a, cudaStream_t st) {
-  const unsigned grid = (unsigned)(((int64_t)a.D * a.N + 255) / 256);
+  const dim3 grid((unsigned)((a.N + 255) / 256), (unsigned)a.D);
   switch (a.nfc) {
     case 3: src2_kernel<R, G, 3><<<grid, 256, 0, st>>>(a); break;
     case 4: src2_kernel<R, G, 4><<<grid, 256, 0, st>>>(a); break;
@@ -697,7 +696,7 @@ static cudaError_t launch_src2_g(const Src2Args<R>& a, cudaStream_t st) {
 template <typename R>
 cudaError_t launch_src2(const Src2Args<R>& a, cudaStream_t st) {
   if ((int64_t)a.n_items * a.N == 0) return cudaSuccess;
-  if (a.Bp != a.n_groups * a.G) return cudaErrorInvalidValue;
+  if (a.Bp != a.n_groups * a.G || a.D > 65535) return cudaErrorInvalidValue;
   switch (a.G) {
     case 1: return launch_src2_g<R, 1>(a, st);
     case 2: return launch_src2_g<R, 2>(a, st);
