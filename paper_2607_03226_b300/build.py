@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libnanobte.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["mesh.cpp", "plan.cpp", "coarse.cpp", "capi.cpp", "kernels.cu", "sweep.cu", "noalloc.cu"]
+SOURCES = ["mesh.cpp", "plan.cpp", "coarse.cpp", "capi.cpp", "kernels.cu", "sweep.cu", "sweep_data.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
