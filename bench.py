@@ -154,7 +154,7 @@ def _sweep_traffic(G, threads):
             k, _, v = line.partition(":")
             fields[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for f in ("sweep.cu", "vecio.cuh", "layout.h", "kernels.h"):
+    for f in ("sweep.cu", "vecio.cuh", "layout.h", "sweep_args.h"):
         with open(os.path.join(ROOT, "paper_2607_03226_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if fields.get("sweep_source_digest") != h.hexdigest()[:16]:

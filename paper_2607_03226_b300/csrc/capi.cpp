@@ -360,8 +360,8 @@ int ensure_records(nbte_solver* S) {
 // level count and level ends), its records, then room for its (T', Qdot)
 // pairs, so that one bulk copy brings all three.
 // chunk_doff holds each block's byte offset; tq_dst, per position
-// (direction-major), the index of its pair in units of pairs.  Packed on the
-// device from the position-ordered records.
+// (direction-major), its cell and the index of its pair in units of pairs.
+// Packed on the device from the position-ordered records.
 template <typename R>
 int ensure_blocks(nbte_solver* S, int cap) {
   const std::string key = S->rec_key + "/" + S->chunk_key;
@@ -387,9 +387,9 @@ int ensure_blocks(nbte_solver* S, int cap) {
   NBTE_CK(upload(S->chunk_sub_ptr, S->h_sub_ptr));
   NBTE_CK(upload(S->chunk_sub_end, S->h_sub_end));
   NBTE_CK(S->rec.alloc(total));
-  NBTE_CK(S->tq_dst.alloc((size_t)P.D * P.N * 4));
+  NBTE_CK(S->tq_dst.alloc((size_t)P.D * P.N * 8));
   NBTE_CK(cudaMemsetAsync(S->rec.p, 0, S->rec.bytes, S->stream));
-  NBTE_CK(launch_pack_blocks(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->rec_pos.as<unsigned char>(),
+  NBTE_CK(launch_pack_blocks(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->rec_pos.as<unsigned char>(),
                              S->chunks.as<Chunk>(), S->chunk_doff.as<int64_t>(), S->chunk_dir.as<int32_t>(),
                              S->chunk_sub_ptr.as<int64_t>(), S->chunk_sub_end.as<int32_t>(), (int64_t)nch, P.N,
                              L.size, pair, S->stream));
@@ -627,8 +627,9 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   const int threads = cap + 32;
   if (estimate) {
     const size_t N = (size_t)S->mesh->m.n_cells, D = (size_t)S->D, Gp = (size_t)padded_group(G, sz);
-    size_t b = D * N * (2 * RL.size + 8 + 2 * sz);                      // records (by position and in chunk
-                                                                         // blocks), cells, pair index, (T', Qdot)
+    size_t b = D * N * (2 * RL.size + 12 + 2 * sz);                     // records (by position and in chunk
+                                                                         // blocks), cells, (cell, pair) index,
+                                                                         // (T', Qdot)
     b += (size_t)D * ng * N * sz;                                        // collision partials
     b += (size_t)ng * (S->n_exp + S->n_imp) * Gp * sz;                   // export / import rows
     if (gr) b += (size_t)D * ng * (((size_t)(S->max_slots + 1) * G + 3) / 4 * 4) * sz;   // global rings
@@ -1173,7 +1174,7 @@ cudaError_t enqueue_pre(nbte_solver* S, cudaStream_t st) {
   launch_walls<R>(wall_args<R>(S), st);
   cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  e = launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
+  e = launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->srcTQ.as<R>(),
                           (int64_t)S->D * S->mesh->m.n_cells, st);
   if (e != cudaSuccess) return e;
   // second order: this sweep's reconstruction sources from the previous sweep's distribution
@@ -1280,7 +1281,7 @@ int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
   if (rc) return rc;
   cudaStream_t st = S->stream;
   launch_walls<R>(wall_args<R>(S), st);
-  NBTE_CK(launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->pos_cell.as<int32_t>(), S->srcTQ.as<R>(),
+  NBTE_CK(launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->srcTQ.as<R>(),
                               (int64_t)S->D * S->mesh->m.n_cells, st));
   NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 0), S->K, S->G, S->n_items, S->threads, S->smem, st));
   cudaEvent_t e0, e1;
@@ -1475,7 +1476,7 @@ int run_finish(Run& run, nbte_solve_info* info) {
     NBTE_CK(cudaMemsetAsync(S->accE.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
     launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
-    NBTE_CK(launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<uint32_t>(), S->pos_cell.as<int32_t>(), S->srcTQ_fin.as<R>(), (int64_t)S->D * N,
+    NBTE_CK(launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->srcTQ_fin.as<R>(), (int64_t)S->D * N,
                                 st));
     NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 1), S->K, S->G, S->n_items, S->threads, S->smem, st));
     WallHeatArgs<R> wh{};

@@ -6,54 +6,9 @@
 #include <cstdint>
 
 #include "layout.h"
+#include "sweep_args.h"
 
 namespace nbte {
-
-// device error word values (written by bounded waits, read by the host)
-enum DevError : int32_t { DEV_OK = 0, DEV_BARRIER_TIMEOUT = 1, DEV_QUEUE_TIMEOUT = 2 };
-
-// shared-memory budget of one sweep CTA (the rest of the SM's 228 KB stays
-// free for a second CTA when the ring is small)
-constexpr int kSweepSmemMax = 227 * 1024;
-
-template <typename R>
-struct SweepArgs {
-  int N, dim;
-  int full;                      // also accumulate E and q (atomics)
-  int Gpad;                      // padded row length of the import/export tables
-  int n_stages;                  // shared-memory stages of the copy pipeline
-  int stage_bytes, off_ring, off_stage, off_imp, off_den, off_src2;   // shared-memory layout
-  const R* dinv;                 // FP64 only: [n_items*N*G] denominators 1/(1/tau + v G), else null
-  const R* src2;                 // second-order upwind: [n_items*N*G] per position, the
-                                 // reconstruction's extra source (sum over faces), else null
-  int64_t n_exp, n_imp;
-  const int32_t* item_dir;       // [n_items]
-  const int32_t* item_grp;       // [n_items]
-  const int64_t* chunk_off;      // [D+1]
-  const Chunk* chunks;
-  const unsigned char* rec;      // per chunk: its packed position records, then its (T', Qdot) pairs
-  const int64_t* chunk_doff;     // [chunks] byte offset of each chunk's block in rec
-  const int64_t* exp_off;        // [D+1]
-  const int64_t* imp_off;
-  const R* imp;                  // band-group-major import rows
-  R* exp;                        // band-group-major export rows
-  const R* band_v;               // [Bp]
-  const R* band_inv_tau;
-  const R* band_cw;              // C / W
-  const R* band_aQ;              // C / (C_tot W)
-  const double* dir_w;           // [D]
-  const double* dir_s;           // [D*3]
-  int item0;                     // first work item of the launch (block b runs item item0 + b)
-  R* e_out;                      // null, or every cell's outgoing values of the item's bands at
-                                 // e_out + i * e_out_dstride + g * e_out_gstride + cell * e_out_cstride
-  int64_t e_out_dstride, e_out_gstride, e_out_cstride;   // (direction i, band group g)
-  R* gring;                      // global-memory value rings, or null for the shared-memory ring
-  int64_t gring_stride;          // elements per CTA's global ring
-  R* part;                       // [n_items*N] collision-moment partials (of e - e0)
-  double* accE;                  // [N]   (full)
-  double* accQ;                  // [N*dim] (full)
-  int32_t* err;                  // device error word
-};
 
 template <typename R>
 cudaError_t launch_sweep(const SweepArgs<R>& a, int K, int G, int n_items, int threads, size_t smem,
@@ -71,16 +26,16 @@ cudaError_t launch_fill_dinv(double* dinv, const double* pos_G, const double* ba
                              int D, int n_groups, int G, int64_t N, cudaStream_t st);
 // Rearrange position-ordered records into chunk blocks (header with the
 // chunk's level ends, records, then room for the chunk's (T', Qdot) pairs)
-// and set tq_dst: one block per chunk.
-cudaError_t launch_pack_blocks(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
+// and set tq_dst (per position: its cell and the index of its (T', Qdot)
+// pair in the blocks, in pairs): one block per chunk.
+cudaError_t launch_pack_blocks(unsigned char* blk, int2* tq_dst, const unsigned char* rec_pos,
                                const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
                                const int64_t* sub_ptr, const int32_t* sub_end, int64_t n_chunks, int64_t N,
                                int rec_size, int pair_bytes, cudaStream_t st);
 // (T', Qdot) of every position's cell into its chunk's block:
-// ((R2*)data)[tq_dst[q]] = ((R2*)srcTQ)[pos_cell[q]], q = i*N + position
+// ((R2*)data)[tq_dst[q].y] = ((R2*)srcTQ)[tq_dst[q].x], q = i*N + position
 template <typename R>
-cudaError_t launch_gather_tq(unsigned char* data, const uint32_t* tq_dst, const int32_t* pos_cell, const R* srcTQ,
-                             int64_t n, cudaStream_t st);
+cudaError_t launch_gather_tq(unsigned char* data, const int2* tq_dst, const R* srcTQ, int64_t n, cudaStream_t st);
 
 // Second-order upwind source of every work item and position, from the
 // previous sweep's distribution e[(i*N + cell)*Bp + band] (direction i, all

@@ -1,0 +1,57 @@
+// Arguments of the transport sweep kernels and the device error codes their
+// bounded waits report (internal; no torch types).
+#pragma once
+
+#include <cstdint>
+
+#include "layout.h"
+
+namespace nbte {
+
+// device error word values (written by bounded waits, read by the host)
+enum DevError : int32_t { DEV_OK = 0, DEV_BARRIER_TIMEOUT = 1, DEV_QUEUE_TIMEOUT = 2 };
+
+// shared-memory budget of one sweep CTA (the rest of the SM's 228 KB stays
+// free for a second CTA when the ring is small)
+constexpr int kSweepSmemMax = 227 * 1024;
+
+template <typename R>
+struct SweepArgs {
+  int N, dim;
+  int full;                      // also accumulate E and q (atomics)
+  int Gpad;                      // padded row length of the import/export tables
+  int n_stages;                  // shared-memory stages of the copy pipeline
+  int stage_bytes, off_ring, off_stage, off_imp, off_den, off_src2;   // shared-memory layout
+  const R* dinv;                 // FP64 only: [n_items*N*G] denominators 1/(1/tau + v G), else null
+  const R* src2;                 // second-order upwind: [n_items*N*G] per position, the
+                                 // reconstruction's extra source (sum over faces), else null
+  int64_t n_exp, n_imp;
+  const int32_t* item_dir;       // [n_items]
+  const int32_t* item_grp;       // [n_items]
+  const int64_t* chunk_off;      // [D+1]
+  const Chunk* chunks;
+  const unsigned char* rec;      // per chunk: its packed position records, then its (T', Qdot) pairs
+  const int64_t* chunk_doff;     // [chunks] byte offset of each chunk's block in rec
+  const int64_t* exp_off;        // [D+1]
+  const int64_t* imp_off;
+  const R* imp;                  // band-group-major import rows
+  R* exp;                        // band-group-major export rows
+  const R* band_v;               // [Bp]
+  const R* band_inv_tau;
+  const R* band_cw;              // C / W
+  const R* band_aQ;              // C / (C_tot W)
+  const double* dir_w;           // [D]
+  const double* dir_s;           // [D*3]
+  int item0;                     // first work item of the launch (block b runs item item0 + b)
+  R* e_out;                      // null, or every cell's outgoing values of the item's bands at
+                                 // e_out + i * e_out_dstride + g * e_out_gstride + cell * e_out_cstride
+  int64_t e_out_dstride, e_out_gstride, e_out_cstride;   // (direction i, band group g)
+  R* gring;                      // global-memory value rings, or null for the shared-memory ring
+  int64_t gring_stride;          // elements per CTA's global ring
+  R* part;                       // [n_items*N] collision-moment partials (of e - e0)
+  double* accE;                  // [N]   (full)
+  double* accQ;                  // [N*dim] (full)
+  int32_t* err;                  // device error word
+};
+
+}  // namespace nbte

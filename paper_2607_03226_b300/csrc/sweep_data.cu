@@ -14,7 +14,7 @@ namespace nbte {
 
 // One block per chunk: its positions' records (multiples of 16 bytes, copied
 // as 16-byte words) to the chunk's block, and each position's pair index
-__global__ void pack_blocks_kernel(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
+__global__ void pack_blocks_kernel(unsigned char* blk, int2* tq_dst, const unsigned char* rec_pos,
                                    const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
                                    const int64_t* sub_ptr, const int32_t* sub_end, int64_t N, int rec_size,
                                    int pair_bytes) {
@@ -31,10 +31,13 @@ __global__ void pack_blocks_kernel(unsigned char* blk, uint32_t* tq_dst, const u
   uint4* dst = reinterpret_cast<uint4*>(blk + roff);
   for (int t = threadIdx.x; t < ch.len * w16; t += blockDim.x) dst[t] = src[t];
   const uint32_t tq0 = (uint32_t)((roff + (int64_t)ch.len * rec_size) / pair_bytes);
-  for (int j = threadIdx.x; j < ch.len; j += blockDim.x) tq_dst[q0 + j] = tq0 + (uint32_t)j;
+  // the cell is the record's first word
+  for (int j = threadIdx.x; j < ch.len; j += blockDim.x)
+    tq_dst[q0 + j] = make_int2(*reinterpret_cast<const int32_t*>(rec_pos + (size_t)(q0 + j) * rec_size),
+                               (int32_t)(tq0 + (uint32_t)j));
 }
 
-cudaError_t launch_pack_blocks(unsigned char* blk, uint32_t* tq_dst, const unsigned char* rec_pos,
+cudaError_t launch_pack_blocks(unsigned char* blk, int2* tq_dst, const unsigned char* rec_pos,
                                const Chunk* chunks, const int64_t* chunk_doff, const int32_t* chunk_dir,
                                const int64_t* sub_ptr, const int32_t* sub_end, int64_t n_chunks, int64_t N,
                                int rec_size, int pair_bytes, cudaStream_t st) {
@@ -68,12 +71,12 @@ cudaError_t launch_fill_dinv(double* dinv, const double* pos_G, const double* ba
 // (T', Qdot) of every position's cell, in each direction's level order, so
 // the sweep's producer can bulk-copy them with the position records
 template <typename R>
-__global__ void gather_tq_kernel(R* data, const uint32_t* tq_dst, const int32_t* pos_cell, const R* srcTQ,
-                                 int64_t n) {
+__global__ void gather_tq_kernel(R* data, const int2* tq_dst, const R* srcTQ, int64_t n) {
   using R2 = typename Vec2<R>::T;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  reinterpret_cast<R2*>(data)[__ldcs(tq_dst + q)] = __ldg(reinterpret_cast<const R2*>(srcTQ) + __ldcs(pos_cell + q));
+  const int2 cd = __ldcs(tq_dst + q);   // (cell, pair index)
+  reinterpret_cast<R2*>(data)[(uint32_t)cd.y] = __ldg(reinterpret_cast<const R2*>(srcTQ) + cd.x);
 }
 
 // Second-order upwind sources.  One thread per (direction, position): it
@@ -184,19 +187,15 @@ cudaError_t launch_src2(const Src2Args<R>& a, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_gather_tq(unsigned char* data, const uint32_t* tq_dst, const int32_t* pos_cell, const R* srcTQ,
-                             int64_t n, cudaStream_t st) {
+cudaError_t launch_gather_tq(unsigned char* data, const int2* tq_dst, const R* srcTQ, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  gather_tq_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<R*>(data), tq_dst, pos_cell,
-                                                                    srcTQ, n);
+  gather_tq_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<R*>(data), tq_dst, srcTQ, n);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_src2<float>(const Src2Args<float>&, cudaStream_t);
 template cudaError_t launch_src2<double>(const Src2Args<double>&, cudaStream_t);
-template cudaError_t launch_gather_tq<float>(unsigned char*, const uint32_t*, const int32_t*, const float*, int64_t,
-                                             cudaStream_t);
-template cudaError_t launch_gather_tq<double>(unsigned char*, const uint32_t*, const int32_t*, const double*, int64_t,
-                                              cudaStream_t);
+template cudaError_t launch_gather_tq<float>(unsigned char*, const int2*, const float*, int64_t, cudaStream_t);
+template cudaError_t launch_gather_tq<double>(unsigned char*, const int2*, const double*, int64_t, cudaStream_t);
 
 }  // namespace nbte
