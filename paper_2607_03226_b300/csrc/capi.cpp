@@ -1088,6 +1088,7 @@ UpdateArgs<R> update_args(nbte_solver* S, int mode) {
   a.Q = S->Qd.as<double>();
   a.V = S->Vd.as<double>();
   a.T = S->T.as<double>();
+  a.Tprev = S->Tprev.as<double>();
   a.Tkin = S->Tkin.as<double>();
   a.Delta = S->Delta.as<double>();
   a.rhs = S->rhs.as<double>();
@@ -1172,10 +1173,9 @@ Src2Args<R> src2_args(nbte_solver* S) {
 template <typename R>
 cudaError_t enqueue_pre(nbte_solver* S, cudaStream_t st) {
   launch_walls<R>(wall_args<R>(S), st);
-  cudaError_t e = cudaMemcpyAsync(S->Tprev.p, S->T.p, S->mesh->m.n_cells * 8, cudaMemcpyDeviceToDevice, st);
-  if (e != cudaSuccess) return e;
-  e = launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->srcTQ.as<R>(),
-                          (int64_t)S->D * S->mesh->m.n_cells, st);
+  // the gather also clears the residual words of this iteration's update
+  cudaError_t e = launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->srcTQ.as<R>(),
+                                      (int64_t)S->D * S->mesh->m.n_cells, S->res.as<unsigned long long>(), st);
   if (e != cudaSuccess) return e;
   // second order: this sweep's reconstruction sources from the previous sweep's distribution
   if (S->order == 2) e = launch_src2<R>(src2_args<R>(S), st);
@@ -1184,8 +1184,6 @@ cudaError_t enqueue_pre(nbte_solver* S, cudaStream_t st) {
 
 template <typename R>
 cudaError_t enqueue_mid(nbte_solver* S, int scheme, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(S->res.p, 0, 16, st);
-  if (e != cudaSuccess) return e;
   launch_update<R>(update_args<R>(S, scheme == 0 ? 0 : 3), st);
   return cudaGetLastError();
 }
@@ -1195,7 +1193,8 @@ cudaError_t enqueue_post(nbte_solver* S, int scheme, cudaStream_t st) {
   if (scheme != 0) launch_update<R>(update_args<R>(S, scheme == 1 ? 1 : 2), st);
   cudaError_t e = cudaMemcpyAsync(S->h_res, S->res.p, 24, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(S->h_misc, S->cg_err.p ? S->cg_err.p : S->res.p, 4, cudaMemcpyDeviceToHost, st);
+  // the CG's error word (synthetic schemes only)
+  if (scheme != 0 && S->cg_err.p) e = cudaMemcpyAsync(S->h_misc, S->cg_err.p, 4, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -1282,7 +1281,7 @@ int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
   cudaStream_t st = S->stream;
   launch_walls<R>(wall_args<R>(S), st);
   NBTE_CK(launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->srcTQ.as<R>(),
-                              (int64_t)S->D * S->mesh->m.n_cells, st));
+                              (int64_t)S->D * S->mesh->m.n_cells, nullptr, st));
   NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 0), S->K, S->G, S->n_items, S->threads, S->smem, st));
   cudaEvent_t e0, e1;
   NBTE_CK(cudaEventCreate(&e0));
@@ -1477,7 +1476,7 @@ int run_finish(Run& run, nbte_solve_info* info) {
     NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
     launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
     NBTE_CK(launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->srcTQ_fin.as<R>(), (int64_t)S->D * N,
-                                st));
+                                nullptr, st));
     NBTE_CK(launch_sweep<R>(sweep_args<R>(S, 1), S->K, S->G, S->n_items, S->threads, S->smem, st));
     WallHeatArgs<R> wh{};
     wh.Bp = S->Bp;

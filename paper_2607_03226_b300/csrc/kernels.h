@@ -33,9 +33,12 @@ cudaError_t launch_pack_blocks(unsigned char* blk, int2* tq_dst, const unsigned 
                                const int64_t* sub_ptr, const int32_t* sub_end, int64_t n_chunks, int64_t N,
                                int rec_size, int pair_bytes, cudaStream_t st);
 // (T', Qdot) of every position's cell into its chunk's block:
-// ((R2*)data)[tq_dst[q].y] = ((R2*)srcTQ)[tq_dst[q].x], q = i*N + position
+// ((R2*)data)[tq_dst[q].y] = ((R2*)srcTQ)[tq_dst[q].x], q = i*N + position.
+// res_zero, if not null, gets its two words cleared (the residual maxima the
+// iteration's update collects).
 template <typename R>
-cudaError_t launch_gather_tq(unsigned char* data, const int2* tq_dst, const R* srcTQ, int64_t n, cudaStream_t st);
+cudaError_t launch_gather_tq(unsigned char* data, const int2* tq_dst, const R* srcTQ, int64_t n,
+                             unsigned long long* res_zero, cudaStream_t st);
 
 // Second-order upwind source of every work item and position, from the
 // previous sweep's distribution e[(i*N + cell)*Bp + band] (direction i, all
@@ -95,6 +98,7 @@ struct UpdateArgs {
   const double* Q;
   const double* V;
   double* T;                     // T' iterate (in/out)
+  double* Tprev;                 // T' the sweep started from (written by modes 0 and 3)
   double* Tkin;                  // kinetic T'_L of this sweep
   double* Delta;                 // T'^{n+1} - T'_L
   double* rhs;                   // synthetic right-hand side

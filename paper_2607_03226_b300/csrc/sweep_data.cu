@@ -71,9 +71,11 @@ cudaError_t launch_fill_dinv(double* dinv, const double* pos_G, const double* ba
 // (T', Qdot) of every position's cell, in each direction's level order, so
 // the sweep's producer can bulk-copy them with the position records
 template <typename R>
-__global__ void gather_tq_kernel(R* data, const int2* tq_dst, const R* srcTQ, int64_t n) {
+__global__ void gather_tq_kernel(R* data, const int2* tq_dst, const R* srcTQ, int64_t n,
+                                 unsigned long long* res_zero) {
   using R2 = typename Vec2<R>::T;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (res_zero && q < 2) res_zero[q] = 0ull;
   if (q >= n) return;
   const int2 cd = __ldcs(tq_dst + q);   // (cell, pair index)
   reinterpret_cast<R2*>(data)[(uint32_t)cd.y] = __ldg(reinterpret_cast<const R2*>(srcTQ) + cd.x);
@@ -187,15 +189,19 @@ cudaError_t launch_src2(const Src2Args<R>& a, cudaStream_t st) {
 }
 
 template <typename R>
-cudaError_t launch_gather_tq(unsigned char* data, const int2* tq_dst, const R* srcTQ, int64_t n, cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
-  gather_tq_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<R*>(data), tq_dst, srcTQ, n);
+cudaError_t launch_gather_tq(unsigned char* data, const int2* tq_dst, const R* srcTQ, int64_t n,
+                             unsigned long long* res_zero, cudaStream_t st) {
+  if (n == 0 && !res_zero) return cudaSuccess;
+  const int64_t blocks = n > 0 ? (n + 255) / 256 : 1;
+  gather_tq_kernel<R><<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<R*>(data), tq_dst, srcTQ, n, res_zero);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_src2<float>(const Src2Args<float>&, cudaStream_t);
 template cudaError_t launch_src2<double>(const Src2Args<double>&, cudaStream_t);
-template cudaError_t launch_gather_tq<float>(unsigned char*, const int2*, const float*, int64_t, cudaStream_t);
-template cudaError_t launch_gather_tq<double>(unsigned char*, const int2*, const double*, int64_t, cudaStream_t);
+template cudaError_t launch_gather_tq<float>(unsigned char*, const int2*, const float*, int64_t, unsigned long long*,
+                                              cudaStream_t);
+template cudaError_t launch_gather_tq<double>(unsigned char*, const int2*, const double*, int64_t, unsigned long long*,
+                                               cudaStream_t);
 
 }  // namespace nbte
