@@ -261,7 +261,10 @@ int nbte_solve_steady(nbte_solver* solver, const nbte_solve_opts* opts, nbte_sol
 int nbte_solve_batch(nbte_solver* const* solvers, int32_t n, const nbte_solve_opts* opts,
                      nbte_solve_info* infos);
 
-/* Results of the last solve, in the caller's cell order.
+/* Results of the last solve, in the caller's cell order, written to the
+ * caller's out[n_cells] (both calls return after out is written).  When out
+ * is page-locked host memory (cudaHostAlloc, cudaHostRegister) the values
+ * are copied into it by DMA directly, else through a pinned staging buffer.
  *   kind 0: lattice temperature T_L after the last update (K);
  *   kind 1: energy temperature sum_l sum_i w_i e / C_tot of the last sweep (K);
  *   kind 2: kinetic pseudo-temperature of the last sweep, Eq. (5), before any

@@ -2340,6 +2340,32 @@ static double* host_stage(const nbte_solver* S, size_t n) {
   return S->h_stage;
 }
 
+// page-locked host memory (the device copies into it directly)
+static bool host_pinned(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+// n doubles of the device staging buffer to the caller's out, directly when
+// out is pinned
+static int download(nbte_solver* S, double* out, size_t n) {
+  if (host_pinned(out)) {
+    NBTE_CK(cudaMemcpyAsync(out, S->io_d.p, n * 8, cudaMemcpyDeviceToHost, S->stream));
+    NBTE_CK(cudaStreamSynchronize(S->stream));
+    return NBTE_OK;
+  }
+  double* tmp = host_stage(S, n);
+  if (!tmp) return fail(NBTE_ERR_OOM, "pinned host allocation failed");
+  NBTE_CK(cudaMemcpyAsync(tmp, S->io_d.p, n * 8, cudaMemcpyDeviceToHost, S->stream));
+  NBTE_CK(cudaStreamSynchronize(S->stream));
+  std::memcpy(out, tmp, n * 8);
+  return NBTE_OK;
+}
+
 extern "C" {
 
 int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
@@ -2350,8 +2376,6 @@ int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
   DeviceGuard g(S->device);
   const Mesh& m = S->mesh->m;
   const int64_t N = m.n_cells;
-  double* tmp = host_stage(S, (size_t)N);
-  if (!tmp) return fail(NBTE_ERR_OOM, "pinned host allocation failed");
   const DBuf& src = kind == 0 ? S->T : (kind == 1 ? S->accE : S->Tkin);
   nbte_solver* Sm = const_cast<nbte_solver*>(S);   // device staging only
   int rc = ensure_perm(Sm);
@@ -2359,10 +2383,7 @@ int nbte_get_temperature(const nbte_solver* S, int kind, double* out) {
   NBTE_CK(Sm->io_d.alloc(std::max<size_t>(Sm->io_d.bytes, (size_t)N * 8 * m.dim)));
   NBTE_CK(launch_to_caller(Sm->io_d.as<double>(), src.as<double>(), Sm->perm_d.as<int32_t>(), (int)N, 1,
                            kind == 1 ? 1.0 / S->Ctot : 1.0, S->T_ref, S->stream));
-  NBTE_CK(cudaMemcpyAsync(tmp, Sm->io_d.p, N * 8, cudaMemcpyDeviceToHost, S->stream));
-  NBTE_CK(cudaStreamSynchronize(S->stream));
-  std::memcpy(out, tmp, (size_t)N * 8);
-  return NBTE_OK;
+  return download(Sm, out, (size_t)N);
 }
 
 int nbte_get_heat_flux(const nbte_solver* S, double* out) {
@@ -2372,18 +2393,13 @@ int nbte_get_heat_flux(const nbte_solver* S, double* out) {
   DeviceGuard g(S->device);
   const Mesh& m = S->mesh->m;
   const int64_t N = m.n_cells;
-  double* tmp = host_stage(S, (size_t)N * m.dim);
-  if (!tmp) return fail(NBTE_ERR_OOM, "pinned host allocation failed");
   nbte_solver* Sm = const_cast<nbte_solver*>(S);   // device staging only
   int rc = ensure_perm(Sm);
   if (rc) return rc;
   NBTE_CK(Sm->io_d.alloc(std::max<size_t>(Sm->io_d.bytes, (size_t)N * 8 * m.dim)));
   NBTE_CK(launch_to_caller(Sm->io_d.as<double>(), S->accQ.as<double>(), Sm->perm_d.as<int32_t>(), (int)N, m.dim,
                            1.0, 0.0, S->stream));
-  NBTE_CK(cudaMemcpyAsync(tmp, Sm->io_d.p, (size_t)N * m.dim * 8, cudaMemcpyDeviceToHost, S->stream));
-  NBTE_CK(cudaStreamSynchronize(S->stream));
-  std::memcpy(out, tmp, (size_t)N * m.dim * 8);
-  return NBTE_OK;
+  return download(Sm, out, (size_t)N * m.dim);
 }
 
 }  // extern "C"

@@ -313,14 +313,25 @@ class Server:
             pass
 
 
-def nbte_get_temperature(solver, kind, n_cells):
-    out = np.empty(n_cells, dtype=np.float64)
+def _out(out, shape):
+    """The caller's result array (C-contiguous float64 of this shape), or a
+    new one.  A page-locked array (e.g. a pinned torch tensor's .numpy())
+    is filled by DMA directly."""
+    if out is None:
+        return np.empty(shape, dtype=np.float64)
+    if out.dtype != np.float64 or out.shape != shape or not out.flags.c_contiguous or not out.flags.writeable:
+        raise ValueError(f"out must be a writeable C-contiguous float64 array of shape {shape}")
+    return out
+
+
+def nbte_get_temperature(solver, kind, n_cells, out=None):
+    out = _out(out, (n_cells,))
     _check(load().nbte_get_temperature(solver, int(kind), out.ctypes.data_as(_D)))
     return out
 
 
-def nbte_get_heat_flux(solver, n_cells, dim):
-    out = np.empty((n_cells, dim), dtype=np.float64)
+def nbte_get_heat_flux(solver, n_cells, dim, out=None):
+    out = _out(out, (n_cells, dim))
     _check(load().nbte_get_heat_flux(solver, out.ctypes.data_as(_D)))
     return out
 
@@ -390,11 +401,11 @@ class Solver:
         d["status"] = rc
         return d
 
-    def temperature(self, kind=0):
-        return nbte_get_temperature(self.solver, kind, self.n_cells)
+    def temperature(self, kind=0, out=None):
+        return nbte_get_temperature(self.solver, kind, self.n_cells, out)
 
-    def heat_flux(self):
-        return nbte_get_heat_flux(self.solver, self.n_cells, self.dim)
+    def heat_flux(self, out=None):
+        return nbte_get_heat_flux(self.solver, self.n_cells, self.dim, out)
 
     def wall_heat(self, tag):
         return nbte_get_wall_heat(self.solver, tag)

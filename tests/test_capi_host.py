@@ -139,6 +139,16 @@ def test_setup_argument_errors(lib):
     nbte.nbte_mesh_destroy(h)
 
 
+def test_result_buffer_checked_before_the_call(lib):
+    """A caller's result array of the wrong dtype, shape or layout is
+    refused by the binding before the library writes anything."""
+    for bad in (np.empty(10, dtype=np.float32), np.empty(9), np.empty((10, 2))[:, 0]):
+        with pytest.raises(ValueError):
+            nbte.nbte_get_temperature(None, 0, 10, out=bad)
+    with pytest.raises(ValueError):
+        nbte.nbte_get_heat_flux(None, 10, 2, out=np.empty((2, 10)))
+
+
 def test_struct_layout_matches_c_compiler(lib, tmp_path):
     """The binding's ctypes structs have the size and field offsets the C
     compiler gives the header's structs."""
