@@ -126,8 +126,16 @@ struct RecField<double> {
 }  // namespace
 
 // One work item (direction i, band group g) of one solver; the whole CTA.
-template <typename R, int K, int G, bool GR, bool O2>
+// MODE selects the outputs beyond the collision partials: 0 none, 1 every
+// outgoing value to e_out, 2 the energy and flux moments.  Second order
+// always writes e_out (the next iteration's gradients read it).  They are
+// compile-time switches: behind runtime flags the compiler evaluated their
+// address arithmetic and FP64 products ahead of the branches, for every
+// position of every sweep (the FP64 products on the FP64 pipe, a small
+// fraction of the FP32 rate on this part).
+template <typename R, int K, int G, bool GR, bool O2, int MODE>
 __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item, unsigned char* smem) {
+  constexpr bool EOUT = O2 || MODE == 1;
   const int NS = a.n_stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + NS;
@@ -338,12 +346,15 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         }
         if (slot >= 0) store_vals<R, G>(ring + slot * G, e);
         if (ex >= 0) store_vals<R, G>(exp_g + (size_t)ex * GP, e);
-        if (a.e_out)
-          store_vals<R, G>(a.e_out + (size_t)i * a.e_out_dstride + (size_t)g * a.e_out_gstride +
-                               (size_t)cell * a.e_out_cstride,
-                           e);
+        if constexpr (EOUT) {
+          if (a.e_out)
+            store_vals<R, G>(a.e_out + (size_t)i * a.e_out_dstride + (size_t)g * a.e_out_gstride +
+                                 (size_t)cell * a.e_out_cstride,
+                             e);
+        }
         part[cell] = nl;
-        if (a.full) {
+        // energy and flux moments, Eq. (7): the output sweep only
+        if constexpr (MODE == 2) {
           R es = R(0), evs = R(0);
 #pragma unroll
           for (int b = 0; b < G; ++b) {
@@ -368,10 +379,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
   }
 }
 
-template <typename R, int K, int G, bool GR, bool O2>
+template <typename R, int K, int G, bool GR, bool O2, int MODE>
 __global__ void __launch_bounds__(544) sweep_kernel(const SweepArgs<R> a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  sweep_item<R, K, G, GR, O2>(a, blockIdx.x + a.item0, smem);
+  sweep_item<R, K, G, GR, O2, MODE>(a, blockIdx.x + a.item0, smem);
 }
 
 // Work items of several solvers in one launch: block b runs item
@@ -395,12 +406,15 @@ __global__ void __launch_bounds__(544) sweep_batch_kernel(const SweepArgs<R>* ar
     s_item = (int)blockIdx.x - item_start[lo];
   }
   __syncthreads();
-  sweep_item<R, K, G, GR, O2>(sa, s_item, smem);
+  sweep_item<R, K, G, GR, O2, 0>(sa, s_item, smem);
 }
 
 template <typename R, int K, int G, bool GR, bool O2>
 static cudaError_t launch_one(const SweepArgs<R>& a, int n_items, int threads, size_t smem, cudaStream_t st) {
-  auto kern = sweep_kernel<R, K, G, GR, O2>;
+  auto kern = a.full ? sweep_kernel<R, K, G, GR, O2, 2> : sweep_kernel<R, K, G, GR, O2, 0>;
+  if constexpr (!O2) {
+    if (!a.full && a.e_out) kern = sweep_kernel<R, K, G, GR, O2, 1>;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<n_items, threads, smem, st>>>(a);

@@ -18,7 +18,8 @@ constexpr int kSweepSmemMax = 227 * 1024;
 template <typename R>
 struct SweepArgs {
   int N, dim;
-  int full;                      // also accumulate E and q (atomics)
+  int full;                      // also accumulate E and q (atomics): selects the output-sweep
+                                 // kernel variant of launch_sweep; launch_sweep_batch ignores it
   int Gpad;                      // padded row length of the import/export tables
   int n_stages;                  // shared-memory stages of the copy pipeline
   int stage_bytes, off_ring, off_stage, off_imp, off_den, off_src2;   // shared-memory layout
@@ -45,6 +46,8 @@ struct SweepArgs {
   int item0;                     // first work item of the launch (block b runs item item0 + b)
   R* e_out;                      // null, or every cell's outgoing values of the item's bands at
                                  // e_out + i * e_out_dstride + g * e_out_gstride + cell * e_out_cstride
+                                 // (written by second-order sweeps and by launch_sweep's
+                                 // e_out variant; the first-order batched launch ignores it)
   int64_t e_out_dstride, e_out_gstride, e_out_cstride;   // (direction i, band group g)
   R* gring;                      // global-memory value rings, or null for the shared-memory ring
   int64_t gring_stride;          // elements per CTA's global ring
