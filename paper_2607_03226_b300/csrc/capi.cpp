@@ -150,8 +150,10 @@ struct nbte_solver {
   size_t smem = 0;
   int order = 1;                              // upwind order of the current layout
   // second-order upwind: previous distribution [n_items*N*G], per-position
-  // sources [n_items*N*G], reconstruction tables (mesh only; kept per precision)
-  DBuf o2_e, o2_src, rc_nb, rc_twin, rc_AnV, rc_a;
+  // sources [n_items*N*G], gradients of one batch of directions
+  // [o2_db*N*Bp*dim], reconstruction tables (mesh only; kept per precision)
+  DBuf o2_e, o2_src, o2_grad, rc_nb, rc_twin, rc_AnV, rc_a, rc_gw, rc_rf;
+  int o2_db = 0;                              // directions per gradient batch
   int rc_prec = -1;
   int64_t rc_cells = 0;
   // most wall/lag imports in one chunk, per chunk length (sizes the stages' import region)
@@ -236,8 +238,8 @@ size_t device_bytes(const nbte_solver* S) {
                        &S->cg_rcx, &S->cg_scx, &S->cg_xw, &S->cg_bar, &S->cg_Ainv64,
                        &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell, &S->cg_blk_agg,
                        &S->cg_Ainv, &S->L_ecol, &S->L_eval,
-                       &S->L_diag, &S->L_dinv, &S->o2_e, &S->o2_src, &S->rc_nb, &S->rc_twin,
-                       &S->rc_AnV, &S->rc_a};
+                       &S->L_diag, &S->L_dinv, &S->o2_e, &S->o2_src, &S->o2_grad, &S->rc_nb, &S->rc_twin,
+                       &S->rc_AnV, &S->rc_a, &S->rc_gw, &S->rc_rf};
   size_t t = 0;
   for (auto* b : all) t += b->bytes;
   return t;
@@ -635,9 +637,12 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     if (gr) b += (size_t)D * ng * (((size_t)(S->max_slots + 1) * G + 3) / 4 * 4) * sz;   // global rings
     b += N * (4 * sz + 12 * 8 + 8 * (size_t)S->mesh->m.dim);            // per-cell fields
     if (!prec) b += (size_t)D * Bp * N * 8;                              // FP64 denominators
-    if (order2) {                                                        // previous distribution, sources, tables
-      const size_t nf = (size_t)S->mesh->m.nfc;
-      b += 2 * D * Bp * N * sz + N * nf * (8 + 3 * sz + nf * sz);
+    if (order2) {                                                        // previous distribution, sources,
+      const size_t nf = (size_t)S->mesh->m.nfc;                         // gradients of one batch, tables
+      const size_t grad_dir = N * Bp * (size_t)S->mesh->m.dim * sz;
+      b += 2 * D * Bp * N * sz + N * nf * (8 + 3 * sz);
+      if (nf == 6) b += std::max<size_t>(1, std::min<size_t>(D, ((size_t)2 << 30) / grad_dir)) * grad_dir + N * nf * 6 * sz;
+      else b += N * nf * nf * sz;
     }
     b += D * N / 8 + (size_t)S->n_dbf * Bp * 8 + (size_t)S->n_wf * 16;  // chunks, diffuse sums, wall heat
     *estimate = b;
@@ -733,17 +738,35 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     NBTE_CK(S->o2_src.alloc(((size_t)S->n_items * N + 16) * G * sz));
     NBTE_CK(cudaMemsetAsync(S->o2_e.p, 0, S->o2_e.bytes, S->stream));
     NBTE_CK(cudaMemsetAsync(S->o2_src.p, 0, S->o2_src.bytes, S->stream));
-    if (S->rc_prec != prec || !S->rc_a.p) {
+    // hexahedra: the gradients of as many directions as fit in about 2 GiB
+    // at once (two passes); other cells: one pass over all directions
+    const bool two_pass = S->mesh->m.nfc == 6;
+    const size_t grad_dir = (size_t)N * S->Bp * S->mesh->m.dim * sz;
+    S->o2_db = two_pass ? (int)std::max<size_t>(1, std::min<size_t>((size_t)S->D, ((size_t)2 << 30) / grad_dir))
+                        : S->D;
+    if (two_pass) NBTE_CK(S->o2_grad.alloc((size_t)S->o2_db * grad_dir));
+    else S->o2_grad.release();
+    if (S->rc_prec != prec || !S->rc_AnV.p) {
       Reconstruction rcn;
       build_reconstruction(S->mesh->m, rcn);
       NBTE_CK(upload(S->rc_nb, rcn.nb));
       NBTE_CK(upload(S->rc_twin, rcn.twin));
       if (prec) {
         NBTE_CK(upload(S->rc_AnV, to_float(rcn.AnV)));
-        NBTE_CK(upload(S->rc_a, to_float(rcn.a)));
+        if (two_pass) {
+          NBTE_CK(upload(S->rc_gw, to_float(rcn.gw)));
+          NBTE_CK(upload(S->rc_rf, to_float(rcn.rf)));
+        } else {
+          NBTE_CK(upload(S->rc_a, to_float(rcn.a)));
+        }
       } else {
         NBTE_CK(upload(S->rc_AnV, rcn.AnV));
-        NBTE_CK(upload(S->rc_a, rcn.a));
+        if (two_pass) {
+          NBTE_CK(upload(S->rc_gw, rcn.gw));
+          NBTE_CK(upload(S->rc_rf, rcn.rf));
+        } else {
+          NBTE_CK(upload(S->rc_a, rcn.a));
+        }
       }
       S->rc_prec = prec;
       S->rc_cells = rcn.cells_with_gradient;
@@ -751,6 +774,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   } else {
     S->o2_e.release();
     S->o2_src.release();
+    S->o2_grad.release();
+    S->o2_db = 0;
   }
   NBTE_CK(S->T.alloc(N * 8));
   NBTE_CK(S->Tprev.alloc(N * 8));
@@ -1154,6 +1179,7 @@ Src2Args<R> src2_args(nbte_solver* S) {
   Src2Args<R> a{};
   a.N = (int)S->mesh->m.n_cells;
   a.nfc = S->mesh->m.nfc;
+  a.dim = S->mesh->m.dim;
   a.G = S->G;
   a.n_items = S->n_items;
   a.n_groups = S->n_groups;
@@ -1161,11 +1187,14 @@ Src2Args<R> src2_args(nbte_solver* S) {
   a.D = S->D;
   a.e = S->o2_e.as<R>();
   a.src2 = S->o2_src.as<R>();
+  a.grad = S->o2_grad.as<R>();
   a.pos_cell = S->pos_cell.as<int32_t>();
   a.nb = S->rc_nb.as<int32_t>();
   a.twin = S->rc_twin.as<int32_t>();
   a.AnV = S->rc_AnV.as<R>();
   a.rc_a = S->rc_a.as<R>();
+  a.gw = S->rc_gw.as<R>();
+  a.rf = S->rc_rf.as<R>();
   a.dir_s = S->dir_s.as<double>();
   return a;
 }
@@ -1177,8 +1206,16 @@ cudaError_t enqueue_pre(nbte_solver* S, cudaStream_t st) {
   cudaError_t e = launch_gather_tq<R>(S->rec.as<unsigned char>(), S->tq_dst.as<int2>(), S->srcTQ.as<R>(),
                                       (int64_t)S->D * S->mesh->m.n_cells, S->res.as<unsigned long long>(), st);
   if (e != cudaSuccess) return e;
-  // second order: this sweep's reconstruction sources from the previous sweep's distribution
-  if (S->order == 2) e = launch_src2<R>(src2_args<R>(S), st);
+  // second order: this sweep's reconstruction sources from the previous
+  // sweep's distribution, one batch of directions at a time
+  if (S->order == 2) {
+    Src2Args<R> a = src2_args<R>(S);
+    for (int d0 = 0; d0 < S->D && e == cudaSuccess; d0 += S->o2_db) {
+      a.dir0 = d0;
+      a.n_dirs = std::min(S->o2_db, S->D - d0);
+      e = launch_src2<R>(a, st);
+    }
+  }
   return e;
 }
 
@@ -1390,7 +1427,8 @@ struct Run {
   std::chrono::steady_clock::time_point t0, t1;
 
   int64_t kernels_per_iter() const {
-    return (S->n_dbf > 0) + (S->n_imp > 0) + 2 + (o.scheme == 0 ? 1 : 3) + (S->order == 2);
+    return (S->n_dbf > 0) + (S->n_imp > 0) + 2 + (o.scheme == 0 ? 1 : 3) +
+           (S->order == 2 ? (S->mesh->m.nfc == 6 ? 2 : 1) * ((S->D + S->o2_db - 1) / S->o2_db) : 0);
   }
   // after an iteration's residual words reached the host: true to stop
   bool check() {
@@ -1832,8 +1870,8 @@ void shrink(nbte_solver* S) {
                  &S->delta, &S->dsum, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s, &S->cg_w, &S->cg_x, &S->cg_xw,
                  &S->cg_rw, &S->cg_rcx, &S->cg_scx, &S->cg_Ainv, &S->cg_Ainv64, &S->L_ecol, &S->L_eval,
                  &S->L_diag, &S->L_dinv, &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell,
-                 &S->cg_blk_agg, &S->cg_slots, &S->dinv, &S->o2_e, &S->o2_src, &S->rc_nb, &S->rc_twin,
-                 &S->rc_AnV, &S->rc_a};
+                 &S->cg_blk_agg, &S->cg_slots, &S->dinv, &S->o2_e, &S->o2_src, &S->o2_grad, &S->rc_nb,
+                 &S->rc_twin, &S->rc_AnV, &S->rc_a, &S->rc_gw, &S->rc_rf};
   for (DBuf* b : big) b->release();
   S->rc_prec = -1;
   S->layout_key.clear();

@@ -40,24 +40,34 @@ template <typename R>
 cudaError_t launch_gather_tq(unsigned char* data, const int2* tq_dst, const R* srcTQ, int64_t n,
                              unsigned long long* res_zero, cudaStream_t st);
 
-// Second-order upwind source of every work item and position, from the
-// previous sweep's distribution e[(i*N + cell)*Bp + band] (direction i, all
-// bands of a cell contiguous):
+// Second-order upwind source of every work item and position of the
+// directions [dir0, dir0 + n_dirs), from the previous sweep's distribution
+// e[(i*N + cell)*Bp + band] (direction i, all bands of a cell contiguous):
 //   src2 = -sum over the cell's interior faces f of (s_i . An_f / V) *
-//          sum_m rc_a[u, f_u, m] (e[nb(u, m)] - e[u]),
+//          grad_u . rf[u, f_u],
+//   grad_u = sum_m gw[u, m] (e[nb(u, m)] - e[u]),
 // u the face's upwind cell (the cell itself on outflow faces) and f_u the
-// face's local index in u.  Written at src2[(item*N + pos)*G + b], item =
-// i*n_groups + g, the layout the sweep's chunks copy.
+// face's local index in u.  Hexahedra take two launches: the gradients of
+// the batch into grad[(j*N + cell)*Bp*dim + (group*dim + d)*G + b]
+// (j = i - dir0), then the face sums.  Other cells take one, with the
+// weights toward each face precombined (rc_a).  Written at
+// src2[(item*N + pos)*G + b], item = i*n_groups + g, the layout the sweep's
+// chunks copy.
 template <typename R>
 struct Src2Args {
-  int N, nfc, G, n_items, n_groups, Bp, D;
+  int N, nfc, dim, G, n_items, n_groups, Bp, D;
+  int dir0, n_dirs;              // the batch of directions
   const R* e;
   R* src2;
+  R* grad;                       // [n_dirs*N*Bp*dim] gradients of the batch
   const int32_t* pos_cell;       // [D*N] cell of each position
   const int32_t* nb;             // [N*nfc] neighbour or -1
   const int32_t* twin;           // [N*nfc] the face's local index in the neighbour
   const R* AnV;                  // [N*nfc*3] outward face vector / cell volume
-  const R* rc_a;                 // [N*nfc*nfc] reconstruction weights
+  const R* rc_a;                 // [N*nfc*nfc] weights toward each face (one pass: nfc <= 4)
+  const R* gw;                   // [N*nfc*3] gradient weights, zero without a gradient (two
+                                 // passes: hexahedra)
+  const R* rf;                   // [N*nfc*3] face centroid minus cell centroid (two passes)
   const double* dir_s;           // [D*3]
 };
 template <typename R>

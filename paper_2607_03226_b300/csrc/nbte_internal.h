@@ -113,6 +113,11 @@ void build_laplacian(const Mesh& m, const std::vector<BC>& bcs, double kappa_bul
 struct Reconstruction {
   std::vector<int32_t> nb, twin;
   std::vector<double> AnV, a;
+  // the same operator in two factors: gradient weights gw[(c*nf + m)*3 + d]
+  // (grad_d = sum_m gw (e[nb m] - e[c]); zero without a gradient) and face
+  // offsets rf[(c*nf + k)*3 + d] (face centroid minus cell centroid), so
+  // that a[(c*nf + k)*nf + m] = sum_d gw[(c*nf + m)*3 + d] rf[(c*nf + k)*3 + d]
+  std::vector<double> gw, rf;
   int64_t cells_with_gradient = 0;
 };
 void build_reconstruction(const Mesh& m, Reconstruction& rc);

@@ -543,6 +543,8 @@ void build_reconstruction(const Mesh& m, Reconstruction& rc) {
   rc.twin.assign((size_t)N * nf, -1);
   rc.AnV.assign((size_t)N * nf * 3, 0.0);
   rc.a.assign((size_t)N * nf * nf, 0.0);
+  rc.gw.assign((size_t)N * nf * 3, 0.0);
+  rc.rf.assign((size_t)N * nf * 3, 0.0);
   rc.cells_with_gradient = 0;
   for (int64_t c = 0; c < N; ++c) {
     int n_nb = 0;
@@ -551,6 +553,7 @@ void build_reconstruction(const Mesh& m, Reconstruction& rc) {
     for (int k = 0; k < nf; ++k) {
       const int64_t h = c * nf + k;
       for (int d = 0; d < dim; ++d) rc.AnV[h * 3 + d] = m.An[h * dim + d] / m.V[c];
+      for (int d = 0; d < dim; ++d) rc.rf[h * 3 + d] = m.xf[h * dim + d] - m.xc[c * dim + d];
       const int64_t nk = m.nb[h];
       if (nk < 0) continue;
       rc.nb[h] = (int32_t)nk;
@@ -579,6 +582,7 @@ void build_reconstruction(const Mesh& m, Reconstruction& rc) {
       double g[3] = {0, 0, 0};   // P r_m
       for (int i = 0; i < dim; ++i)
         for (int j = 0; j < dim; ++j) g[i] += P[i][j] * r[mm][j];
+      for (int d = 0; d < dim; ++d) rc.gw[((size_t)c * nf + mm) * 3 + d] = g[d];
       for (int k = 0; k < nf; ++k) {
         const int64_t h = c * nf + k;
         double w = 0.0;

@@ -81,7 +81,8 @@ __global__ void gather_tq_kernel(R* data, const int2* tq_dst, const R* srcTQ, in
   reinterpret_cast<R2*>(data)[(uint32_t)cd.y] = __ldg(reinterpret_cast<const R2*>(srcTQ) + cd.x);
 }
 
-// Second-order upwind sources.  One thread per (direction, position): it
+// Second-order upwind sources in one pass (triangles, quadrilaterals,
+// tetrahedra).  One thread per (direction, position): it
 // resolves the cell's faces once -- upwind cell, its neighbours and the
 // reconstruction weights toward the face -- and keeps them in registers
 // while it walks the band groups along each needed row of the direction's
@@ -93,7 +94,7 @@ __global__ void gather_tq_kernel(R* data, const int2* tq_dst, const R* srcTQ, in
 // zero weight): no branches between the loads.
 template <typename R, int G, int NF>
 __global__ void __launch_bounds__(256, NF > 4 ? 3 : 1) src2_kernel(const Src2Args<R> a) {
-  const int i = blockIdx.y;   // direction (a 2D grid: no division by N)
+  const int i = a.dir0 + blockIdx.y;   // direction (a 2D grid: no division by N)
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.N) return;
   const int c = __ldg(a.pos_cell + (int64_t)i * a.N + p);
@@ -161,13 +162,129 @@ __global__ void __launch_bounds__(256, NF > 4 ? 3 : 1) src2_kernel(const Src2Arg
   }
 }
 
+// Second-order upwind sources in two passes (hexahedra), over a batch of
+// directions.
+//  1. grad_kernel: one thread per (direction, cell) takes the least-squares
+//     gradient of every band, grad_d = sum_m gw[c, m, d] (e[nb m] - e[c]),
+//     from the cell's row of the previous sweep's distribution and its
+//     neighbours' rows (NF + 1 gathered rows per cell), stored as
+//     grad[dir][cell][group][d][G].
+//  2. face_src_kernel: one thread per (direction, position) sums over the
+//     cell's interior faces f: -(s . An_f / V) (grad_u . rf[u, f_u]), u the
+//     face's upwind cell (the cell itself on outflow faces) and f_u the
+//     face's local index in u: NF gathered gradient blocks per position.
+// The single pass gathers NF (NF + 1) rows per position (the upwind cell
+// and its neighbours, for every face): 42 for hexahedra against 7 + 6 here.
+// For NF <= 4 the gradient buffer's traffic outweighs the saving (measured
+// on triangles and tetrahedra), so those meshes keep the single pass.  Wall faces get d = 0; a wall
+// neighbour reads the cell itself (zero difference, zero weight).  Results
+// go to the [item][position][G] layout the sweep copies, one contiguous run
+// per band group.
+template <typename R, int G, int NF, int DIM>
+__global__ void __launch_bounds__(256) grad_kernel(const Src2Args<R> a) {
+  const int i = a.dir0 + blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.N) return;
+  int nb[NF];
+  R w[NF][DIM];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    const int nm = __ldg(a.nb + (int64_t)c * NF + m);
+    nb[m] = nm >= 0 ? nm : c;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) w[m][d] = __ldg(a.gw + ((int64_t)c * NF + m) * 3 + d);
+  }
+  const R* e = a.e + (size_t)i * a.N * a.Bp;
+  R* gr = a.grad + ((size_t)blockIdx.y * a.N + c) * a.Bp * DIM;
+  for (int g = 0; g < a.n_groups; ++g) {
+    const R* eg = e + g * G;
+    R ec[G], acc[DIM][G];
+    load_vals<R, G>(eg + (size_t)c * a.Bp, ec);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int b = 0; b < G; ++b) acc[d][b] = R(0);
+#pragma unroll
+    for (int m = 0; m < NF; ++m) {
+      R en[G];
+      load_vals<R, G>(eg + (size_t)nb[m] * a.Bp, en);
+#pragma unroll
+      for (int b = 0; b < G; ++b) {
+        const R diff = en[b] - ec[b];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) acc[d][b] += w[m][d] * diff;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) store_vals<R, G>(gr + (size_t)(g * DIM + d) * G, acc[d]);
+  }
+}
+
+template <typename R, int G, int NF, int DIM>
+__global__ void __launch_bounds__(256) face_src_kernel(const Src2Args<R> a) {
+  const int bi = blockIdx.y;   // direction within the batch (a 2D grid: no division by N)
+  const int i = a.dir0 + bi;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.N) return;
+  const int c = __ldg(a.pos_cell + (int64_t)i * a.N + p);
+  const R sx = (R)a.dir_s[i * 3], sy = (R)a.dir_s[i * 3 + 1], sz = (R)a.dir_s[i * 3 + 2];
+  R dk[NF], rf[NF][DIM];
+  int u[NF];
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    const int nk = __ldg(a.nb + (int64_t)c * NF + k);
+    const int tw = __ldg(a.twin + (int64_t)c * NF + k);
+    const R* An = a.AnV + ((int64_t)c * NF + k) * 3;
+    R d = sx * __ldg(An) + sy * __ldg(An + 1) + sz * __ldg(An + 2);
+    if (nk < 0) d = R(0);
+    const bool in = d < R(0);
+    dk[k] = d;
+    u[k] = in ? nk : c;
+    const int h = in ? tw : k;
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) rf[k][q] = __ldg(a.rf + ((int64_t)u[k] * NF + h) * 3 + q);
+  }
+  const R* grad = a.grad + (size_t)bi * a.N * a.Bp * DIM;
+  R* out = a.src2 + ((size_t)i * a.n_groups * a.N + p) * G;
+  for (int g = 0; g < a.n_groups; ++g) {
+    R acc[G];
+#pragma unroll
+    for (int b = 0; b < G; ++b) acc[b] = R(0);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+      const R* gu = grad + ((size_t)u[k] * a.Bp + g * G) * DIM;
+      R face[G];
+#pragma unroll
+      for (int b = 0; b < G; ++b) face[b] = R(0);
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        R gq[G];
+        load_vals<R, G>(gu + q * G, gq);
+#pragma unroll
+        for (int b = 0; b < G; ++b) face[b] += rf[k][q] * gq[b];
+      }
+#pragma unroll
+      for (int b = 0; b < G; ++b) acc[b] -= dk[k] * face[b];
+    }
+    store_vals<R, G>(out + (size_t)g * a.N * G, acc);
+  }
+}
+
+template <typename R, int G, int NF, int DIM>
+static cudaError_t launch_src2_fd(const Src2Args<R>& a, cudaStream_t st) {
+  const dim3 grid((unsigned)((a.N + 255) / 256), (unsigned)a.n_dirs);
+  grad_kernel<R, G, NF, DIM><<<grid, 256, 0, st>>>(a);
+  face_src_kernel<R, G, NF, DIM><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename R, int G>
 static cudaError_t launch_src2_g(const Src2Args<R>& a, cudaStream_t st) {
-  const dim3 grid((unsigned)((a.N + 255) / 256), (unsigned)a.D);
+  if (a.nfc == 6 && a.dim == 3) return launch_src2_fd<R, G, 6, 3>(a, st);
+  const dim3 grid((unsigned)((a.N + 255) / 256), (unsigned)a.n_dirs);
   switch (a.nfc) {
     case 3: src2_kernel<R, G, 3><<<grid, 256, 0, st>>>(a); break;
     case 4: src2_kernel<R, G, 4><<<grid, 256, 0, st>>>(a); break;
-    case 6: src2_kernel<R, G, 6><<<grid, 256, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -175,8 +292,9 @@ static cudaError_t launch_src2_g(const Src2Args<R>& a, cudaStream_t st) {
 
 template <typename R>
 cudaError_t launch_src2(const Src2Args<R>& a, cudaStream_t st) {
-  if ((int64_t)a.n_items * a.N == 0) return cudaSuccess;
-  if (a.Bp != a.n_groups * a.G || a.D > 65535) return cudaErrorInvalidValue;
+  if ((int64_t)a.n_dirs * a.N == 0) return cudaSuccess;
+  if (a.Bp != a.n_groups * a.G || a.n_dirs > 65535 || a.dir0 < 0 || a.dir0 + a.n_dirs > a.D)
+    return cudaErrorInvalidValue;
   switch (a.G) {
     case 1: return launch_src2_g<R, 1>(a, st);
     case 2: return launch_src2_g<R, 2>(a, st);
