@@ -93,18 +93,15 @@ __global__ void gather_tq_kernel(R* data, const int2* tq_dst, const R* srcTQ, in
 // a wall neighbour of the upwind cell reads the upwind cell (zero difference,
 // zero weight): no branches between the loads.
 template <typename R, int G, int NF>
-__global__ void __launch_bounds__(256, NF > 4 ? 3 : 1) src2_kernel(const Src2Args<R> a) {
+__global__ void __launch_bounds__(256, 1) src2_kernel(const Src2Args<R> a) {
+  static_assert(NF <= 4, "hexahedra take the two-pass form");
   const int i = a.dir0 + blockIdx.y;   // direction (a 2D grid: no division by N)
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.N) return;
   const int c = __ldg(a.pos_cell + (int64_t)i * a.N + p);
   const R sx = (R)a.dir_s[i * 3], sy = (R)a.dir_s[i * 3 + 1], sz = (R)a.dir_s[i * 3 + 2];
-  // hexahedra (36 weights and neighbours) re-read the tables from L1 per band
-  // group instead of holding them in registers
-  constexpr bool kHold = NF <= 4;
-  constexpr int NH = kHold ? NF : 1;
-  R d[NF], w[NH][NH];
-  int u[NF], h[NF], nbu[NH][NH];
+  R d[NF], w[NF][NF];
+  int u[NF], h[NF], nbu[NF][NF];
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
     const int nk = __ldg(a.nb + (int64_t)c * NF + k);
@@ -116,13 +113,11 @@ __global__ void __launch_bounds__(256, NF > 4 ? 3 : 1) src2_kernel(const Src2Arg
     d[k] = dk;
     u[k] = in ? nk : c;
     h[k] = in ? tw : k;
-    if constexpr (kHold) {
 #pragma unroll
-      for (int m2 = 0; m2 < NF; ++m2) {
-        const int nm = __ldg(a.nb + (int64_t)u[k] * NF + m2);
-        nbu[k][m2] = nm >= 0 ? nm : u[k];
-        w[k][m2] = __ldg(a.rc_a + ((int64_t)u[k] * NF + h[k]) * NF + m2);
-      }
+    for (int m2 = 0; m2 < NF; ++m2) {
+      const int nm = __ldg(a.nb + (int64_t)u[k] * NF + m2);
+      nbu[k][m2] = nm >= 0 ? nm : u[k];
+      w[k][m2] = __ldg(a.rc_a + ((int64_t)u[k] * NF + h[k]) * NF + m2);
     }
   }
   const R* e = a.e + (size_t)i * a.N * a.Bp;
@@ -140,20 +135,10 @@ __global__ void __launch_bounds__(256, NF > 4 ? 3 : 1) src2_kernel(const Src2Arg
       for (int b = 0; b < G; ++b) inc[b] = R(0);
 #pragma unroll
       for (int m2 = 0; m2 < NF; ++m2) {
-        int nm;
-        R wm;
-        if constexpr (kHold) {
-          nm = nbu[k][m2];
-          wm = w[k][m2];
-        } else {
-          nm = __ldg(a.nb + (int64_t)u[k] * NF + m2);
-          nm = nm >= 0 ? nm : u[k];
-          wm = __ldg(a.rc_a + ((int64_t)u[k] * NF + h[k]) * NF + m2);
-        }
         R en[G];
-        load_vals<R, G>(eg + (size_t)nm * a.Bp, en);
+        load_vals<R, G>(eg + (size_t)nbu[k][m2] * a.Bp, en);
 #pragma unroll
-        for (int b = 0; b < G; ++b) inc[b] += wm * (en[b] - eu[b]);
+        for (int b = 0; b < G; ++b) inc[b] += w[k][m2] * (en[b] - eu[b]);
       }
 #pragma unroll
       for (int b = 0; b < G; ++b) acc[b] -= d[k] * inc[b];
