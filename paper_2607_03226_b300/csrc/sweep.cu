@@ -6,11 +6,12 @@
 //
 // Warp-specialised pipeline, one CTA per work item:
 //  * warp 0 (one elected lane) is the producer.  It walks the direction's
-//    chunks (up to CAP consecutive positions of one level) and, several chunks
-//    ahead of the consumers, bulk-copies (cp.async.bulk, completion counted on
-//    an mbarrier) each chunk's packed position records, its pre-gathered
-//    (T', Qdot) pairs and its slice of wall/lag import values into a ring of
-//    shared-memory stages;
+//    chunks (whole consecutive levels of at most CAP positions together, or a
+//    piece of one wider level) and, several chunks ahead of the consumers,
+//    bulk-copies (cp.async.bulk, completion counted on an mbarrier) each
+//    chunk's block -- a header of level ends, the packed position records and
+//    the pre-gathered (T', Qdot) pairs -- and its slice of wall/lag import
+//    values into a ring of shared-memory stages;
 //  * the other warps are consumers: they wait on a stage's "full" barrier,
 //    compute one position per thread from shared memory and the value ring,
 //    release the stage on its "empty" barrier, and meet on a named barrier
