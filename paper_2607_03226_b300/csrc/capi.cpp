@@ -520,6 +520,18 @@ int64_t tune_key(const nbte_solver* S) { return S->plan_built * 1000003 + S->ver
 // non-null nothing is allocated: *estimate receives the device bytes the
 // layout would hold (records, tables, distributions' in-flight buffers,
 // per-cell fields), for admission by memory budget.
+// bytes of second-order gradients held at once (hexahedra compute them in
+// direction batches of this size): 2 GiB, or NBTE_O2_GRAD_BYTES when set
+// (smaller batches exercise the batching on small meshes)
+static size_t o2_grad_budget() {
+  size_t budget = (size_t)2 << 30;
+  if (const char* v = std::getenv("NBTE_O2_GRAD_BYTES")) {
+    const long long x = std::atoll(v);
+    if (x > 0) budget = (size_t)x;
+  }
+  return budget;
+}
+
 int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = nullptr) {
   if (S->B <= 0) return fail(NBTE_ERR_STATE, "nbte_set_bands must be called before solving");
   const int prec = o.precision;
@@ -641,7 +653,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
       const size_t nf = (size_t)S->mesh->m.nfc;                         // gradients of one batch, tables
       const size_t grad_dir = N * Bp * (size_t)S->mesh->m.dim * sz;
       b += 2 * D * Bp * N * sz + N * nf * (8 + 3 * sz);
-      if (nf == 6) b += std::max<size_t>(1, std::min<size_t>(D, ((size_t)2 << 30) / grad_dir)) * grad_dir + N * nf * 6 * sz;
+      if (nf == 6) b += std::max<size_t>(1, std::min<size_t>(D, o2_grad_budget() / grad_dir)) * grad_dir + N * nf * 6 * sz;
       else b += N * nf * nf * sz;
     }
     b += D * N / 8 + (size_t)S->n_dbf * Bp * 8 + (size_t)S->n_wf * 16;  // chunks, diffuse sums, wall heat
@@ -738,11 +750,11 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     NBTE_CK(S->o2_src.alloc(((size_t)S->n_items * N + 16) * G * sz));
     NBTE_CK(cudaMemsetAsync(S->o2_e.p, 0, S->o2_e.bytes, S->stream));
     NBTE_CK(cudaMemsetAsync(S->o2_src.p, 0, S->o2_src.bytes, S->stream));
-    // hexahedra: the gradients of as many directions as fit in about 2 GiB
-    // at once (two passes); other cells: one pass over all directions
+    // hexahedra: the gradients of as many directions as fit in the gradient
+    // budget at once (two passes); other cells: one pass over all directions
     const bool two_pass = S->mesh->m.nfc == 6;
     const size_t grad_dir = (size_t)N * S->Bp * S->mesh->m.dim * sz;
-    S->o2_db = two_pass ? (int)std::max<size_t>(1, std::min<size_t>((size_t)S->D, ((size_t)2 << 30) / grad_dir))
+    S->o2_db = two_pass ? (int)std::max<size_t>(1, std::min<size_t>((size_t)S->D, o2_grad_budget() / grad_dir))
                         : S->D;
     if (two_pass) NBTE_CK(S->o2_grad.alloc((size_t)S->o2_db * grad_dir));
     else S->o2_grad.release();

@@ -130,6 +130,25 @@ def test_order2_warm_start_continues(nbte_mod):
     s.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_hex_gradients_in_direction_batches(nbte_mod, monkeypatch, precision):
+    """Hexahedra compute the reconstruction gradients in direction batches
+    sized by a memory budget.  A budget of one byte (one direction per
+    batch) gives bitwise the same second-order iterations as one batch of
+    all directions."""
+    p = CASES["cube_hex"]()
+    s = nbte_mod.Solver(p)
+    s.solve(scheme="sequential", precision=precision, n_iter=3, order=2)
+    T_one = s.temperature(0)
+    s.close()
+    monkeypatch.setenv("NBTE_O2_GRAD_BYTES", "1")
+    s = nbte_mod.Solver(p)
+    info = s.solve(scheme="sequential", precision=precision, n_iter=3, order=2)
+    assert info["status"] == 0
+    assert np.array_equal(s.temperature(0), T_one)
+    s.close()
+
+
 def test_order2_in_a_batch(nbte_mod):
     """A second-order solve batched with first-order ones (fused sweep
     launches) equals the same solve alone; the first-order solves too."""
