@@ -1,4 +1,5 @@
-"""The benchmark's multi-rank logic on CPU: two gloo ranks on 127.0.0.1.
+"""The benchmark's host logic on CPU: two gloo ranks on 127.0.0.1 (max over
+ranks), the roofline's algorithmic bytes and the traffic digest.
 The job time is the slowest rank's (max over ranks), the value the units of
 all ranks over it; the reference arm prints from rank 0 only."""
 import io
@@ -52,3 +53,42 @@ def test_reference_arm_prints_from_rank_zero_only(monkeypatch):
     with contextlib.redirect_stdout(buf):
         bench.run_reference(type("A", (), {"steps": 1, "warmup": 1, "cpu_seconds": 1.0})())
     assert buf.getvalue() == ""
+
+
+def test_sweep_algorithmic_bytes_by_hand():
+    """The roofline's algorithmic bytes for the 32^3 cube's sweep, item by
+    item: records (cell, slot, export, G and three inflow (reference,
+    coefficient) pairs = 40 B) per (direction, cell), one FP32 partial per
+    (work item, cell), the (T', Qdot) pairs, and the wall rows of all
+    bands."""
+    st = {"K": 3, "items": 1280, "exports": 381056, "imports": 393216}
+    N, D, Bp = 32768, 128, 40
+    expect = D * N * 40 + 1280 * N * 4 + N * 8 + (381056 + 393216) * Bp * 4
+    assert bench.sweep_algorithmic_bytes(st, N, D, 4, Bp) == expect == 459689984
+    # second order adds the source read and the distribution kept, per band
+    assert bench.sweep_algorithmic_bytes(st, N, D, 4, Bp, order=2) == expect + 2 * D * N * Bp * 4
+
+
+def test_sweep_traffic_only_for_the_captured_sources(tmp_path, monkeypatch):
+    """The committed DRAM traffic is reported only while the digest of the
+    sweep's sources and the launch layout match the capture's."""
+    import hashlib
+    import shutil
+    csrc = tmp_path / "paper_2607_03226_b300" / "csrc"
+    csrc.mkdir(parents=True)
+    names = ("sweep.cu", "vecio.cuh", "layout.h", "sweep_args.h")
+    for f in names:
+        shutil.copy(os.path.join(os.path.dirname(HERE), "paper_2607_03226_b300", "csrc", f), csrc / f)
+    h = hashlib.sha256()
+    for f in names:
+        h.update((csrc / f).read_bytes())
+    (tmp_path / "profiles").mkdir()
+    prof = tmp_path / "profiles" / "sweep_kernel_finfet2d_fp32.md"
+    prof.write_text("# capture\n\ntraffic_bytes_per_launch: 123456\n"
+                    f"sweep_source_digest: {h.hexdigest()[:16]}\nlayout: band_group=2 cta_threads=192\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._sweep_traffic(2, 192) == 123456
+    assert bench._sweep_traffic(4, 256) is None          # another layout
+    with open(csrc / "sweep.cu", "a") as fh:             # the kernel changed since the capture
+        fh.write("\n// edited\n")
+    assert bench._sweep_traffic(2, 192) is None
