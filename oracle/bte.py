@@ -413,7 +413,7 @@ class OracleSolver:
             div[c] += np.sum(wv * a[None, :] * up)
         return div
 
-    # ------------------------------------------------------------------ driver
+    # ---------------------------------------------------------- iteration loop
     def solve(self, scheme=None, tol=None, max_iter=None, n_iter=None, T_init=None, init="tref",
               store_e=False, verbose=False, order=1):
         """Run the outer iteration.

@@ -1,5 +1,5 @@
 // extern "C" entry points of libnanobte (see include/nbte.h) and the solve
-// driver.  One outer iteration (Sec. II, Eq. (6) / Eq. (12)) is
+// iteration loop.  One outer iteration (Sec. II, Eq. (6) / Eq. (12)) is
 //   walls -> sweep -> moment reduction + update [-> CG correction -> update]
 // on the solver's stream; the host reads two residual words per iteration
 // and stops at tol.  With use_graph the iteration is captured once as a CUDA
