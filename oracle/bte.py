@@ -61,6 +61,24 @@ from .geometry import build_geometry
 THERMALIZING, DIFFUSE, SPECULAR, PARTIAL = 0, 1, 2, 3
 
 
+class _OrderedSystem:
+    """``A = I/tau + v K`` of one (band, direction) task whose upwind graph is
+    acyclic, held as the permutation ``order`` (a topological order of the
+    graph) and ``Kp = K[order][:, order]`` (lower triangular).  ``solve``
+    returns ``A^{-1} rhs`` in the original cell order."""
+
+    def __init__(self, order, Kp, inv_tau, v):
+        self.order, self.Kp, self.inv_tau, self.v = order, Kp, inv_tau, v
+
+    def solve(self, rhs):
+        n = self.order.size
+        A = (sp.identity(n, format="csc") * self.inv_tau + self.Kp * self.v).tocsc()
+        x = spla.spsolve_triangular(A, rhs[self.order], lower=True, overwrite_A=True)
+        e = np.empty_like(x)
+        e[self.order] = x
+        return e
+
+
 def quadrature_moments(s, w):
     """Zeroth, first and second moments of a direction set (pin: Eq. (11)'s W)."""
     s = np.asarray(s, dtype=np.float64)
@@ -129,6 +147,9 @@ class OracleSolver:
         # first use (see _direction)
         self._dir = {}
         self._lu = {}
+        self._order = {}
+        self._ordered = {}
+        self._S = None
         self._lap = None
 
     def _direction(self, i):
@@ -156,7 +177,9 @@ class OracleSolver:
     # ------------------------------------------------------------------ pieces
     def source(self):
         """S_cl = Qdot_c C_l / (C_tot W) (Sec. III B)."""
-        return self.Qdot[:, None] * (self.C / (self.Ctot * self.W))[None, :]
+        if self._S is None:
+            self._S = self.Qdot[:, None] * (self.C / (self.Ctot * self.W))[None, :]
+        return self._S
 
     def equilibrium_walls(self, Tdev):
         """Wall-cell distribution at equilibrium with ``Tdev`` (iteration-0 state)."""
@@ -274,29 +297,91 @@ class OracleSolver:
         inc = np.sum(grad[u] * (g.hf_xf[m] - g.xc[u]), axis=1)
         return -np.bincount(g.hf_cell[m], weights=a * inc / g.V[g.hf_cell[m]], minlength=self.N)
 
+    def upwind_order(self, i):
+        """A topological order of direction i's upwind graph (every cell after
+        the neighbours it receives from across an inflow face), or None when
+        the graph has a cycle.  Kahn's algorithm: repeatedly take every cell
+        whose upstream neighbours are all placed."""
+        got = self._order.get(i)
+        if got is not None or i in self._order:
+            return got
+        g = self.g
+        a = g.hf_An @ self.s[i]
+        m = (a < 0) & (g.hf_nb >= 0)
+        dn, up = g.hf_cell[m], g.hf_nb[m]          # edge up -> dn
+        indeg = np.bincount(dn, minlength=self.N)
+        srt = np.argsort(up, kind="stable")
+        dn_by_up = dn[srt]
+        ptr = np.searchsorted(up[srt], np.arange(self.N + 1))
+        placed = []
+        front = np.flatnonzero(indeg == 0)
+        while front.size:
+            placed.append(front)
+            lens = ptr[front + 1] - ptr[front]
+            tot = int(lens.sum())
+            if tot == 0:
+                break
+            first = np.repeat(ptr[front] - np.concatenate(([0], np.cumsum(lens)[:-1])), lens)
+            reached, cnt = np.unique(dn_by_up[first + np.arange(tot)], return_counts=True)
+            indeg[reached] -= cnt
+            front = reached[indeg[reached] == 0]
+        order = np.concatenate(placed) if placed else np.zeros(0, dtype=np.int64)
+        got = order if order.size == self.N else None
+        self._order[i] = got
+        return got
+
     def _factor(self, i, l):
+        """The factorised system ``I/tau_l + v_l K_i`` of Eq. (13), as an object
+        with ``solve(rhs)``.
+
+        When direction i's upwind graph is acyclic, the system permuted to
+        the graph's topological order is lower triangular, so its LU factors
+        are read off with no fill (L the permuted matrix scaled to a unit
+        diagonal, U its diagonal; SciPy's triangular solve); the permutation
+        is only a fill-free ordering of the same unknowns.  Otherwise (an
+        upwind cycle) the matrix is factorised by ``splu``."""
         key = (i, l)
         lu = self._lu.get(key)
-        if lu is None:
+        if lu is not None:
+            return lu
+        order = self.upwind_order(i)
+        if order is None:
             A = (sp.identity(self.N, format="csc") / self.tau[l] + self.v[l] * self._direction(i)[0]).tocsc()
             lu = spla.splu(A)
             self._lu[key] = lu
-        return lu
+            return lu
+        Kp = self._ordered.get(i)
+        if Kp is None:
+            Kp = self._direction(i)[0].tocsr()[order][:, order].tocsc()
+            if sp.triu(Kp, 1).nnz != 0:
+                raise AssertionError("upwind order does not make K_i lower triangular")
+            self._ordered[i] = Kp
+        return _OrderedSystem(order, Kp, 1.0 / self.tau[l], self.v[l])
 
-    def sweep(self, Tdev, eb_prev, store_e=False, tasks=None, e_prev=None):
+    def sweep(self, Tdev, eb_prev, store_e=False, tasks=None, e_prev=None, e_in=None, eb_dirs=None):
         """One transport pass over every (band, direction) task of Eq. (4).
 
         Returns the moments of the new distribution, its values at the wall
         cells (for the next iteration's wall coupling), the incoming wall
         values that were used, and optionally the full distribution.  With
         ``e_prev`` (N, B, D), the previous distribution, the interior face
-        values are second order (:meth:`second_order_source`)."""
-        e_in = self.incoming(eb_prev)
+        values are second order (:meth:`second_order_source`).
+
+        A pass may be split over several callers by task: ``tasks`` lists the
+        (direction, band) pairs to solve (the moments are then those tasks'
+        terms), ``e_in`` supplies the incoming wall values instead of
+        computing them from ``eb_prev`` (any object indexed as
+        ``e_in[half_faces, band, direction]``), and ``eb_dirs`` lists the
+        directions whose wall-cell values are returned (the last axis of
+        ``eb``)."""
+        if e_in is None:
+            e_in = self.incoming(eb_prev)
         S = self.source()
         NL = np.zeros(self.N)
         E = np.zeros(self.N)
         q = np.zeros((self.N, self.dim))
-        eb_new = np.empty_like(eb_prev)
+        col = {i: k for k, i in enumerate(eb_dirs)} if eb_dirs is not None else None
+        eb_new = np.empty((self.bcells.size, self.B, self.D if col is None else len(col)))
         e_all = np.zeros((self.N, self.B, self.D)) if store_e else None
         todo = tasks if tasks is not None else [(i, l) for i in range(self.D) for l in range(self.B)]
         for (i, l) in todo:
@@ -310,7 +395,7 @@ class OracleSolver:
             NL += self.w[i] * e / self.tau[l]
             E += self.w[i] * e
             q += (self.w[i] * self.v[l] * e)[:, None] * self.s[i][None, :]
-            eb_new[:, l, i] = e[self.bcells]
+            eb_new[:, l, i if col is None else col[i]] = e[self.bcells]
             if store_e:
                 e_all[:, l, i] = e
         return dict(NL=NL, E=E, q=q, eb=eb_new, e_in=e_in, e=e_all)
@@ -361,7 +446,8 @@ class OracleSolver:
         np.add.at(diag, g.hf_cell[th], (kap + k1 * 2.0 * dist) * area[th] / dist)
         L = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                           shape=(self.N, self.N)) + sp.diags(diag)
-        self._lap = spla.splu(L.tocsc())
+        # a symmetric fill-reducing ordering (the operator is symmetric)
+        self._lap = spla.splu(L.tocsc(), permc_spec="MMD_AT_PLUS_A")
         self._lap_matrix = L.tocsr()
         return self._lap
 
@@ -415,7 +501,7 @@ class OracleSolver:
 
     # ---------------------------------------------------------- iteration loop
     def solve(self, scheme=None, tol=None, max_iter=None, n_iter=None, T_init=None, init="tref",
-              store_e=False, verbose=False, order=1):
+              store_e=False, verbose=False, order=1, sweep=None, callback=None):
         """Run the outer iteration.
 
         ``n_iter`` runs exactly that many sweeps (no convergence test);
@@ -424,7 +510,12 @@ class OracleSolver:
         equilibrium with it) instead of T_init / T_ref.  ``order=2`` uses
         second-order upwind face values, each sweep reconstructing from the
         distribution of the sweep before it (none before the first sweep).
+        ``sweep`` replaces :meth:`sweep` (same arguments and result), e.g. by
+        one that splits the pass over processes by task.  ``callback``, if
+        given, is called after every iteration with its number, the new
+        temperature, the kinetic temperature and the sweep's heat flux.
         Returned temperatures are absolute (K)."""
+        sweep = sweep or self.sweep
         if order not in (1, 2):
             raise ValueError(order)
         scheme = scheme or self.p.scheme
@@ -445,7 +536,7 @@ class OracleSolver:
         TL = T
         e_prev = None
         while it < limit:
-            out = self.sweep(T, eb, store_e=store_e or order == 2, e_prev=e_prev)
+            out = sweep(T, eb, store_e=store_e or order == 2, e_prev=e_prev)
             if order == 2:
                 e_prev = out["e"]
             TL = out["NL"] / self.beta
@@ -465,6 +556,8 @@ class OracleSolver:
             eb = out["eb"] + ((Tn - TL)[self.bcells][:, None] * self.C[None, :] / self.W)[:, :, None]
             T = Tn
             it += 1
+            if callback is not None:
+                callback(it, T + self.T_ref, TL + self.T_ref, out["q"])
             if verbose:
                 print(it, r)
             if n_iter is None and r < tol:

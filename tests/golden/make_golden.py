@@ -5,14 +5,15 @@ output file records the command, the problem parameters and the oracle's
 iteration count; values are absolute temperatures (K) and heat fluxes (W/m^2).
 
 Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_converged|
-                                            finfet2d_order2_steps ...]
+                                            finfet2d_order2_steps|cube3d_tasks|finfet3d_tasks|
+                                            cube3d_converged|finfet3d_steps ...]
 
 * ``square``              - the 40x40 in-plane square, sequential to 1e-12
                             (all 1600 cells).
 * ``finfet2d_steps``      - the ~50k-triangle fin, 20 bands, 64 directions:
                             the lattice temperature after sequential iterations
                             1 and 2 from T_ref, on 4096 seeded sample cells.
-* ``finfet2d_converged``  - the same problem converged (sequential, 1e-10),
+* ``finfet2d_converged``  - the same problem converged (sequential, 1e-13),
                             T_L and q on the sample cells.
 * ``finfet2d_order2_steps`` - the same fin with second-order upwind face
                             values: T_L after sequential iterations 2 and 3
@@ -24,10 +25,20 @@ Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_conve
                             sequential iteration from T_ref (walls at
                             equilibrium with T_ref), on 4096 sample cells.
                             Each task is one sparse solve of Eq. (4).
+* ``cube3d_converged``    - the 64^3 cube converged with the synthetic scheme
+                            (1e-12, from the diffusion guess): T_L and q on
+                            the sample cells.
+* ``finfet3d_steps``      - the 1.14M-tet FinFET: T_L after sequential
+                            iterations 1, 2 and 3 from T_ref and q of the
+                            third sweep, on the sample cells.
+
+The last three split every pass over worker processes by direction (one per
+available core; ``PoolSweep``).
 """
 from __future__ import annotations
 
 import json
+import multiprocessing as mp
 import os
 import sys
 import time
@@ -49,6 +60,69 @@ def _write(name, payload):
     with open(path, "w") as f:
         json.dump(payload, f, indent=None, separators=(",", ":"))
     print("wrote", path)
+
+
+# ---------------------------------------------------------------- task pool
+# An oracle pass at the 3D workloads' sizes is thousands of sparse solves.
+# The pool below splits each pass by direction over worker processes (each
+# builds its own OracleSolver of the same problem) and adds up their moments;
+# every solve and every moment term is the oracle's own.  Only the order in
+# which the per-task terms are summed differs from a serial pass (rounding).
+_O = None
+
+
+def _pool_init(name, kwargs):
+    global _O
+    _O = OracleSolver(getattr(W.problems, name)(**kwargs))
+
+
+class _Cols:
+    """Incoming wall values of some directions, indexed like the full
+    (half-face, band, direction) array."""
+
+    def __init__(self, a, dirs):
+        self.a = a
+        self.col = {i: k for k, i in enumerate(dirs)}
+
+    def __getitem__(self, key):
+        h, l, i = key
+        return self.a[h, l, self.col[i]]
+
+
+def _pool_sweep(Tdev, e_in_sub, dirs):
+    tasks = [(i, l) for i in dirs for l in range(_O.B)]
+    r = _O.sweep(Tdev, None, tasks=tasks, e_in=_Cols(e_in_sub, dirs), eb_dirs=dirs)
+    return r["NL"], r["E"], r["q"], r["eb"]
+
+
+class PoolSweep:
+    """Drop-in for ``OracleSolver.sweep`` (first-order passes) that solves
+    the (direction, band) tasks on ``workers`` processes."""
+
+    def __init__(self, o, name, kwargs=None, workers=None):
+        self.o = o
+        workers = workers or max(1, len(os.sched_getaffinity(0)))
+        self.dirs = [list(range(k, o.D, workers)) for k in range(workers)]
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(name, kwargs or {}))
+
+    def __call__(self, Tdev, eb_prev, store_e=False, e_prev=None):
+        if store_e or e_prev is not None:
+            raise ValueError("the pool runs first-order passes without the full distribution")
+        o = self.o
+        e_in = o.incoming(eb_prev)
+        jobs = [(Tdev, np.ascontiguousarray(e_in[:, :, d]), d) for d in self.dirs]
+        NL, E, q = np.zeros(o.N), np.zeros(o.N), np.zeros((o.N, o.dim))
+        eb = np.empty((o.bcells.size, o.B, o.D))
+        for d, (nl, en, qq, ebk) in zip(self.dirs, self.pool.starmap(_pool_sweep, jobs)):
+            NL += nl
+            E += en
+            q += qq
+            eb[:, :, d] = ebk
+        return dict(NL=NL, E=E, q=q, eb=eb, e_in=e_in, e=None)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def square():
@@ -84,14 +158,18 @@ def finfet2d_steps():
 def finfet2d_converged():
     p = W.problems.finfet2d()
     o = OracleSolver(p)
+    pool = PoolSweep(o, "finfet2d")
     idx = _sample(p.n_cells)
     t = time.time()
-    r = o.solve(scheme="sequential", tol=1e-10, verbose=True)
+    r = o.solve(scheme="sequential", tol=1e-13, max_iter=20000, sweep=pool, verbose=True)
+    pool.close()
     _write("finfet2d_converged.json", dict(
-        problem="finfet2d()", scheme="sequential", tol=1e-10, iterations=r["iterations"],
+        problem="finfet2d()", scheme="sequential", tol=1e-13, iterations=r["iterations"],
         converged=r["converged"], seconds=time.time() - t, sample_seed=SAMPLE_SEED,
+        command="python tests/golden/make_golden.py finfet2d_converged",
         cells=idx.tolist(), T=r["T"][idx].tolist(), q=r["q"][idx].tolist(),
-        T_max=float(r["T"].max()), energy_imbalance=r["energy_imbalance"]))
+        T_max=float(r["T"].max()), q_max=float(np.abs(r["q"]).max()),
+        energy_imbalance=r["energy_imbalance"]))
 
 
 def finfet2d_order2_steps():
@@ -136,6 +214,53 @@ def cube3d_tasks():
 def finfet3d_tasks():
     p = W.problems.finfet3d()
     _tasks("finfet3d", p, [(0, 0), (p.n_dirs // 2, 21), (p.n_dirs - 1, p.n_bands - 1)])
+
+
+def cube3d_converged():
+    """The 64^3 cube, synthetic scheme to 1e-12 from the diffusion (Fourier)
+    initial guess (the oracle's correction is an exact sparse LU solve of
+    Eq. (10)); the fixed point does not depend on the start."""
+    p = W.problems.cube3d()
+    o = OracleSolver(p)
+    pool = PoolSweep(o, "cube3d")
+    idx = _sample(p.n_cells)
+    t = time.time()
+    r = o.solve(scheme="synthetic", tol=1e-12, max_iter=5000, init="fourier", sweep=pool, verbose=True)
+    pool.close()
+    _write("cube3d_converged.json", dict(
+        problem="cube3d()", scheme="synthetic", init="fourier", tol=1e-12, iterations=r["iterations"],
+        converged=r["converged"], seconds=time.time() - t, sample_seed=SAMPLE_SEED,
+        command="python tests/golden/make_golden.py cube3d_converged",
+        cells=idx.tolist(), T=r["T"][idx].tolist(), q=r["q"][idx].tolist(),
+        T_max=float(r["T"].max()), T_min=float(r["T"].min()), q_max=float(np.abs(r["q"]).max()),
+        energy_imbalance=r["energy_imbalance"], residuals=r["residuals"]))
+
+
+def finfet3d_steps():
+    """The 1.14M-tet FinFET, sequential iterations 1, 2 and 3 from T_ref:
+    T_L after each and the heat flux of the third sweep, on the sample
+    cells.  From the second iteration on, the diffuse, specular and
+    partially specular walls feed in the previous sweep's values."""
+    p = W.problems.finfet3d()
+    o = OracleSolver(p)
+    pool = PoolSweep(o, "finfet3d")
+    idx = _sample(p.n_cells)
+    out = dict(problem="finfet3d()", scheme="sequential", sample_seed=SAMPLE_SEED,
+               command="python tests/golden/make_golden.py finfet3d_steps", cells=idx.tolist())
+    t = time.time()
+
+    def keep(it, T, TL, q):
+        out[f"T_iter{it}"] = T[idx].tolist()
+        out[f"T_iter{it}_max_dev"] = float(np.abs(T - p.T_ref).max())
+        out[f"seconds_iter{it}"] = time.time() - t
+        if it == 3:
+            out["q_iter3"] = q[idx].tolist()
+            out["q_iter3_max"] = float(np.abs(q).max())
+        print("iteration", it, time.time() - t, flush=True)
+
+    o.solve(scheme="sequential", n_iter=3, sweep=pool, callback=keep)
+    pool.close()
+    _write("finfet3d_steps.json", out)
 
 
 if __name__ == "__main__":
