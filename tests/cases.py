@@ -34,6 +34,23 @@ def cube_hex():
     return p
 
 
+def tets_cyclic():
+    """A twisted annulus of tetrahedra (workloads.mesh.twisted_ring_tets):
+    conforming and untangled, yet the upwind graph of many directions has
+    cycles around the ring (checked on the CPU in test_oracle_tasks), so the
+    sweep lags faces to break them.  Inner wall thermalizing at 302 K, outer
+    at 299 K, diffuse bottom, partially specular top, a uniform heat source."""
+    from workloads import mesh as M, quadrature as Qd, spectra as S
+    from workloads.problems import Problem
+    m = M.twisted_ring_tets()
+    C, v, tau = S.silicon_like(2, 11)
+    s, w = Qd.gl_azimuth(4, 8)
+    bcs = [Boundary(1, THERMALIZING, 302.0), Boundary(2, THERMALIZING, 299.0), Boundary(3, DIFFUSE),
+           Boundary(4, PARTIAL, 0.0, 0.5)]
+    Q = np.full(m.n_cells, 1e17)
+    return Problem("tets_cyclic", m, C, v, tau, s, w, bcs, Q, 300.0, scheme="sequential", tol=1e-10)
+
+
 CASES = {"square_mixed": square_mixed, "fin2d_mixed": fin2d_mixed, "fin3d_tets": fin3d_tets,
          "cube_hex": cube_hex}
 

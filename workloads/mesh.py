@@ -332,3 +332,44 @@ def finfet3d_tets(h: float = 2e-9, seed: int = 2607032264, jitter: float = 0.1,
                 meta=dict(kind="finfet3d_tets", h=h, seed=seed, jitter=jitter, sub_x=sub_x,
                           sub_y=sub_y, sub_z=sub_z, fin_w=fin_w, fin_h=fin_h,
                           fin_cell=fin_cell))
+
+
+def twisted_ring_tets(n_ring: int = 12, n_rad: int = 2, n_ax: int = 2, r0: float = 20e-9, r1: float = 40e-9,
+                      H: float = 20e-9, twist: float = 0.5) -> Mesh:
+    """An annulus ``r0 <= r <= r1``, ``0 <= z <= H`` whose node layers are
+    turned about the z axis in proportion to height (``twist`` radians from
+    bottom to top), meshed by the Kuhn split of its (ring, radius, height)
+    index grid.  The faces between ring neighbours lean along the ring, so a
+    direction with a z component crosses them all in the same turning sense:
+    the upwind graph of such directions has cycles around the ring, while the
+    mesh stays conforming and untangled.
+
+    Tags: 1 inner wall (r = r0), 2 outer wall (r = r1), 3 bottom (z = 0),
+    4 top (z = H).
+    """
+    def nid(i, j, k):
+        return (k * (n_rad + 1) + j) * n_ring + (i % n_ring)
+
+    kk, jj, ii = np.meshgrid(np.arange(n_ax + 1), np.arange(n_rad + 1), np.arange(n_ring), indexing="ij")
+    th = 2.0 * np.pi * ii / n_ring + twist * kk / n_ax
+    r = r0 + (r1 - r0) * jj / n_rad
+    nodes = np.stack([(r * np.cos(th)).ravel(), (r * np.sin(th)).ravel(), (H * kk / n_ax).ravel()], axis=1)
+    I, J, K = np.meshgrid(np.arange(n_ring), np.arange(n_rad), np.arange(n_ax), indexing="ij")
+    I, J, K = I.ravel(), J.ravel(), K.ravel()
+    tets = np.stack([np.stack([nid(I + p[0], J + p[1], K + p[2]) for p in path], 1) for path in _KUHN], 1)
+    tets = tets.reshape(-1, 4).astype(np.int64)
+    loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    faces = np.sort(tets[:, loc].reshape(-1, 3), axis=1)
+    _, idx, cnt = np.unique(faces, axis=0, return_index=True, return_counts=True)
+    bfaces = faces[idx[cnt == 1]]
+    gj = (bfaces // n_ring) % (n_rad + 1)
+    gk = bfaces // (n_ring * (n_rad + 1))
+    tags = np.zeros(bfaces.shape[0], dtype=np.int32)
+    tags[np.all(gj == 0, axis=1)] = 1
+    tags[np.all(gj == n_rad, axis=1)] = 2
+    tags[np.all(gk == 0, axis=1)] = 3
+    tags[np.all(gk == n_ax, axis=1)] = 4
+    assert np.all(tags > 0), "untagged boundary face in generator"
+    return Mesh(3, nodes, TET, tets, bfaces.astype(np.int64), tags,
+                meta=dict(kind="twisted_ring_tets", n_ring=n_ring, n_rad=n_rad, n_ax=n_ax, r0=r0, r1=r1, H=H,
+                          twist=twist))
