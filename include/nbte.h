@@ -342,27 +342,49 @@ int nbte_server_destroy(nbte_server* server);
  * framework's memory pool or under a fixed device-memory budget, or a
  * real-time loop where an allocation may block or fail.  It is a one-level
  * variant of the CG kernel that solves the synthetic correction.
- *   n                 rows, 1 <= n <= 262144 (larger n: NBTE_ERR_ARG).
+ *   n                 rows, 0 <= n <= 262144 (larger n: NBTE_ERR_ARG);
+ *                     n = 0 only does the per-device set-up described below
+ *                     (the other arguments are then ignored).
  *   row_ptr, col, val the matrix in CSR form, int32 indices, FP64 values,
- *                     DEVICE pointers owned by the caller; every row holds
- *                     its diagonal entry.
+ *                     DEVICE pointers owned by the caller; every row holds a
+ *                     positive diagonal entry (else NBTE_ERR_ARG).
  *   rhs, x            DEVICE arrays of n doubles owned by the caller; x is
  *                     overwritten with the solution (start value 0).
- *   tol, max_iter     stop when |r|_2 <= tol |rhs|_2, at most max_iter steps.
- *   iterations, residual  host outputs (may be NULL).
+ *   tol, max_iter     stop when |r|_2 <= tol |rhs|_2 (tested on the device
+ *                     as r.r <= tol^2 rhs.rhs), at most max_iter steps.
+ *   iterations, residual  host outputs (may be NULL); residual is
+ *                     |r|_2 / |rhs|_2 of the last iterate.
  *   cuda_stream       cudaStream_t as void* (NULL = legacy default stream);
  *                     the call returns after the solve has finished on it.
- * Working vectors live in one fixed array of about 8 MB in the library's
- * device image: every GPU that loads the library holds it until the process
- * exits.  All calls on a device share that array, so calls that overlap on
- * the GPU (other streams, other host threads) race; serialise them.  The
- * first call on each device looks up the array's device address with that
- * device current; make that first call outside any CUDA stream capture.
+ * Working vectors live in one fixed array of about 10 MB in the library's
+ * device code.  With lazy module loading (the CUDA default) the driver
+ * allocates that array on a device when the first call there loads that
+ * code, not when the library is loaded: make a first call (n = 0 suffices)
+ * on each device before a memory budget applies; calls after it allocate
+ * nothing.  The array then stays allocated on that device until the process
+ * exits.  The first call on each device also looks up the array's device
+ * address with that device current; make it outside any CUDA stream
+ * capture.  All calls on a device share the array and its contents, so calls
+ * that overlap on the GPU (other streams, other host threads) race;
+ * serialise them.
  * Returns NBTE_OK, NBTE_ERR_ARG, NBTE_ERR_NOT_CONVERGED (x holds the last
  * iterate), NBTE_ERR_DEVICE_TIMEOUT or NBTE_ERR_CUDA.                      */
 int nbte_laplacian_solve_noalloc(int n, const int32_t* row_ptr, const int32_t* col, const double* val,
                                  const double* rhs, double* x, double tol, int max_iter, int32_t* iterations,
                                  double* residual, void* cuda_stream);
+
+/* ------------------------------------------------------------ diagnostics --
+ * nbte_set_wait_limit: every device-side wait of the library is bounded (the
+ * sweep's copy pipeline, the CG grid barriers, the allocation-free solve's
+ * barrier); a wait that gives up sets an error word, its kernel returns, and
+ * the call reports NBTE_ERR_DEVICE_TIMEOUT.  polls > 0 makes every such wait
+ * give up after that many polls, for the launches made after this call in
+ * the whole process; polls <= 0 restores each wait's default (about a
+ * second).  For testing the timeout paths: with a small limit the solves
+ * that follow fail with NBTE_ERR_DEVICE_TIMEOUT.  After a timeout the
+ * solver's iterate is incomplete: the next nbte_solve_steady starts again
+ * from its initial state even when warm is set.  No paper counterpart.   */
+int nbte_set_wait_limit(int64_t polls);
 
 /* Message of the last failing call on this thread (library-owned string). */
 const char* nbte_last_error(void);

@@ -8,6 +8,7 @@ import hashlib
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -38,18 +39,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     dg = _digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dg:
         return LIB
-    objs = []
     common = ["-O3", "-std=c++17", "-I", INCLUDE, "-Xcompiler", "-fPIC", "-lineinfo"]
-    for src in SOURCES:
+
+    def compile_one(src):
         obj = os.path.join(BUILD, src + ".o")
         cmd = [NVCC, *common, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
-        if src.endswith(".cu"):
-            cmd += ["-Xptxas", "-v"] if verbose else []
-        else:
-            cmd += ["-x", "cu"] if False else []
+        if src.endswith(".cu") and verbose:
+            cmd += ["-Xptxas", "-v"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        return src, obj, cmd, r
+
+    # the translation units are independent: compile them side by side
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(compile_one, SOURCES))
+    objs = []
+    for src, obj, cmd, r in results:
         if verbose:
             print(" ".join(cmd))
-        r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         if verbose and r.stderr:

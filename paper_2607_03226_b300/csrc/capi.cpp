@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cmath>
@@ -20,6 +21,7 @@
 #include <thread>
 #include <vector>
 
+#include "iteration_monitor.h"
 #include "kernels.h"
 #include "nbte_internal.h"
 
@@ -28,6 +30,13 @@ using namespace nbte;
 namespace nbte {
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+// poll limit of every bounded device wait set with nbte_set_wait_limit (0 =
+// each wait's own default)
+static std::atomic<unsigned long long> g_wait_limit{0};
+unsigned long long wait_limit_or(unsigned long long dflt) {
+  const unsigned long long v = g_wait_limit.load(std::memory_order_relaxed);
+  return v > 0 ? v : dflt;
+}
 }  // namespace nbte
 
 #define NBTE_CK(call)                                                                               \
@@ -127,11 +136,10 @@ struct nbte_solver {
   std::vector<BC> bcs;
   bool bcs_set = false;
   // heat source: caller order in pinned host memory (what the caller set),
-  // internal order on the host on demand (Q) and on the device (Qd)
+  // internal order on the device (Qd)
   double* h_qc = nullptr;   // pinned, or ordinary memory where pinning is unavailable
   bool h_qc_pinned = false;
-  int64_t q_dev_version = -1, q_host_version = -1;
-  std::vector<double> Q;   // internal order, valid for q_host_version
+  int64_t q_dev_version = -1;
   int64_t version_plan = 0, version_bands = 0, version_q = 0;
 
   // ---- plan (depends on quadrature and walls)
@@ -195,7 +203,11 @@ struct nbte_solver {
   cudaGraphExec_t graph = nullptr;
   std::string graph_key;
   double last_energy_imbalance = 0;
-  std::vector<double> wall_heat_by_face;
+  // wall heat per tag of the last output sweep, computed on the device:
+  // tag_list[t] is the tag of index t, wall_heat_by_tag[t] its heat
+  std::vector<int32_t> tag_list;
+  std::vector<double> wall_heat_by_tag;
+  DBuf wf_tagidx, tag_therm, balance, fbc;
 
   ~nbte_solver() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -239,7 +251,8 @@ size_t device_bytes(const nbte_solver* S) {
                        &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell, &S->cg_blk_agg,
                        &S->cg_Ainv, &S->L_ecol, &S->L_eval,
                        &S->L_diag, &S->L_dinv, &S->o2_e, &S->o2_src, &S->o2_grad, &S->rc_nb, &S->rc_twin,
-                       &S->rc_AnV, &S->rc_a, &S->rc_gw, &S->rc_rf};
+                       &S->rc_AnV, &S->rc_a, &S->rc_gw, &S->rc_rf, &S->wf_tagidx, &S->tag_therm, &S->balance,
+                       &S->fbc};
   size_t t = 0;
   for (auto* b : all) t += b->bytes;
   return t;
@@ -311,6 +324,24 @@ int ensure_plan(nbte_solver* S) {
   S->n_dbf = (int64_t)P.dif_ptr.size() - 1;
   S->n_wf = (int64_t)P.wf_tag.size();
   S->wf_tag_h = P.wf_tag;
+  {
+    // wall faces by tag index, and which tags are thermalizing (the energy
+    // balance and the per-tag wall heat are summed on the device)
+    std::vector<int32_t> tags(P.wf_tag.begin(), P.wf_tag.end());
+    std::sort(tags.begin(), tags.end());
+    tags.erase(std::unique(tags.begin(), tags.end()), tags.end());
+    std::vector<int32_t> idx(P.wf_tag.size()), th(tags.size(), 0);
+    for (size_t f = 0; f < P.wf_tag.size(); ++f)
+      idx[f] = (int32_t)(std::lower_bound(tags.begin(), tags.end(), P.wf_tag[f]) - tags.begin());
+    for (const BC& b : S->bcs) {
+      auto it = std::lower_bound(tags.begin(), tags.end(), b.tag);
+      if (it != tags.end() && *it == b.tag && b.type == NBTE_THERMALIZING) th[it - tags.begin()] = 1;
+    }
+    NBTE_CK(upload(S->wf_tagidx, idx));
+    NBTE_CK(upload(S->tag_therm, th));
+    NBTE_CK(S->balance.alloc((3 + tags.size()) * 8));
+    S->tag_list = tags;
+  }
   S->lagged = P.lagged_faces;
   S->total_levels = P.total_levels;
   S->max_levels = P.max_levels;
@@ -840,18 +871,6 @@ int ensure_q(nbte_solver* S) {
   return NBTE_OK;
 }
 
-// host heat source in internal order (energy balance, diffusion guess)
-const std::vector<double>& host_q(nbte_solver* S) {
-  const int64_t N = S->mesh->m.n_cells;
-  if (S->q_host_version != S->version_q || (int64_t)S->Q.size() != N) {
-    S->Q.assign(N, 0.0);
-    if (S->h_qc)
-      for (int64_t c = 0; c < N; ++c) S->Q[c] = S->h_qc[S->mesh->m.perm[c]];
-    S->q_host_version = S->version_q;
-  }
-  return S->Q;
-}
-
 int ensure_laplacian(nbte_solver* S) {
   const int64_t want = S->version_bands * 1000003 + S->version_plan;
   if (S->lap_built == want && S->L_diag.p) return NBTE_OK;
@@ -877,6 +896,10 @@ int ensure_laplacian(nbte_solver* S) {
   // faces of g_f (T_wall - T_ref), per internal cell
   S->h_fourier_bc.resize(m.n_cells);
   for (int64_t c = 0; c < m.n_cells; ++c) S->h_fourier_bc[c] = L.bc_gT[c] - S->T_ref * L.bc_g[c];
+  {
+    DeviceGuard g0(S->device);
+    NBTE_CK(upload(S->fbc, S->h_fourier_bc));
+  }
   const int64_t N = m.n_cells;
   // ---- coarse space: geometric aggregates, rows reordered so each
   // aggregate's cells are contiguous, blocks owning whole aggregates
@@ -1085,6 +1108,7 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.gring_stride = S->gring_stride;
   a.accE = S->accE.as<double>();
   a.accQ = S->accQ.as<double>();
+  a.wait_limit = wait_limit_or(kSweepWaitPolls);
   return a;
 }
 
@@ -1171,6 +1195,7 @@ CGArgs cg_args(nbte_solver* S, double tol, int max_it) {
   a.slots = S->cg_slots.as<CGSlot>();
   a.bar = S->cg_bar.as<unsigned long long>();
   a.err = S->cg_err.as<int32_t>();
+  a.spin_limit = wait_limit_or(kCgSpinPolls);
   a.tol = tol;
   a.max_it = max_it;
   a.it_out = S->cg_it.as<int32_t>();
@@ -1292,10 +1317,8 @@ int init_state(nbte_solver* S, const nbte_solve_opts& o) {
     // diffusion initial guess: L T' = Qdot V + sum_thermalizing g_f T'_w,
     // the synthetic correction's operator with the wall temperatures as
     // Dirichlet data, solved with the same CG to FP64 accuracy
-    std::vector<double> rhs(N);
-    const std::vector<double>& Qh = host_q(S);
-    for (int64_t c = 0; c < N; ++c) rhs[c] = Qh[c] * m.V[c] + S->h_fourier_bc[c];
-    NBTE_CK(cudaMemcpyAsync(S->rhs.p, rhs.data(), N * 8, cudaMemcpyHostToDevice, st));
+    NBTE_CK(launch_fourier_rhs(S->rhs.as<double>(), S->Qd.as<double>(), S->Vd.as<double>(), S->fbc.as<double>(), N,
+                               st));
     NBTE_CK(cudaMemsetAsync(S->cg_x.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->cg_err.p, 0, 4, st));
     NBTE_CK(launch_cg(cg_args(S, 1e-12, 20000), false, S->cg_grid, S->cg_threads, cg_smem_for(S, false), st));
@@ -1426,13 +1449,10 @@ struct Run {
   int cg_max = 5000;
   bool fixed = false;
   int limit = 0;
-  int it = 0;
+  int it = 0;                  // iterations enqueued
   double r = INFINITY;
   int status = NBTE_OK;
-  double best_r = INFINITY;
-  int it_best = 0;
-  bool floor_reached = false;
-  bool done = false;
+  IterationMonitor mon;        // stopping rule (iteration_monitor.h)
   int64_t kernels = 0;
   double sweep_ms = 0.0;
   int64_t sweeps_timed = 0;
@@ -1444,9 +1464,12 @@ struct Run {
   }
   // after an iteration's residual words reached the host: true to stop
   bool check() {
+    // a wait that gave up leaves this iteration's fields incomplete: the
+    // next solve starts from its initial state again (not warm)
     if (S->h_res[2] != 0) {
       status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
       zero_now(S->res.p, 32, S->stream);
+      S->have_state = false;
       return true;
     }
     if (S->h_misc[0] != 0 && o.scheme != 0) {
@@ -1454,32 +1477,27 @@ struct Run {
       zero_now(S->cg_err.p, 16, S->stream);
       zero_now(S->cg_slots.p, S->cg_slots.bytes, S->stream);
       zero_now(S->cg_bar.p, 16, S->stream);
+      S->have_state = false;
       return true;
     }
     double dmax, tmax;
     std::memcpy(&dmax, &S->h_res[0], 8);
     std::memcpy(&tmax, &S->h_res[1], 8);
-    if (!std::isfinite(dmax) || !std::isfinite(tmax)) {
-      status = fail(NBTE_ERR_DIVERGED, "non-finite temperature: the iteration diverged");
-      r = INFINITY;
+    mon.it = it - 1;   // the words are those of iteration `it`
+    const IterationMonitor::Verdict v = mon.step(dmax, tmax);
+    r = mon.r;
+    if (v == IterationMonitor::DIVERGED) {
+      status = fail(NBTE_ERR_DIVERGED, std::isfinite(r) ? "the temperature increment grew without bound: the iteration diverged"
+                                                          : "non-finite temperature: the iteration diverged");
+      S->have_state = false;
       return true;
     }
-    r = dmax / std::max(tmax, 1e-300);   // the convergence measure (relative increment of T')
-    if (tmax == 0.0 && dmax == 0.0) r = 0.0;
-    if (!fixed && r < o.tol) return true;
-    // FP32 sweep: the relative increment bottoms out at the rounding floor;
-    // stop once it is below 1e-5 and has not dropped by 10% in 200 iterations
-    if (S->prec && !fixed) {
-      if (r < 0.9 * best_r) {
-        best_r = r;
-        it_best = it;
-      }
-      if (best_r < 1e-5 && it - it_best >= 200) {
-        floor_reached = true;
-        return true;
-      }
-    }
-    return it >= limit;
+    return v != IterationMonitor::CONTINUE;
+  }
+  // the solve stopped where its options say it should (tolerance or floor
+  // reached, or the fixed iteration count done)
+  bool finished_ok() const {
+    return fixed || mon.last == IterationMonitor::CONVERGED || mon.last == IterationMonitor::FLOOR;
   }
 };
 
@@ -1491,6 +1509,11 @@ int run_begin(Run& run, nbte_solver* S, const nbte_solve_opts& o) {
   run.cg_max = o.cg_max_iter > 0 ? o.cg_max_iter : 5000;
   run.fixed = o.n_iter > 0;
   run.limit = run.fixed ? o.n_iter : o.max_iter;
+  run.mon = IterationMonitor{};
+  run.mon.tol = o.tol;
+  run.mon.limit = run.limit;
+  run.mon.fixed = run.fixed;
+  run.mon.fp32 = S->prec != 0;
   cudaStream_t st = S->stream;
   if (!(o.warm && S->have_state)) {
     run.kernels += 2;
@@ -1517,11 +1540,11 @@ int run_finish(Run& run, nbte_solve_info* info) {
   cudaStream_t st = S->stream;
   run.t1 = std::chrono::steady_clock::now();
   int status = run.status;
-  if (status == NBTE_OK && !run.fixed && !(run.r < o.tol) && !run.floor_reached) status = NBTE_ERR_NOT_CONVERGED;
+  if (status == NBTE_OK && !run.finished_ok()) status = NBTE_ERR_NOT_CONVERGED;
   S->have_results = status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED;
   S->have_outputs = false;
   if ((status == NBTE_OK || status == NBTE_ERR_NOT_CONVERGED) && !o.skip_outputs) {
-    run.kernels += 4;
+    run.kernels += 5;
     NBTE_CK(cudaMemsetAsync(S->accE.p, 0, N * 8, st));
     NBTE_CK(cudaMemsetAsync(S->accQ.p, 0, (size_t)N * m.dim * 8, st));
     launch_fill_srcTQ<R>(S->srcTQ_fin.as<R>(), S->Tprev.as<double>(), S->Qd.as<double>(), (int)N, st);
@@ -1544,24 +1567,16 @@ int run_finish(Run& run, nbte_solve_info* info) {
     wh.heat = S->heat.as<double>();
     launch_wall_heat<R>(wh, st);
     NBTE_CK(cudaGetLastError());
-    S->wall_heat_by_face.assign(S->n_wf, 0.0);
-    NBTE_CK(cudaMemcpyAsync(S->wall_heat_by_face.data(), S->heat.p, S->n_wf * 8, cudaMemcpyDeviceToHost, st));
+    // wall heat per tag and the energy balance (FP64, on the device)
+    const int n_tags = (int)S->tag_list.size();
+    NBTE_CK(launch_wall_balance(S->heat.as<double>(), S->wf_tagidx.as<int32_t>(), S->tag_therm.as<int32_t>(), n_tags,
+                                S->n_wf, S->Qd.as<double>(), S->Vd.as<double>(), N, S->balance.as<double>(), st));
+    std::vector<double> bal(3 + n_tags, 0.0);
+    NBTE_CK(cudaMemcpyAsync(bal.data(), S->balance.p, bal.size() * 8, cudaMemcpyDeviceToHost, st));
     NBTE_CK(cudaStreamSynchronize(st));
     S->have_outputs = true;
-    // energy balance (FP64)
-    std::map<int32_t, int> type;
-    for (auto& b : S->bcs) type[b.tag] = b.type;
-    double therm = 0, absall = 0, qtot = 0, qabs = 0;
-    for (int64_t f = 0; f < S->n_wf; ++f) {
-      absall += std::fabs(S->wall_heat_by_face[f]);
-      if (type[S->wf_tag_h[f]] == NBTE_THERMALIZING) therm += S->wall_heat_by_face[f];
-    }
-    const std::vector<double>& Qh = host_q(S);
-    for (int64_t c = 0; c < N; ++c) {
-      qtot += Qh[c] * m.V[c];
-      qabs += std::fabs(Qh[c] * m.V[c]);
-    }
-    S->last_energy_imbalance = std::fabs(therm - qtot) / std::max(std::max(qabs, absall), 1e-300);
+    S->last_energy_imbalance = bal[0];
+    S->wall_heat_by_tag.assign(bal.begin() + 3, bal.end());
   }
   if (info) {
     info->iterations = run.it;
@@ -1591,7 +1606,8 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   bool use_graph = o.use_graph != 0;
   const std::string gkey = S->layout_key + "/" + std::to_string(scheme) + "/" + std::to_string(run.cg_tol) + "/" +
                            std::to_string(run.cg_max) + "/" + std::to_string(S->lap_built) + "/" +
-                           std::to_string(S->cg_part_key) + "/" + std::to_string((long long)(intptr_t)st);
+                           std::to_string(S->cg_part_key) + "/" + std::to_string((long long)(intptr_t)st) + "/" +
+                           std::to_string(wait_limit_or(0));
   if (use_graph && (S->graph == nullptr || S->graph_key != gkey)) {
     drop_graph(S);
     cudaGraph_t gr = nullptr;
@@ -2069,6 +2085,11 @@ void nbte_server::work_loop() {
 extern "C" {
 
 const char* nbte_last_error(void) { return g_err.c_str(); }
+
+int nbte_set_wait_limit(int64_t polls) {
+  g_wait_limit.store(polls > 0 ? (unsigned long long)polls : 0ull, std::memory_order_relaxed);
+  return NBTE_OK;
+}
 const char* nbte_version(void) { return "nanobte-b300 1.0 (sm_103a)"; }
 
 int nbte_mesh_create(int dim, int64_t n_nodes, const double* xyz, int cell_type, int64_t n_cells,
@@ -2501,12 +2522,10 @@ int nbte_get_wall_heat(const nbte_solver* S, int32_t tag, double* out) {
   if (!S || !out) return fail(NBTE_ERR_ARG, "null argument");
   if (!S->have_results) return fail(NBTE_ERR_STATE, "no results: call nbte_solve_steady first");
   if (!S->have_outputs) return fail(NBTE_ERR_STATE, "the last solve skipped its outputs");
-  double h = 0;
-  bool found = false;
-  for (size_t f = 0; f < S->wall_heat_by_face.size(); ++f)
-    if (S->wf_tag_h[f] == tag) { h += S->wall_heat_by_face[f]; found = true; }
-  if (!found) return fail(NBTE_ERR_ARG, "no boundary face carries tag " + std::to_string(tag));
-  *out = h;
+  auto it = std::lower_bound(S->tag_list.begin(), S->tag_list.end(), tag);
+  if (it == S->tag_list.end() || *it != tag || S->wall_heat_by_tag.size() != S->tag_list.size())
+    return fail(NBTE_ERR_ARG, "no boundary face carries tag " + std::to_string(tag));
+  *out = S->wall_heat_by_tag[it - S->tag_list.begin()];
   return NBTE_OK;
 }
 

@@ -336,7 +336,6 @@ cudaError_t launch_to_caller(double* dst, const double* src, const int32_t* perm
 // one thread, block sums go through shared memory to one warp per value, and
 // with a loose tolerance the coarse preconditioner runs in FP32.
 namespace {
-constexpr unsigned long long kSpinLimit = 1ull << 24;   // polls of the barrier word before giving up (seconds)
 
 __device__ __forceinline__ double warp_sum(double s) {
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -358,8 +357,8 @@ __device__ __forceinline__ float warp_sumf(float s) {
 // their reciprocals while it waits (work off the critical path).
 template <int NV>
 __device__ bool grid_reduce(const double* v, double* tot, double* red_s, CGSlot* slots, unsigned long long* bar,
-                            unsigned gen, int32_t* err, int blk, unsigned nb, double* inv = nullptr,
-                            int n_inv = 0) {
+                            unsigned gen, int32_t* err, int blk, unsigned nb, unsigned long long spin_limit,
+                            double* inv = nullptr, int n_inv = 0) {
   static_assert(NV >= 0 && NV <= 3, "a slot carries up to three sums");
   __shared__ double s_tot[3];
   __shared__ int s_abort;
@@ -384,7 +383,7 @@ __device__ bool grid_reduce(const double* v, double* tot, double* red_s, CGSlot*
     volatile unsigned long long* vb = bar;
     unsigned long long spins = 0;
     while (*vb < target) {
-      if (++spins > kSpinLimit) {
+      if (++spins > spin_limit) {
         atomicExch(err, (int32_t)DEV_BARRIER_TIMEOUT);
         abort = 1;
         break;
@@ -591,7 +590,7 @@ __device__ __forceinline__ void cg_body(const CGArgs& a, const int blk, const un
     v3[1] = fma(x[l], qx, v3[1]);
     v3[2] = fma(b, b, v3[2]);
   }
-  if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err, blk, nb)) return;
+  if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err, blk, nb, a.spin_limit)) return;
   if (tid == 0) {
     const double th = t3[1] > 0.0 ? t3[0] / t3[1] : 0.0;
     s_scal[0] = isfinite(th) ? th : 0.0;
@@ -609,7 +608,7 @@ __device__ __forceinline__ void cg_body(const CGArgs& a, const int blk, const un
   }
   __syncthreads();
   restrict_own(rcx);
-  if (grid_reduce<1>(v1, t1, red_s, a.slots, a.bar, gen++, a.err, blk, nb)) return;
+  if (grid_reduce<1>(v1, t1, red_s, a.slots, a.bar, gen++, a.err, blk, nb, a.spin_limit)) return;
   double rho = t1[0];
   const double stop = a.tol * a.tol * bb;
   int it = 0;
@@ -617,7 +616,7 @@ __device__ __forceinline__ void cg_body(const CGArgs& a, const int blk, const un
     for (int k = tid; k < Nc; k += T) rc_s[k] = __ldcg(rcx + k);
     __syncthreads();
     precondition();
-    if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err, blk, nb)) return;
+    if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err, blk, nb, a.spin_limit)) return;
     // s_scal[2], s_scal[3]: 1/gamma and 1/alpha of the previous step (thread 0)
     while (true) {
       // -- w = A u, (r,u), (w,u), (r,r), aggregate sums of w
@@ -639,7 +638,7 @@ __device__ __forceinline__ void cg_body(const CGArgs& a, const int blk, const un
       }
       __syncthreads();
       restrict_own(rw);
-      if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err, blk, nb)) return;
+      if (grid_reduce<3>(v3, t3, red_s, a.slots, a.bar, gen++, a.err, blk, nb, a.spin_limit)) return;
       const double gamma = t3[0], delta = t3[1];
       rho = t3[2];
       if (!(rho > stop) || it >= a.max_it) break;
@@ -682,7 +681,7 @@ __device__ __forceinline__ void cg_body(const CGArgs& a, const int blk, const un
         s_scal[3] = alpha;
       }
       ++it;
-      if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err, blk, nb, s_scal + 2, 2)) return;
+      if (grid_reduce<0>(nullptr, nullptr, red_s, a.slots, a.bar, gen++, a.err, blk, nb, a.spin_limit, s_scal + 2, 2)) return;
     }
   }
   // every read of the previous correction happened before the first barrier
@@ -788,6 +787,73 @@ template <typename R>
 void launch_wall_heat(const WallHeatArgs<R>& a, cudaStream_t st) {
   if (a.n_wf == 0) return;
   wall_heat_kernel<R><<<(unsigned)((a.n_wf + 127) / 128), 128, 0, st>>>(a);
+}
+
+// ============================================================================ balance
+// One block; every sum is a per-thread strided sum followed by a fixed tree
+// over the block, so the result does not depend on scheduling.
+constexpr int kBalThreads = 512;
+
+__device__ double block_sum_fixed(double x, double* sh) {
+  sh[threadIdx.x] = x;
+  __syncthreads();
+  for (int o = kBalThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double t = sh[0];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(kBalThreads)
+wall_balance_kernel(const double* heat, const int32_t* tag_of, const int32_t* therm, int n_tags, int64_t n_wf,
+                    const double* Q, const double* V, int64_t N, double* out) {
+  __shared__ double sh[kBalThreads];
+  double habs = 0.0;
+  for (int64_t f = threadIdx.x; f < n_wf; f += kBalThreads) habs += fabs(heat[f]);
+  const double absall = block_sum_fixed(habs, sh);
+  double therm_sum = 0.0;
+  for (int t = 0; t < n_tags; ++t) {
+    double h = 0.0;
+    for (int64_t f = threadIdx.x; f < n_wf; f += kBalThreads)
+      if (tag_of[f] == t) h += heat[f];
+    const double tot = block_sum_fixed(h, sh);
+    if (therm[t]) therm_sum += tot;
+    if (threadIdx.x == 0) out[3 + t] = tot;
+  }
+  double q = 0.0, qa = 0.0;
+  for (int64_t c = threadIdx.x; c < N; c += kBalThreads) {
+    const double x = Q[c] * V[c];
+    q += x;
+    qa += fabs(x);
+  }
+  const double qtot = block_sum_fixed(q, sh);
+  const double qabs = block_sum_fixed(qa, sh);
+  if (threadIdx.x == 0) {
+    out[0] = fabs(therm_sum - qtot) / fmax(fmax(qabs, absall), 1e-300);
+    out[1] = therm_sum;
+    out[2] = qtot;
+  }
+}
+
+cudaError_t launch_wall_balance(const double* heat, const int32_t* tag_of, const int32_t* therm, int n_tags,
+                                int64_t n_wf, const double* Q, const double* V, int64_t N, double* out,
+                                cudaStream_t st) {
+  wall_balance_kernel<<<1, kBalThreads, 0, st>>>(heat, tag_of, therm, n_tags, n_wf, Q, V, N, out);
+  return cudaGetLastError();
+}
+
+__global__ void fourier_rhs_kernel(double* rhs, const double* Q, const double* V, const double* bc, int64_t N) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c < N) rhs[c] = fma(Q[c], V[c], bc[c]);
+}
+
+cudaError_t launch_fourier_rhs(double* rhs, const double* Q, const double* V, const double* bc, int64_t N,
+                               cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  fourier_rhs_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rhs, Q, V, bc, N);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- instantiations

@@ -165,11 +165,15 @@ struct CGArgs {
   CGSlot* slots;                 // [grid]
   unsigned long long* bar;       // barrier counter (only grows)
   int32_t* err;
+  unsigned long long spin_limit; // polls of the barrier word before giving up (kCgSpinPolls unless
+                                 // changed with nbte_set_wait_limit)
   double tol;
   int max_it;
   int32_t* it_out;
   double* res_out;
 };
+// default polls of the CG grid barrier before it gives up (seconds)
+constexpr unsigned long long kCgSpinPolls = 1ull << 24;
 // persistent cooperative PCG; coarse32 selects the FP32 coarse preconditioner
 cudaError_t launch_cg(const CGArgs& a, bool coarse32, int grid, int threads, size_t smem, cudaStream_t st);
 // several solvers' corrections in one cooperative launch; args[s] and
@@ -223,6 +227,22 @@ struct WallHeatArgs {
 };
 template <typename R>
 void launch_wall_heat(const WallHeatArgs<R>& a, cudaStream_t st);
+
+// Wall heat per boundary tag and the energy balance of the last sweep, FP64,
+// in one block with a fixed summation order:
+//   out[0]            |sum_thermalizing tags heat - integral Qdot| /
+//                     max(integral |Qdot|, sum |heat|)
+//   out[1], out[2]    sum over thermalizing tags of the heat, integral Qdot
+//   out[3 + t]        heat through tag index t (t < n_tags)
+// heat[f] is the net outward flow through wall face f (launch_wall_heat),
+// tag_of[f] its tag index, therm[t] = 1 for thermalizing tags.
+cudaError_t launch_wall_balance(const double* heat, const int32_t* tag_of, const int32_t* therm, int n_tags,
+                                int64_t n_wf, const double* Q, const double* V, int64_t N, double* out,
+                                cudaStream_t st);
+// rhs[c] = Q[c] V[c] + bc[c]: the right-hand side of the diffusion initial
+// guess (bc holds the thermalizing walls' Dirichlet terms)
+cudaError_t launch_fourier_rhs(double* rhs, const double* Q, const double* V, const double* bc, int64_t N,
+                               cudaStream_t st);
 
 template <typename R>
 void launch_fill_srcTQ(R* srcTQ, const double* T, const double* Q, int N, cudaStream_t st);

@@ -11,6 +11,11 @@ namespace nbte {
 
 void set_error(const std::string& msg);
 
+// The poll limit every bounded device wait uses: `dflt` unless a positive
+// limit was set with nbte_set_wait_limit (a diagnostic for testing the
+// timeout paths).
+unsigned long long wait_limit_or(unsigned long long dflt);
+
 struct Status {
   int code = NBTE_OK;
   std::string msg;

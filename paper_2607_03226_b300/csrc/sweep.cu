@@ -15,14 +15,17 @@
 //  * the other warps are consumers: they wait on a stage's "full" barrier,
 //    compute one position per thread from shared memory and the value ring,
 //    release the stage on its "empty" barrier, and meet on a named barrier
-//    only at the end of a level (so the next level sees the ring writes).
+//    between the levels of a chunk and at the start of every chunk (so the
+//    next level sees the ring writes); the chunk-start barrier also carries
+//    a vote on whether any consumer's wait gave up.
 // The value ring holds the outgoing values of the direction's live cells
 // (slots assigned by the planner).  It lives in shared memory when it fits
 // (GR = false); otherwise (GR = true, large 3D meshes whose sweep front has
 // tens of thousands of live cells) in a per-CTA global-memory region, where
 // the concurrently running CTAs' live windows stay mostly in L2.  Every wait
-// is bounded: on timeout the error word is set, the producer waits (bounded)
-// for the copies it issued, and the CTA leaves.
+// is bounded (SweepArgs::wait_limit polls): on timeout the error word is set,
+// the consumers leave together after their vote, the producer waits (with
+// the fixed limit) for the copies it issued, and the CTA leaves.
 //
 // Per cell and band the balance is solved for the deviation from the cell's
 // own equilibrium e0 = C T'/W (Eq. (11)):
@@ -44,8 +47,6 @@
 namespace nbte {
 
 namespace {
-
-constexpr unsigned long long kWaitLimit = 1ull << 26;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -69,9 +70,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (unsigned long long k = 0; k < kWaitLimit; ++k)
+// bounded wait (at most `limit` polls); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit) {
+  for (unsigned long long k = 0; k < limit; ++k)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -84,6 +85,17 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void consumer_barrier(int count) {
   asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+// A barrier over the `count` consumer threads (named barrier 2) that also
+// returns whether any of them passed p = true.
+__device__ __forceinline__ bool consumers_any(bool p, int count) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, 2, %2, a;\n selp.u32 %0, 1, 0, b;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(count)
+      : "memory");
+  return r != 0;
 }
 
 // FP32: the hardware approximate reciprocal (relative error below 2^-22,
@@ -200,7 +212,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       m.nimp_end = __shfl_sync(0xffffffffu, cur.w, c & 31);
       if (lane == 0) {
         const int s = sp;
-        if (c >= NS && !mbar_wait(empty + s, php ^ 1u)) {
+        if (c >= NS && !mbar_wait(empty + s, php ^ 1u, a.wait_limit)) {
           atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
           ok = false;
         }
@@ -251,9 +263,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         php ^= 1u;
       }
     }
-    // every copy issued must land before the CTA leaves
+    // every copy issued must land before the CTA leaves (with the fixed
+    // limit: a configured short limit must not leave copies in flight)
     if (lane == 0)
-      for (int c = issued - NS > 0 ? issued - NS : 0; c < issued; ++c) mbar_wait(full + (c % NS), (c / NS) & 1);
+      for (int c = issued - NS > 0 ? issued - NS : 0; c < issued; ++c)
+        mbar_wait(full + (c % NS), (c / NS) & 1, kSweepWaitPolls);
     return;
   }
 
@@ -273,20 +287,47 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
   }
   R* part = a.part + (int64_t)item * a.N;
   R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * GP;
-  consumer_barrier(ncons);
 
   int sc = 0;          // stage of chunk c, and the parity of its round
   unsigned phc = 0;
+  bool level_start = true;   // chunk c starts a level (chunk c - 1 ended one)
+  bool aborting = false;     // a wait of this warp gave up inside a level
   for (int c = 0; c < nch; ++c) {
     const int s = sc;
-    if (!mbar_wait(full + s, phc)) {
+    // A wait that gives up must not leave the other consumers at a level
+    // barrier.  At a chunk that starts a level all consumers meet on one
+    // barrier, which closes the previous level (for chunk 0: the zero slot)
+    // and tells them whether any wait gave up: then they all leave.  A
+    // thread whose wait gives up in a chunk that continues a level (a piece
+    // of a level wider than a chunk) stops computing but keeps the chunks'
+    // barrier sequence, read from the chunk descriptors in global memory,
+    // until that vote.  The decision is per warp (any lane's wait gave up),
+    // so that every barrier is reached by whole warps.
+    const bool timed_out = aborting || __any_sync(0xffffffffu, !mbar_wait(full + s, phc, a.wait_limit));
+    if (level_start) {
+      if (consumers_any(timed_out, ncons)) {
+        if (ct == 0) atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
+        break;
+      }
+    } else if (timed_out && !aborting) {
+      aborting = true;
       atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
-      break;
     }
-    const Chunk m = meta[s];
+    const Chunk m = aborting ? a.chunks[ch0 + c] : meta[s];
+    const int n_lev = chunk_levels(m.nimp_end);
+    level_start = chunk_level_end(m.nimp_end);
+    if (aborting) {
+      for (int lv = 0; lv + 1 < n_lev; ++lv) consumer_barrier(ncons);
+      __syncwarp();
+      if ((ct & 31) == 0) mbar_arrive(empty + s);
+      if (++sc == NS) {
+        sc = 0;
+        phc ^= 1u;
+      }
+      continue;
+    }
     const unsigned char* st = stages + (size_t)s * a.stage_bytes;
     // the block: header (level count, level ends), records, (T', Qdot) pairs
-    const int n_lev = chunk_levels(m.nimp_end);
     const int32_t* lev_end = reinterpret_cast<const int32_t*>(st) + 1;
     const unsigned char* recs = st + chunk_header_bytes(n_lev);
     using R2 = typename Vec2<R>::T;
@@ -374,7 +415,6 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     }
     __syncwarp();
     if ((ct & 31) == 0) mbar_arrive(empty + s);
-    if (chunk_level_end(m.nimp_end)) consumer_barrier(ncons);
     if (++sc == NS) {
       sc = 0;
       phc ^= 1u;

@@ -11,6 +11,12 @@ namespace nbte {
 // device error word values (written by bounded waits, read by the host)
 enum DevError : int32_t { DEV_OK = 0, DEV_BARRIER_TIMEOUT = 1, DEV_QUEUE_TIMEOUT = 2 };
 
+// Polls of an mbarrier before a sweep wait gives up (about a second): the
+// default of SweepArgs::wait_limit, and the fixed limit of the final wait for
+// the copies a CTA issued (which must land before it leaves, whatever the
+// configured limit).
+constexpr unsigned long long kSweepWaitPolls = 1ull << 26;
+
 // shared-memory budget of one sweep CTA (the rest of the SM's 228 KB stays
 // free for a second CTA when the ring is small)
 constexpr int kSweepSmemMax = 227 * 1024;
@@ -55,6 +61,8 @@ struct SweepArgs {
   double* accE;                  // [N]   (full)
   double* accQ;                  // [N*dim] (full)
   int32_t* err;                  // device error word
+  unsigned long long wait_limit; // polls before a pipeline wait gives up (kSweepWaitPolls unless
+                                 // changed with nbte_set_wait_limit)
 };
 
 }  // namespace nbte
