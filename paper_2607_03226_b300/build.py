@@ -1,6 +1,9 @@
-"""Build libnanobte.so in-tree with nvcc for sm_103a (no GPU needed).
+"""Build libnanobte.so in-tree with nvcc for sm_103a (no GPU needed), and
+libnanobte_checks.so, the same library with the sweep's device-side
+consistency checks compiled in (NBTE_CHECKS: index bounds, level order and
+ring-slot reuse, reported as an error status instead of a fault).
 
-    python -m paper_2607_03226_b300.build [--force]
+    python -m paper_2607_03226_b300.build [--force] [--checks]
 """
 from __future__ import annotations
 
@@ -15,6 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libnanobte.so")
+LIB_CHECKS = os.path.join(HERE, "libnanobte_checks.so")
 BUILD = os.path.join(HERE, "_build")
 
 SOURCES = ["mesh.cpp", "plan.cpp", "coarse.cpp", "capi.cpp", "kernels.cu", "sweep.cu", "sweep_data.cu", "noalloc.cu"]
@@ -33,16 +37,20 @@ def _digest():
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "stamp")
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    lib = LIB_CHECKS if checks else LIB
+    bdir = os.path.join(BUILD, "checks") if checks else BUILD
+    os.makedirs(bdir, exist_ok=True)
+    stamp = os.path.join(bdir, "stamp")
     dg = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dg:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read() == dg:
+        return lib
     common = ["-O3", "-std=c++17", "-I", INCLUDE, "-Xcompiler", "-fPIC", "-lineinfo"]
+    if checks:
+        common.append("-DNBTE_CHECKS")
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(bdir, src + ".o")
         cmd = [NVCC, *common, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu") and verbose:
             cmd += ["-Xptxas", "-v"]
@@ -62,14 +70,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and r.stderr:
             print(r.stderr)
         objs.append(obj)
-    cmd = [NVCC, "-shared", *ARCH, "-o", LIB, *objs, "-lpthread"]
+    cmd = [NVCC, "-shared", *ARCH, "-o", lib, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     with open(stamp, "w") as f:
         f.write(dg)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checks="--checks" in sys.argv))

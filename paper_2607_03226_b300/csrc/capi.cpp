@@ -208,6 +208,7 @@ struct nbte_solver {
   std::vector<int32_t> tag_list;
   std::vector<double> wall_heat_by_tag;
   DBuf wf_tagidx, tag_therm, balance, fbc;
+  DBuf pos_last, chk_level, chk_last;         // NBTE_CHECKS builds only
 
   ~nbte_solver() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -252,7 +253,7 @@ size_t device_bytes(const nbte_solver* S) {
                        &S->cg_Ainv, &S->L_ecol, &S->L_eval,
                        &S->L_diag, &S->L_dinv, &S->o2_e, &S->o2_src, &S->o2_grad, &S->rc_nb, &S->rc_twin,
                        &S->rc_AnV, &S->rc_a, &S->rc_gw, &S->rc_rf, &S->wf_tagidx, &S->tag_therm, &S->balance,
-                       &S->fbc};
+                       &S->fbc, &S->pos_last, &S->chk_level, &S->chk_last};
   size_t t = 0;
   for (auto* b : all) t += b->bytes;
   return t;
@@ -262,6 +263,14 @@ void drop_graph(nbte_solver* S) {
   if (S->graph) cudaGraphExecDestroy(S->graph);
   S->graph = nullptr;
   S->graph_key.clear();
+}
+
+// status of a non-zero sweep error word (a bounded wait gave up, or, in
+// NBTE_CHECKS builds, a consistency check failed)
+int sweep_error(uint64_t word) {
+  if (word == (uint64_t)DEV_CHECK_FAILED)
+    return fail(NBTE_ERR_STATE, "a device-side consistency check of the sweep failed (index bounds or level order)");
+  return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
 }
 
 // ------------------------------------------------------------------ plan
@@ -384,6 +393,7 @@ int ensure_records(nbte_solver* S) {
     }
   NBTE_CK(upload(S->rec_pos, buf));
   NBTE_CK(upload(S->pos_cell, P.pos_cell));
+  if (kChecks) NBTE_CK(upload(S->pos_last, P.pos_last));
   S->rec_key = key;
   S->blk_key.clear();
   return NBTE_OK;
@@ -759,6 +769,10 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   } else {
     S->gring.release();
   }
+  if (kChecks) {
+    NBTE_CK(S->chk_level.alloc((size_t)S->n_items * (S->max_slots + 1) * 4));
+    NBTE_CK(S->chk_last.alloc((size_t)S->n_items * (S->max_slots + 1) * 4));
+  }
   if (!prec) {
     // FP64: the denominators 1/(1/tau + v G) of every (work item, position),
     // iteration-independent, so the sweep reads them instead of dividing
@@ -1109,6 +1123,12 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.accE = S->accE.as<double>();
   a.accQ = S->accQ.as<double>();
   a.wait_limit = wait_limit_or(kSweepWaitPolls);
+  a.ring_slots = S->max_slots + 1;
+  if (kChecks) {
+    a.chk_level = S->chk_level.as<int32_t>();
+    a.chk_last = S->chk_last.as<int32_t>();
+    a.pos_last = S->pos_last.as<int32_t>();
+  }
   return a;
 }
 
@@ -1371,7 +1391,7 @@ int time_sweep(nbte_solver* S, const nbte_solve_opts& o, float* ms) {
   NBTE_CK(cudaMemcpy(&err, S->res.as<unsigned long long>() + 2, 8, cudaMemcpyDeviceToHost));
   if (err) {
     zero_now(S->res.p, 32, S->stream);
-    return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
+    return sweep_error(err);
   }
   *ms = t / 2;
   return NBTE_OK;
@@ -1467,7 +1487,7 @@ struct Run {
     // a wait that gave up leaves this iteration's fields incomplete: the
     // next solve starts from its initial state again (not warm)
     if (S->h_res[2] != 0) {
-      status = fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
+      status = sweep_error(S->h_res[2]);
       zero_now(S->res.p, 32, S->stream);
       S->have_state = false;
       return true;
@@ -1899,7 +1919,8 @@ void shrink(nbte_solver* S) {
                  &S->cg_rw, &S->cg_rcx, &S->cg_scx, &S->cg_Ainv, &S->cg_Ainv64, &S->L_ecol, &S->L_eval,
                  &S->L_diag, &S->L_dinv, &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell,
                  &S->cg_blk_agg, &S->cg_slots, &S->dinv, &S->o2_e, &S->o2_src, &S->o2_grad, &S->rc_nb,
-                 &S->rc_twin, &S->rc_AnV, &S->rc_a, &S->rc_gw, &S->rc_rf};
+                 &S->rc_twin, &S->rc_AnV, &S->rc_a, &S->rc_gw, &S->rc_rf, &S->pos_last, &S->chk_level,
+                 &S->chk_last, &S->fbc};
   for (DBuf* b : big) b->release();
   S->rc_prec = -1;
   S->layout_key.clear();
@@ -2499,7 +2520,7 @@ static int distribution(nbte_solver* S, int dir, int band, double* out) {
   NBTE_CK(cudaStreamSynchronize(st));
   if (err) {
     zero_now(S->res.p, 32, S->stream);
-    return fail(NBTE_ERR_DEVICE_TIMEOUT, "a bounded wait of the sweep's copy pipeline gave up");
+    return sweep_error(err);
   }
   const int b = band % G;
   for (int64_t c = 0; c < N; ++c) out[m.perm[c]] = (double)tmp[(size_t)c * G + b];

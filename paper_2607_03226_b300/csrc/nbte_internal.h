@@ -11,6 +11,16 @@ namespace nbte {
 
 void set_error(const std::string& msg);
 
+// Builds with NBTE_CHECKS defined add device-side consistency checks to the
+// sweep (index bounds, upstream level before the reading level, ring-slot
+// reuse only after the slot's last reader); a failed check is reported as
+// NBTE_ERR_STATE.  Normal builds carry none of them.
+#ifdef NBTE_CHECKS
+constexpr bool kChecks = true;
+#else
+constexpr bool kChecks = false;
+#endif
+
 // The poll limit every bounded device wait uses: `dflt` unless a positive
 // limit was set with nbte_set_wait_limit (a diagnostic for testing the
 // timeout paths).
@@ -61,6 +71,8 @@ struct Plan {
   std::vector<int32_t> max_width;          // [D] widest level (cells)
   // position records, direction-major, N per direction
   std::vector<int32_t> pos_cell, pos_slot, pos_exp;   // [D*N]
+  std::vector<int32_t> pos_last;                      // [D*N] last level that reads the position's value
+                                                      // (-1: none); filled in NBTE_CHECKS builds only
   std::vector<double> pos_G;                          // [D*N]
   std::vector<int32_t> pos_ref;                       // [D*K*N]
   std::vector<double> pos_coef;                       // [D*K*N]

@@ -142,6 +142,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
   P.pos_cell.assign((size_t)D * N, 0);
   P.pos_slot.assign((size_t)D * N, -1);
   P.pos_exp.assign((size_t)D * N, -1);
+  if (kChecks) P.pos_last.assign((size_t)D * N, -1);
   P.pos_G.assign((size_t)D * N, 0.0);
   P.pos_ref.assign((size_t)D * K * N, 0);
   P.pos_coef.assign((size_t)D * K * N, 0.0);
@@ -282,6 +283,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
         P.pos_cell[base + p] = c;
         P.pos_slot[base + p] = slot[c];
         P.pos_exp[base + p] = exp_local[c];
+        if (kChecks) P.pos_last[base + p] = last_use[c];
         double G = 0.0;
         int kk = 0;
         for (int k = 0; k < nfc; ++k) {

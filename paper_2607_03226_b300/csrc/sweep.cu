@@ -15,17 +15,16 @@
 //  * the other warps are consumers: they wait on a stage's "full" barrier,
 //    compute one position per thread from shared memory and the value ring,
 //    release the stage on its "empty" barrier, and meet on a named barrier
-//    between the levels of a chunk and at the start of every chunk (so the
-//    next level sees the ring writes); the chunk-start barrier also carries
-//    a vote on whether any consumer's wait gave up.
+//    only at the end of a level (so the next level sees the ring writes).
 // The value ring holds the outgoing values of the direction's live cells
 // (slots assigned by the planner).  It lives in shared memory when it fits
 // (GR = false); otherwise (GR = true, large 3D meshes whose sweep front has
 // tens of thousands of live cells) in a per-CTA global-memory region, where
 // the concurrently running CTAs' live windows stay mostly in L2.  Every wait
 // is bounded (SweepArgs::wait_limit polls): on timeout the error word is set,
-// the consumers leave together after their vote, the producer waits (with
-// the fixed limit) for the copies it issued, and the CTA leaves.
+// a consumer lane whose wait gave up stops computing but keeps the barrier
+// sequence, the producer waits (with the fixed limit) for the copies it
+// issued, and the CTA leaves.
 //
 // Per cell and band the balance is solved for the deviation from the cell's
 // own equilibrium e0 = C T'/W (Eq. (11)):
@@ -86,18 +85,6 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void consumer_barrier(int count) {
   asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
 }
-// A barrier over the `count` consumer threads (named barrier 2) that also
-// returns whether any of them passed p = true.
-__device__ __forceinline__ bool consumers_any(bool p, int count) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.or.pred b, 2, %2, a;\n selp.u32 %0, 1, 0, b;\n}"
-      : "=r"(r)
-      : "r"((uint32_t)p), "r"(count)
-      : "memory");
-  return r != 0;
-}
-
 // FP32: the hardware approximate reciprocal (relative error below 2^-22,
 // under the FP32 sweep's own rounding); FP64: a correctly rounded division
 __device__ __forceinline__ float recip(float x) {
@@ -287,45 +274,42 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
   }
   R* part = a.part + (int64_t)item * a.N;
   R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * GP;
+#ifdef NBTE_CHECKS
+  // every slot of this item's ring: not written yet, no reader left
+  const size_t chk0 = (size_t)item * a.ring_slots;
+  for (int t = ct; t < a.ring_slots; t += ncons) {
+    a.chk_level[chk0 + t] = -1;
+    a.chk_last[chk0 + t] = -1;
+  }
+  const int64_t n_exp_i = a.exp_off[i + 1] - a.exp_off[i];
+  int next_level = 0;        // level index of the next chunk's first level
+#endif
+  consumer_barrier(ncons);
+  bool dead = false;   // this lane's wait for a chunk gave up
 
   int sc = 0;          // stage of chunk c, and the parity of its round
   unsigned phc = 0;
-  bool level_start = true;   // chunk c starts a level (chunk c - 1 ended one)
-  bool aborting = false;     // a wait of this warp gave up inside a level
   for (int c = 0; c < nch; ++c) {
     const int s = sc;
-    // A wait that gives up must not leave the other consumers at a level
-    // barrier.  At a chunk that starts a level all consumers meet on one
-    // barrier, which closes the previous level (for chunk 0: the zero slot)
-    // and tells them whether any wait gave up: then they all leave.  A
-    // thread whose wait gives up in a chunk that continues a level (a piece
-    // of a level wider than a chunk) stops computing but keeps the chunks'
-    // barrier sequence, read from the chunk descriptors in global memory,
-    // until that vote.  The decision is per warp (any lane's wait gave up),
-    // so that every barrier is reached by whole warps.
-    const bool timed_out = aborting || __any_sync(0xffffffffu, !mbar_wait(full + s, phc, a.wait_limit));
-    if (level_start) {
-      if (consumers_any(timed_out, ncons)) {
-        if (ct == 0) atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
-        break;
-      }
-    } else if (timed_out && !aborting) {
-      aborting = true;
+    // A lane whose wait gives up is dead from then on: it neither waits nor
+    // computes, but walks the remaining chunks with the barrier sequence of
+    // the chunk descriptors (read from global memory), so no consumer is
+    // left waiting at a level barrier.  A warp releases a stage only when
+    // all its lanes saw the stage's data, so the producer never refills a
+    // stage while a copy into it may still be in flight.
+    if (!dead && !mbar_wait(full + s, phc, a.wait_limit)) {
+      dead = true;
       atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
     }
-    const Chunk m = aborting ? a.chunks[ch0 + c] : meta[s];
+    Chunk m;
+    if (dead) m = a.chunks[ch0 + c];
+    else m = meta[s];
     const int n_lev = chunk_levels(m.nimp_end);
-    level_start = chunk_level_end(m.nimp_end);
-    if (aborting) {
-      for (int lv = 0; lv + 1 < n_lev; ++lv) consumer_barrier(ncons);
-      __syncwarp();
-      if ((ct & 31) == 0) mbar_arrive(empty + s);
-      if (++sc == NS) {
-        sc = 0;
-        phc ^= 1u;
-      }
-      continue;
-    }
+#ifdef NBTE_CHECKS
+    const int level0 = next_level;
+    next_level = level0 + n_lev - (chunk_level_end(m.nimp_end) ? 0 : 1);
+    const int nimp_chunk = chunk_imports(m.nimp_end);
+#endif
     const unsigned char* st = stages + (size_t)s * a.stage_bytes;
     // the block: header (level count, level ends), records, (T', Qdot) pairs
     const int32_t* lev_end = reinterpret_cast<const int32_t*>(st) + 1;
@@ -345,7 +329,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     // the ring values the previous one wrote)
     int lb = 0;
     for (int lv = 0; lv < n_lev; ++lv) {
-      const int le = lev_end[lv];
+      const int le = dead ? 0 : lev_end[lv];
       for (int j = lb + ct; j < le; j += ncons) {
         uint4 w[NQ];
 #pragma unroll
@@ -354,6 +338,31 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         const int slot = (int)rec_word(w, 1);
         const int ex = (int)rec_word(w, 2);
         const R Gc = RecField<R>::get(w, RL.off_G);
+#ifdef NBTE_CHECKS
+        // indices in range, every upstream value written in an earlier level
+        // and still owned by its cell, a slot reused only after its last reader
+        {
+          const int lvl = level0 + lv;
+          bool bad = cell < 0 || cell >= a.N || slot < -1 || slot == 0 || slot >= a.ring_slots || ex < -1 ||
+                     ex >= n_exp_i;
+          for (int k = 0; k < K && !bad; ++k) {
+            const int ref = (int)rec_word(w, RL.off_ref / 4 + k);
+            if (ref >= a.ring_slots) bad = true;
+            else if (ref > 0) bad = !(a.chk_level[chk0 + ref] >= 0 && a.chk_level[chk0 + ref] < lvl &&
+                                      lvl <= a.chk_last[chk0 + ref]);
+            else if (ref < 0) bad = (-1 - ref) - imp0 < 0 || (-1 - ref) - imp0 >= nimp_chunk;
+          }
+          if (!bad && slot > 0) bad = a.chk_last[chk0 + slot] >= lvl;
+          if (bad) {
+            atomicExch(a.err, (int32_t)DEV_CHECK_FAILED);
+            continue;
+          }
+          if (slot > 0) {
+            a.chk_level[chk0 + slot] = lvl;
+            a.chk_last[chk0 + slot] = a.pos_last[(size_t)i * a.N + m.pos + j];
+          }
+        }
+#endif
         const R2 tq = tqs[j];
         const R T = tq.x;
         const R Q = tq.y;
@@ -413,8 +422,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       if (lv + 1 < n_lev) consumer_barrier(ncons);
       lb = le;
     }
-    __syncwarp();
-    if ((ct & 31) == 0) mbar_arrive(empty + s);
+    const bool all_saw = __all_sync(0xffffffffu, !dead);
+    if (all_saw && (ct & 31) == 0) mbar_arrive(empty + s);
+    if (chunk_level_end(m.nimp_end)) consumer_barrier(ncons);
     if (++sc == NS) {
       sc = 0;
       phc ^= 1u;

@@ -9,7 +9,7 @@
 namespace nbte {
 
 // device error word values (written by bounded waits, read by the host)
-enum DevError : int32_t { DEV_OK = 0, DEV_BARRIER_TIMEOUT = 1, DEV_QUEUE_TIMEOUT = 2 };
+enum DevError : int32_t { DEV_OK = 0, DEV_BARRIER_TIMEOUT = 1, DEV_QUEUE_TIMEOUT = 2, DEV_CHECK_FAILED = 3 };
 
 // Polls of an mbarrier before a sweep wait gives up (about a second): the
 // default of SweepArgs::wait_limit, and the fixed limit of the final wait for
@@ -63,6 +63,13 @@ struct SweepArgs {
   int32_t* err;                  // device error word
   unsigned long long wait_limit; // polls before a pipeline wait gives up (kSweepWaitPolls unless
                                  // changed with nbte_set_wait_limit)
+  // consistency checks (NBTE_CHECKS builds only; null otherwise): per work
+  // item and ring slot the level that last wrote the slot and the last level
+  // that may read it, and per position the last level reading its value
+  int32_t* chk_level;
+  int32_t* chk_last;
+  const int32_t* pos_last;       // [D*N]
+  int32_t ring_slots;            // slots of one work item's value ring (zero slot included)
 };
 
 }  // namespace nbte
