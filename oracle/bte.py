@@ -330,6 +330,15 @@ class OracleSolver:
         self._order[i] = got
         return got
 
+    def forget_direction(self, i):
+        """Drop what was cached for direction i (its advection operator,
+        upwind order and factorisations); they are rebuilt on next use."""
+        self._dir.pop(i, None)
+        self._order.pop(i, None)
+        self._ordered.pop(i, None)
+        for key in [k for k in self._lu if k[0] == i]:
+            del self._lu[key]
+
     def _factor(self, i, l):
         """The factorised system ``I/tau_l + v_l K_i`` of Eq. (13), as an object
         with ``solve(rhs)``.

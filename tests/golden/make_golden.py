@@ -33,7 +33,7 @@ Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_conve
                             third sweep, on the sample cells.
 
 The last three split every pass over worker processes by direction (one per
-available core; ``PoolSweep``).
+available core, or GOLDEN_WORKERS; ``PoolSweep``).
 """
 from __future__ import annotations
 
@@ -71,9 +71,13 @@ def _write(name, payload):
 _O = None
 
 
-def _pool_init(name, kwargs):
-    global _O
+_KEEP = True
+
+
+def _pool_init(name, kwargs, keep):
+    global _O, _KEEP
     _O = OracleSolver(getattr(W.problems, name)(**kwargs))
+    _KEEP = keep
 
 
 class _Cols:
@@ -90,20 +94,32 @@ class _Cols:
 
 
 def _pool_sweep(Tdev, e_in_sub, dirs):
-    tasks = [(i, l) for i in dirs for l in range(_O.B)]
-    r = _O.sweep(Tdev, None, tasks=tasks, e_in=_Cols(e_in_sub, dirs), eb_dirs=dirs)
-    return r["NL"], r["E"], r["q"], r["eb"]
+    """The worker's directions one at a time (all bands of each); without
+    _KEEP each direction's cached operators are dropped after its bands."""
+    e_in = _Cols(e_in_sub, dirs)
+    NL, E, q = np.zeros(_O.N), np.zeros(_O.N), np.zeros((_O.N, _O.dim))
+    eb = np.empty((_O.bcells.size, _O.B, len(dirs)))
+    for k, i in enumerate(dirs):
+        r = _O.sweep(Tdev, None, tasks=[(i, l) for l in range(_O.B)], e_in=e_in, eb_dirs=[i])
+        NL += r["NL"]
+        E += r["E"]
+        q += r["q"]
+        eb[:, :, k] = r["eb"][:, :, 0]
+        if not _KEEP:
+            _O.forget_direction(i)
+    return NL, E, q, eb
 
 
 class PoolSweep:
     """Drop-in for ``OracleSolver.sweep`` (first-order passes) that solves
     the (direction, band) tasks on ``workers`` processes."""
 
-    def __init__(self, o, name, kwargs=None, workers=None):
+    def __init__(self, o, name, kwargs=None, workers=None, keep=True):
         self.o = o
-        workers = workers or max(1, len(os.sched_getaffinity(0)))
+        workers = workers or int(os.environ.get("GOLDEN_WORKERS", "0")) or max(1, len(os.sched_getaffinity(0)))
         self.dirs = [list(range(k, o.D, workers)) for k in range(workers)]
-        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(name, kwargs or {}))
+        self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init,
+                                                 initargs=(name, kwargs or {}, keep))
 
     def __call__(self, Tdev, eb_prev, store_e=False, e_prev=None):
         if store_e or e_prev is not None:
@@ -243,7 +259,7 @@ def finfet3d_steps():
     partially specular walls feed in the previous sweep's values."""
     p = W.problems.finfet3d()
     o = OracleSolver(p)
-    pool = PoolSweep(o, "finfet3d")
+    pool = PoolSweep(o, "finfet3d", keep=False)   # per-direction operators are rebuilt each pass (memory)
     idx = _sample(p.n_cells)
     out = dict(problem="finfet3d()", scheme="sequential", sample_seed=SAMPLE_SEED,
                command="python tests/golden/make_golden.py finfet3d_steps", cells=idx.tolist())

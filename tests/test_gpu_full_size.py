@@ -2,12 +2,18 @@
 cells, 40 bands, 128 directions; the FinFET: 1.14M tets, 40 bands, 200
 directions), in the autotuned launch configuration a user gets.
 
-A full oracle iteration at these sizes takes hours, so the oracle's values
-are stored (tests/golden/make_golden.py): the distribution e'_{l i} of a few
-(direction, band) tasks in the first sequential iteration from T_ref, on
-4096 seeded sample cells, each task one sparse solve of Eq. (4).  The device
-values come from nbte_get_distribution.  Tolerances relative to max|e'| of
-the task: FP64 1e-11 (rounding order only), FP32 sweep 1e-6.
+The oracle's values are stored (tests/golden/make_golden.py), on 4096 seeded
+sample cells:
+* the distribution e'_{l i} of a few (direction, band) tasks in the first
+  sequential iteration from T_ref (device values from nbte_get_distribution;
+  relative to max|e'| of the task: FP64 1e-11, rounding order only; FP32
+  sweep 1e-6);
+* the FinFET's temperature after sequential iterations 1, 2 and 3 from T_ref
+  and the heat flux of the third sweep: from the second iteration on every
+  diffuse, specular and partially specular wall feeds back the previous
+  sweep (FP64 1e-11 of the largest deviation, q 1e-10; FP32 1e-6);
+* the cube converged with the synthetic scheme (the CG correction at full
+  size): T 1e-9 and q 1e-8 in FP64, T 1e-6 with the FP32 sweep.
 """
 import json
 import os
@@ -94,3 +100,47 @@ def test_stream_requests_first_iteration_tasks(nbte_mod, k):
             print(f"{p.name} ({p.n_cells} cells) {precision} task ({i}, {l}): rel err {err:.2e}")
             assert err < tol
     s.close()
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    return json.load(open(path))
+
+
+@pytest.mark.parametrize("precision,tol_T,tol_q", [("fp64", 1e-11, 1e-10), ("fp32", 1e-6, 1e-5)])
+def test_finfet3d_full_size_three_iterations(nbte_mod, precision, tol_T, tol_q):
+    g = _golden("finfet3d_steps.json")
+    s = _solver(nbte_mod, "finfet3d")
+    idx = np.array(g["cells"])
+    for n in (1, 2, 3):
+        info = s.solve(scheme="sequential", precision=precision, n_iter=n, use_graph=True, skip_outputs=n < 3)
+        assert info["iterations"] == n
+        err = np.abs(s.temperature(0)[idx] - np.array(g[f"T_iter{n}"])).max() / g[f"T_iter{n}_max_dev"]
+        print(f"finfet3d {precision} iteration {n}: T rel err {err:.2e}")
+        assert err < tol_T
+    eq = np.abs(s.heat_flux()[idx] - np.array(g["q_iter3"])).max() / g["q_iter3_max"]
+    print(f"finfet3d {precision} iteration 3: q rel err {eq:.2e}")
+    assert eq < tol_q
+
+
+def test_cube3d_full_size_converged(nbte_mod):
+    g = _golden("cube3d_converged.json")
+    assert g["tol"] <= 1e-12
+    s = _solver(nbte_mod, "cube3d")
+    idx = np.array(g["cells"])
+    Tg, qg = np.array(g["T"]), np.array(g["q"])
+    dev = max(g["T_max"] - 300.0, 300.0 - g["T_min"])
+    info = s.solve(scheme="synthetic", precision="fp64", tol=1e-13, max_iter=5000, init="fourier")
+    assert info["status"] == 0
+    eT = np.abs(s.temperature(0)[idx] - Tg).max() / dev
+    eq = np.abs(s.heat_flux()[idx] - qg).max() / g["q_max"]
+    print(f"cube3d fp64 synthetic: {info['iterations']} iterations, T {eT:.2e}, q {eq:.2e}")
+    assert eT < 1e-9 and eq < 1e-8
+    assert info["energy_imbalance"] < 1e-9
+    info = s.solve(scheme="synthetic", precision="fp32", tol=1e-9, max_iter=5000)
+    assert info["status"] == 0
+    eT = np.abs(s.temperature(0)[idx] - Tg).max() / dev
+    print(f"cube3d fp32 synthetic: {info['iterations']} iterations (floor {info['residual']:.1e}), T {eT:.2e}")
+    assert eT < 1e-6

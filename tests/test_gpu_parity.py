@@ -249,21 +249,31 @@ def test_finfet2d_full_size_every_layout(nbte_mod, precision, tol):
 
 
 def test_finfet2d_full_size_converged(nbte_mod):
-    """The full-size 2D fin converged with the benchmark's scheme (synthetic,
-    FP32 sweep) and in FP64: T and q on the stored oracle sample cells."""
+    """The full-size 2D fin converged, FP64 and FP32 sweep, against the
+    oracle's field converged to 1e-13 (728 sequential iterations): T and q
+    on the stored sample cells, relative to the oracle's largest deviation
+    and heat flux over all cells.  FP64: T 1e-9, q 1e-8; FP32 sweep: T 1e-6
+    (the stated targets)."""
     g = _fin2d_golden("finfet2d_converged.json")
+    assert g["tol"] <= 1e-13
     p = W.problems.finfet2d()
     idx = np.array(g["cells"])
     Tg, qg = np.array(g["T"]), np.array(g["q"])
     dev = g["T_max"] - p.T_ref
     s = nbte_mod.Solver(p)
-    info = s.solve(scheme="synthetic", precision="fp64", tol=1e-12, max_iter=5000)
+    for scheme in ("synthetic", "sequential"):
+        info = s.solve(scheme=scheme, precision="fp64", tol=1e-13, max_iter=20000)
+        assert info["status"] == 0
+        eT = np.abs(s.temperature(0)[idx] - Tg).max() / dev
+        eq = np.abs(s.heat_flux()[idx] - qg).max() / g["q_max"]
+        print(f"fp64 {scheme}: {info['iterations']} iterations, T {eT:.2e}, q {eq:.2e}")
+        assert eT < 1e-9 and eq < 1e-8
+    info = s.solve(scheme="synthetic", precision="fp32", tol=1e-9, max_iter=20000)
     assert info["status"] == 0
-    assert np.abs(s.temperature(0)[idx] - Tg).max() / dev < 1e-8
-    assert np.abs(s.heat_flux()[idx] - qg).max() / np.abs(qg).max() < 1e-7
-    info = s.solve(scheme="synthetic", precision="fp32", tol=1e-9, max_iter=5000)
-    assert info["status"] == 0
-    assert np.abs(s.temperature(0)[idx] - Tg).max() / dev < 2e-6
+    eT = np.abs(s.temperature(0)[idx] - Tg).max() / dev
+    eq = np.abs(s.heat_flux()[idx] - qg).max() / g["q_max"]
+    print(f"fp32 synthetic: {info['iterations']} iterations (floor {info['residual']:.1e}), T {eT:.2e}, q {eq:.2e}")
+    assert eT < 1e-6
     s.close()
 
 
