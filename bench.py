@@ -1,18 +1,23 @@
-"""Throughput benchmark: band-direction cell updates per second on the 2D
-FinFET-like workload (~50k triangles, 20 bands, 64 directions), in the
-scheme that workload is specified with (sequential; FP32 sweep by default,
-FP64 with --precision fp64).
+"""Throughput benchmark: band-direction cell updates per second on the
+1.14M-tet 3D FinFET workload (fin 7 x 50 x 100 nm on a 300 x 100 x 50 nm
+substrate, 40 bands, 200 directions, 5e17 W/m^3 in the fin), in the scheme
+that workload is specified with (synthetic: the sweep plus the diffusion
+correction), FP32 sweeps with FP64 moments, update and correction; the same
+line carries the FP64 path's step (the paper's precision).
 
 A step is one outer iteration of the hot path: wall coupling, the
 level-scheduled sweep over every (direction, band) with the fused collision
-moment, the moment reduction and the temperature update, on inputs resident
-in device memory.  The same line reports the synthetic scheme's step (the CG
-correction added) and the time to a converged field for both schemes.
+moment, the moment reduction and the temperature update (plus the CG
+correction for the synthetic scheme), on inputs resident in device memory.
+The line also reports the time to a converged field, the end-to-end rate
+through the C ABI with host buffers, the sweep's roofline and the FP64
+oracle timed on this host's cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--precision fp32|fp64] [--scheme synthetic|sequential]
+                    [--workload finfet3d|finfet2d|cube3d] [--precision fp32|fp64]
+                    [--scheme synthetic|sequential]
     python bench.py --workload stream [--requests R] [--load L]     (serving)
-    python bench.py --workload cube3d|finfet3d [--precision fp64]   (time to converged field)
+    python bench.py --converge --workload cube3d|finfet3d           (time to converged field)
 
 Prints one JSON line.  Under torchrun (N > 1) every rank solves its own
 replica (no data exchange); rank 0 prints the aggregate over all ranks.
@@ -33,7 +38,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "band-dir cell updates/s"
 UNIT = "updates/s"
-WORKLOAD = "finfet2d: ~50k-triangle fin-on-substrate, 20 bands, 64 directions, Gaussian hot spot"
+# name -> (description, scheme the workload is specified with)
+WORKLOADS = {
+    "finfet3d": ("finfet3d: 1.14M-tet FinFET (fin 7 x 50 x 100 nm on a 300 x 100 x 50 nm substrate), "
+                 "40 bands, 200 directions, 5e17 W/m^3 in the fin, mixed walls (p = 0.5 fin sides)", "synthetic"),
+    "finfet2d": ("finfet2d: ~50k-triangle fin-on-substrate, 20 bands, 64 directions, Gaussian hot spot",
+                 "sequential"),
+    "cube3d": ("cube3d: 500 nm cube, 64^3 hexes, 40 bands (Kn 0.01-1), 128 directions, 310/300 K walls",
+               "synthetic"),
+}
+# nominal FP64 (non-tensor) arithmetic rate of one B300 (FLOP/s): the FP64
+# sweep's roof; there is no measured figure for it
+FP64_NOMINAL_FLOPS = 1.25e12
 
 
 def _dist():
@@ -118,8 +134,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def sweep_algorithmic_bytes(st, n_cells, n_dirs, prec_bytes, Bp, order=1):
-    """Bytes one sweep launch must move to or from HBM at minimum:
+def sweep_algorithmic_bytes(updates, prec_bytes):
+    """Algorithmic bytes of one sweep launch by the scope table's count for a
+    resident-distribution sweep: every band-direction cell update writes its
+    value once and reads it once (8 B in FP32, 16 B in FP64).  This is the
+    roofline's byte count."""
+    return 2 * prec_bytes * updates
+
+
+def sweep_design_bytes(st, n_cells, n_dirs, prec_bytes, Bp, order=1):
+    """Bytes this design's sweep launch must move to or from HBM at minimum
+    (reported beside the roofline; no distribution is stored):
     * each direction's position records once (cell, ring slot, export index,
       diagonal G, and K inflow references and coefficients; the 16-byte
       padding of the packed record is not counted) -- the band groups of a
@@ -128,9 +153,10 @@ def sweep_algorithmic_bytes(st, n_cells, n_dirs, prec_bytes, Bp, order=1):
     * the (T', Qdot) pair of every cell once;
     * the wall/lag import values read and the export values written
       (boundary cells only), all bands.
-    Upwind values live in the shared-memory ring and cost no HBM traffic.
-    Second order adds, per (direction, cell, band), the reconstruction source
-    read and the outgoing value kept for the next iteration's gradients."""
+    Upwind values live in the value ring (shared memory, or an L2-resident
+    global region) and are not counted.  Second order adds, per (direction,
+    cell, band), the reconstruction source read and the outgoing value kept
+    for the next iteration's gradients."""
     K = st["K"]
     rec = 3 * 4 + prec_bytes + K * (4 + prec_bytes)
     b = (n_dirs * n_cells * rec + st["items"] * n_cells * prec_bytes + n_cells * 2 * prec_bytes
@@ -140,17 +166,27 @@ def sweep_algorithmic_bytes(st, n_cells, n_dirs, prec_bytes, Bp, order=1):
     return b
 
 
-def _sweep_traffic(G, threads):
-    """DRAM bytes per sweep launch from the committed ncu summary, if that
-    capture was taken with the current sweep sources and this launch layout
-    (else None)."""
+def sweep_flops_per_update(n_faces):
+    """FP operations of one band-direction cell update: an inflow face's
+    term is one FMA (about n_faces / 2 inflow faces per cell), plus the
+    equilibrium product, the source FMA, the division (FP64: a product with
+    the precomputed denominator), the update and the collision-moment FMA."""
+    return 2 * (n_faces / 2) + 7
+
+
+def _sweep_traffic(workload, precision, G, threads, updates):
+    """DRAM bytes per sweep launch from the committed ncu summary of this
+    workload's sweep, if that capture was taken with the current sweep
+    sources and this launch layout (else None).  A capture on a smaller case
+    of the same workload (the summary's updates_per_launch) is scaled to a
+    full launch by the updates it processes."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "sweep_kernel_finfet2d_fp32.md")
+    path = os.path.join(ROOT, "profiles", f"sweep_kernel_{workload}_{precision}.md")
     if not os.path.exists(path):
         return None
     fields = {}
     for line in open(path):
-        if ":" in line and not line.startswith(("|", "#", " ")):
+        if ":" in line and not line.startswith(("|", "#", " ", "*", "`")):
             k, _, v = line.partition(":")
             fields[k.strip()] = v.strip()
     h = hashlib.sha256()
@@ -162,9 +198,44 @@ def _sweep_traffic(G, threads):
     if fields.get("layout") != f"band_group={G} cta_threads={threads}":
         return None
     try:
-        return int(fields["traffic_bytes_per_launch"])
+        t = int(fields["traffic_bytes_per_launch"])
+        n = int(fields.get("updates_per_launch", updates))
     except (KeyError, ValueError):
         return None
+    return int(round(t * updates / n))
+
+
+def _event_time(stream, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def _step_record(solver, stream, kw, steps, upd, n_faces, prec):
+    """ms per step (graph replay, CUDA events), the sweep's own duration
+    (events around each launch) and its roofline."""
+    solver.solve(n_iter=3, warm=True, **kw)
+    ms, info = _event_time(stream, lambda: solver.solve(n_iter=steps, warm=True, **kw))
+    prof = solver.solve(n_iter=steps, warm=True, profile=True, **{k: v for k, v in kw.items() if k != "use_graph"})
+    sweep_ms = prof["sweep_seconds"] * 1e3 / max(1, prof["sweep_launches"])
+    rec = {"ms_per_step": ms / steps, "updates_per_s": upd / (ms / steps * 1e-3), "sweep_ms": sweep_ms,
+           "cg_iterations_per_step": info["cg_iterations"] / max(1, steps)}
+    return rec, info
+
+
+def _fp64_roofline(sweep_ms, upd, n_faces):
+    flops = sweep_flops_per_update(n_faces) * upd
+    achieved = flops / (sweep_ms * 1e-3) / 1e12
+    peak = FP64_NOMINAL_FLOPS / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": "nominal FP64 rate (no measured FP64 figure)", "traffic": None,
+            "kernel": "sweep_kernel", "sweep_ms": sweep_ms, "flops_per_update": sweep_flops_per_update(n_faces)}
 
 
 def run_gpu(args):
@@ -180,17 +251,22 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    p = W.problems.finfet2d()
+    desc, scheme0 = WORKLOADS[args.workload]
+    scheme = args.scheme or scheme0
+    p = getattr(W.problems, args.workload)()
+    n_faces = {3: 3, 4: 4, 10: 4, 12: 6}[int(p.mesh.cell_type)]
     stream = torch.cuda.Stream()
     solver = nbte.Solver(p, stream=stream.cuda_stream)
-    kw = dict(scheme=args.scheme, precision=args.precision, cg_tol=args.cg_tol, cg_max_iter=args.cg_max_iter,
+    kw = dict(scheme=scheme, precision=args.precision, cg_tol=args.cg_tol, cg_max_iter=args.cg_max_iter,
               band_group=args.band_group, cta_threads=args.cta_threads, use_graph=True,
               skip_outputs=True, order=args.order)
-    stats = solver.plan_stats(**kw)
+    t_setup = time.perf_counter()
+    stats = solver.plan_stats(**kw)          # plan, upload and (band_group = cta_threads = 0) the autotuner
     upd = p.updates_per_iteration
-    # warm-up (includes planning, upload and graph capture) then the timed steps
+    # warm-up (graph capture) then the timed steps
     solver.solve(n_iter=max(args.warmup, 3), **kw)
     torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -209,116 +285,112 @@ def run_gpu(args):
     t_max = max_over_ranks(ms, dist, "cuda")
     value = aggregate_rate(upd, args.steps, ws, t_max)
 
-    # sweep-kernel duration with events around each launch (same stream)
-    prof = solver.solve(n_iter=args.steps, warm=True, profile=True, **{k: v for k, v in kw.items()
-                                                                        if k != "use_graph"})
+    # the sweep kernel's own duration: events around each launch, same stream
+    prof = solver.solve(n_iter=args.steps, warm=True, profile=True,
+                        **{k: v for k, v in kw.items() if k != "use_graph"})
     sweep_ms = prof["sweep_seconds"] * 1e3 / max(1, prof["sweep_launches"])
     prec_b = 4 if args.precision == "fp32" else 8
     G = stats["band_group"]
     n_items = stats["items"]
     Bp = n_items // p.n_dirs * G
-    bytes_launch = sweep_algorithmic_bytes(stats, p.n_cells, p.n_dirs, prec_b, Bp, args.order)
+    bytes_launch = sweep_algorithmic_bytes(upd, prec_b)
+    design_bytes = sweep_design_bytes(stats, p.n_cells, p.n_dirs, prec_b, Bp, args.order)
     peak, peak_kind = _peaks()
     achieved = bytes_launch / (sweep_ms * 1e-3) / 1e9
-
-    # the other scheme's step, and the time to a converged field from T_ref
-    other = "synthetic" if args.scheme == "sequential" else "sequential"
-    kw_o = dict(kw, scheme=other)
-    solver.solve(n_iter=3, warm=True, **kw_o)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    info_o = solver.solve(n_iter=args.steps, warm=True, **kw_o)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_o = e0.elapsed_time(e1) / args.steps
-    tol_c = 1e-7 if args.precision == "fp32" else 1e-10
-    ttc = {}
-    for sch in ("sequential", "synthetic"):
-        kw_c = dict(kw, scheme=sch, tol=tol_c, max_iter=20000)
-        kw_c.pop("n_iter", None)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        ic = solver.solve(**kw_c)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ttc[sch] = {"seconds": e0.elapsed_time(e1) * 1e-3, "iterations": ic["iterations"],
-                    "residual": ic["residual"], "status": ic["status"]}
-
-    # the other upwind order: its step (the second-order step adds the
-    # reconstruction-source gather and the sweep's extra input), its sweep,
-    # and its time to a converged field
-    order_o = 2 if args.order == 1 else 1
-    kw_r = dict(kw, order=order_o)
-    solver.solve(n_iter=3, **kw_r)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    solver.solve(n_iter=args.steps, warm=True, **kw_r)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_r = e0.elapsed_time(e1) / args.steps
-    prof_r = solver.solve(n_iter=args.steps, warm=True, profile=True,
-                          **{k: v for k, v in kw_r.items() if k != "use_graph"})
-    kw_rc = dict(kw_r, tol=tol_c, max_iter=20000)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    ic = solver.solve(**kw_rc)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    order_step = {"ms_per_step": ms_r, "updates_per_s": upd / (ms_r * 1e-3),
-                  "sweep_ms": prof_r["sweep_seconds"] * 1e3 / max(1, prof_r["sweep_launches"]),
-                  "time_to_converged": {"scheme": args.scheme, "seconds": e0.elapsed_time(e1) * 1e-3,
-                                        "iterations": ic["iterations"], "residual": ic["residual"],
-                                        "status": ic["status"]}}
+    if args.precision == "fp32":
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": peak_kind,
+                    "traffic": (_sweep_traffic(args.workload, args.precision, G, stats["cta_threads"], upd)
+                                if args.order == 1 else None),
+                    "kernel": "sweep_kernel", "sweep_ms": sweep_ms, "algorithmic_bytes_per_launch": bytes_launch,
+                    "bytes_per_update": 2 * prec_b, "design_bytes_per_launch": design_bytes,
+                    "design_frac": design_bytes / (sweep_ms * 1e-3) / 1e9 / peak}
+    else:
+        roofline = _fp64_roofline(sweep_ms, upd, n_faces)
 
     # end to end through the public API with pinned host buffers: per step the
     # heat source goes host->device, one iteration runs, the temperature comes
-    # back
+    # back; the second loop also computes and returns the heat flux (the
+    # output sweep of Eq. (7))
     Qh = torch.empty(p.n_cells, dtype=torch.float64, pin_memory=True).numpy()
-    Qh[:] = p.Q
+    Qh[:] = p.Q if p.Q is not None else 0.0
     Th = torch.empty(p.n_cells, dtype=torch.float64, pin_memory=True).numpy()
-    nbte.nbte_set_heat_source(solver.solver, Qh)   # untimed warm-up of this loop (graph re-capture)
-    solver.solve(n_iter=1, warm=True, **kw)
-    solver.temperature(0, out=Th)
-    t0 = time.perf_counter()
-    e2e_steps = max(3, args.steps // 2)
-    for _ in range(e2e_steps):
-        nbte.nbte_set_heat_source(solver.solver, Qh)
-        solver.solve(n_iter=1, warm=True, **kw)
-        T = solver.temperature(0, out=Th)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": upd * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Qh.nbytes),
-           "d2h_bytes_per_step": int(T.nbytes)}
+    qh = torch.empty((p.n_cells, p.mesh.dim), dtype=torch.float64, pin_memory=True).numpy()
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e = {}
+    for label, outputs in (("T", False), ("T+q", True)):
+        kw_e = dict(kw, skip_outputs=not outputs)
+        nbte.nbte_set_heat_source(solver.solver, Qh)      # untimed warm-up of this loop (graph re-capture)
+        solver.solve(n_iter=1, warm=True, **kw_e)
+        solver.temperature(0, out=Th)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            nbte.nbte_set_heat_source(solver.solver, Qh)
+            solver.solve(n_iter=1, warm=True, **kw_e)
+            solver.temperature(0, out=Th)
+            if outputs:
+                solver.heat_flux(out=qh)
+        e2e[label] = (time.perf_counter() - t0, int(Th.nbytes + (qh.nbytes if outputs else 0)))
+    e2e_line = {"value": upd * e2e_steps / e2e["T"][0], "unit": UNIT, "h2d_bytes_per_step": int(Qh.nbytes),
+                "d2h_bytes_per_step": e2e["T"][1],
+                "per_step": "heat source up, one iteration, temperature down (one call each)",
+                "with_heat_flux": {"value": upd * e2e_steps / e2e["T+q"][0], "unit": UNIT,
+                                   "h2d_bytes_per_step": int(Qh.nbytes), "d2h_bytes_per_step": e2e["T+q"][1],
+                                   "per_step": "as above plus the output sweep of Eq. (7) and the heat flux down"}}
+
+    # the other scheme's step, and the time to a converged field from T_ref
+    other = "synthetic" if scheme == "sequential" else "sequential"
+    other_rec, _ = _step_record(solver, stream, dict(kw, scheme=other), max(3, args.steps // 2), upd, n_faces,
+                                args.precision)
+    ttc = None
+    if not args.no_converge:
+        tol_c = args.converge_tol or (1e-6 if args.precision == "fp32" else 1e-8)
+        kw_c = dict(kw, tol=tol_c, max_iter=args.max_iter)
+        ms_c, ic = _event_time(stream, lambda: solver.solve(**kw_c))
+        ttc = {"scheme": scheme, "seconds": ms_c * 1e-3, "iterations": ic["iterations"],
+               "residual": ic["residual"], "status": ic["status"], "tol": tol_c, "start": "T_ref"}
+
+    # the FP64 path (all sweeps, moments and corrections in FP64)
+    fp64 = None
+    if args.precision == "fp32" and not args.no_fp64:
+        kw64 = dict(kw, precision="fp64", band_group=args.fp64_band_group, cta_threads=args.fp64_cta_threads)
+        t64 = time.perf_counter()
+        st64 = solver.plan_stats(**kw64)
+        solver.solve(n_iter=3, **kw64)
+        t64 = time.perf_counter() - t64
+        rec64, _ = _step_record(solver, stream, kw64, max(3, args.fp64_steps), upd, n_faces, "fp64")
+        fp64 = dict(rec64, roofline=_fp64_roofline(rec64["sweep_ms"], upd, n_faces), band_group=st64["band_group"],
+                    cta_threads=st64["cta_threads"], setup_s=t64,
+                    dtype="f64", scheme=scheme)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 sweep / f64 moments+update+CG" if args.precision == "fp32" else "f64",
-        "data": "synthetic (seeded mesh, spectrum and hot spot)",
-        "config": {"workload": WORKLOAD, "n_cells": p.n_cells, "bands": p.n_bands, "directions": p.n_dirs,
-                   "updates_per_step": upd, "scheme": args.scheme, "precision": args.precision, "cg_tol": args.cg_tol,
+        "data": "synthetic (seeded mesh, spectrum and heat source)",
+        "config": {"workload": desc, "n_cells": p.n_cells, "bands": p.n_bands, "directions": p.n_dirs,
+                   "updates_per_step": upd, "scheme": scheme, "precision": args.precision, "cg_tol": args.cg_tol,
                    "upwind_order": args.order,
-                   "band_group": G, "cta_threads": stats["cta_threads"], "items": n_items, "levels_max": stats["max_levels"],
-                   "ring_slots_max": stats["max_slots"], "parallelism": f"replicas x{ws}",
+                   "band_group": G, "cta_threads": stats["cta_threads"], "items": n_items,
+                   "levels_max": stats["max_levels"], "ring_slots_max": stats["max_slots"],
+                   "ring": "global" if stats["ring"] == 2 else "shared", "lagged_faces": stats["lagged_faces"],
+                   "parallelism": f"replicas x{ws}", "setup_s": t_setup,
                    "l2": "inputs larger than L2: per-step device footprint %.0f MB > 126 MB" % (
                        stats["device_bytes"] / 1e6)},
-        "e2e": e2e,
+        "e2e": e2e_line,
         "gpu_launches": int(info["kernel_launches"]),
         "cg_iterations_per_step": info["cg_iterations"] / max(1, args.steps),
-        other + "_step": {"ms_per_step": ms_o, "updates_per_s": upd / (ms_o * 1e-3),
-                          "cg_iterations_per_step": info_o["cg_iterations"] / max(1, args.steps)},
-        "time_to_converged": dict(ttc, tol=tol_c, start="T_ref"),
-        "upwind_order_%d_step" % order_o: order_step,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind,
-                     "traffic": (_sweep_traffic(G, stats["cta_threads"])
-                                 if args.precision == "fp32" and args.order == 1 else None),
-                     "kernel": "sweep_kernel", "sweep_ms": sweep_ms,
-                     "algorithmic_bytes_per_launch": bytes_launch},
+        "sweep_ms": sweep_ms,
+        other + "_step": other_rec,
+        "time_to_converged": ttc,
+        "fp64": fp64,
+        "roofline": roofline,
         "clocks": clocks,
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(max_seconds=args.cpu_seconds)
     solver.close()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, max_seconds=args.cpu_seconds)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -326,35 +398,107 @@ def run_gpu(args):
         print(json.dumps(out))
 
 
-def cpu_baseline(max_seconds=20.0, steps=1, warmup=1):
-    """The FP64 oracle on this host's cores, on a bounded sample of the same
-    workload: one transport pass over a subset of (direction, band) tasks (the
-    LU factorisations are built in an untimed warm-up pass), scaled to
-    updates/s."""
+# ---------------------------------------------------------------- CPU baseline
+# The FP64 oracle on this host's cores: worker processes (spawned, so that no
+# CUDA state is inherited), each with its own OracleSolver of the workload,
+# each solving a sample of (direction, band) tasks of the first transport
+# pass from T_ref (every wall then feeds in the equilibrium at T_ref).
+_BASE = None
+
+
+class _FirstPassIncoming:
+    """Incoming wall values of the first pass from T_ref, indexed like the
+    oracle's (half-face, band, direction) array, one band at a time."""
+
+    def __init__(self, o):
+        import numpy as np
+        self.o = o
+        self.eb0 = np.zeros((o.bcells.size, o.D))
+        self.band = {}
+
+    def __getitem__(self, key):
+        h, l, i = key
+        if l not in self.band:
+            self.band = {l: self.o.incoming_band(self.eb0, l)}
+        return self.band[l][h, i]
+
+
+def _base_init(workload):
+    global _BASE
     import numpy as np
     import workloads as W
     from oracle import OracleSolver
+    o = OracleSolver(getattr(W.problems, workload)())
+    _BASE = (o, np.zeros(o.N), _FirstPassIncoming(o))
 
-    p = W.problems.finfet2d()
-    o = OracleSolver(p)
-    T = np.zeros(p.n_cells)
-    eb = o.equilibrium_walls(T)
-    # size the sample from one factor+solve timing
+
+def _base_run(tasks):
+    """Solve `tasks` (one transport pass over them, moments included);
+    returns the seconds it took."""
+    o, T0, e_in = _BASE
+    dirs = sorted({i for i, _ in tasks})
     t0 = time.perf_counter()
-    o.sweep(T, eb, tasks=[(0, 0)])
-    o.sweep(T, eb, tasks=[(0, 0)])
-    one = (time.perf_counter() - t0) / 2
-    n_tasks = int(max(2, min(p.n_dirs * p.n_bands, max_seconds / (2.5 * max(one, 1e-3)))))
-    tasks = [(i, l) for i in range(p.n_dirs) for l in range(p.n_bands)][:n_tasks]
+    o.sweep(T0, None, tasks=tasks, e_in=e_in, eb_dirs=dirs)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """``workers`` processes, each owning a set of directions of the
+    workload; ``run(k)`` has every worker solve k tasks of its directions
+    (bands in turn) at once and returns the wall time."""
+
+    def __init__(self, workload, workers=None):
+        import multiprocessing as mp
+        import workloads as W
+        p = getattr(W.problems, workload)()
+        self.n_cells, self.n_bands, self.n_dirs = p.n_cells, p.n_bands, p.n_dirs
+        avail = len(os.sched_getaffinity(0))
+        self.workers = max(1, min(workers or avail, 32, p.n_dirs))
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_base_init, initargs=(workload,))
+        self.next = [0] * self.workers
+
+    def _tasks(self, w, k):
+        out = []
+        for _ in range(k):
+            j = self.next[w]
+            self.next[w] += 1
+            i = (w + self.workers * (j // self.n_bands)) % self.n_dirs
+            out.append((i, j % self.n_bands))
+        return out
+
+    def run(self, k):
+        jobs = [self._tasks(w, k) for w in range(self.workers)]
+        t0 = time.perf_counter()
+        self.pool.map(_base_run, jobs, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(workload, max_seconds=20.0, steps=1, warmup=1, pool=None):
+    """The FP64 oracle on this host's cores on a bounded sample of the same
+    workload: each worker solves the same number of (direction, band) tasks
+    of one transport pass (the per-direction set-up of each worker's first
+    direction runs in an untimed warm-up), scaled to updates/s."""
+    own = pool is None
+    pool = pool or OraclePool(workload)
+    t_one = pool.run(1)                                   # warm-up: builds every worker's first direction
+    k = int(max(1, min(pool.n_bands, max_seconds / (max(steps, 1) * max(t_one, 1e-3)))))
     for _ in range(warmup):
-        o.sweep(T, eb, tasks=tasks)
-    t0 = time.perf_counter()
+        pool.run(k)
+    dt = 0.0
     for _ in range(steps):
-        o.sweep(T, eb, tasks=tasks)
-    dt = (time.perf_counter() - t0) / steps
-    return {"value": n_tasks * p.n_cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_tasks} of {p.n_dirs * p.n_bands} (direction, band) tasks of one iteration, "
-                      f"{p.n_cells} cells each, cached sparse LU solves (SciPy SuperLU, single thread)",
+        dt += pool.run(k)
+    dt /= steps
+    n_tasks = k * pool.workers
+    if own:
+        pool.close()
+    return {"value": n_tasks * pool.n_cells / dt, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+            "sample": f"{n_tasks} of {pool.n_dirs * pool.n_bands} (direction, band) tasks of one transport pass "
+                      f"from T_ref ({pool.n_cells} cells each; moments included), {k} per worker process; "
+                      f"sparse LU of Eq. (13) in a fill-free upwind order (SciPy), one process per core",
             "seconds_per_step": dt}
 
 
@@ -530,36 +674,65 @@ def run_converge(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on this host's cores,
+    timed on a bounded sample of the same workload each step (one transport
+    pass over an equal number of (direction, band) tasks per worker process),
+    so that the whole --steps/--warmup run ends within a few minutes."""
     ws, rank = _dist()
     if rank != 0:
         return
-    cb = cpu_baseline(max_seconds=args.cpu_seconds, steps=args.steps, warmup=args.warmup)
-    out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": cb["seconds_per_step"] * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "scheme": "sequential transport pass (oracle)"},
-           "impl": "reference", "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
-           "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    desc, scheme0 = WORKLOADS[args.workload]
+    pool = OraclePool(args.workload)
+    t_one = pool.run(1)                                   # untimed: every worker's first direction
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    k = int(max(1, min(pool.n_bands, per_step / max(t_one, 1e-3))))
+    for _ in range(args.warmup):
+        pool.run(k)
+    dts = [pool.run(k) for _ in range(args.steps)]
+    pool.close()
+    dt = sum(dts) / len(dts)
+    n_tasks = k * pool.workers
+    value = n_tasks * pool.n_cells / dt
+    sample = (f"{n_tasks} of {pool.n_dirs * pool.n_bands} (direction, band) tasks of one transport pass from T_ref "
+              f"per step ({pool.n_cells} cells each), {k} per worker process; sparse LU of Eq. (13) in a fill-free "
+              f"upwind order (SciPy), one process per core")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mesh, spectrum and heat source)",
+           "config": {"workload": desc, "scheme": f"{scheme0} (oracle transport pass)", "n_cells": pool.n_cells,
+                      "bands": pool.n_bands, "directions": pool.n_dirs},
+           "impl": "reference",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="nbte", choices=["nbte", "reference"])
+    ap.add_argument("--workload", default="finfet3d", choices=["finfet3d", "finfet2d", "cube3d", "stream"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--scheme", default="sequential", choices=["synthetic", "sequential"])
+    ap.add_argument("--scheme", default=None, choices=["synthetic", "sequential"],
+                    help="default: the scheme the workload is specified with")
     ap.add_argument("--band-group", type=int, default=0)
     ap.add_argument("--cta-threads", type=int, default=0)
     ap.add_argument("--cg-tol", type=float, default=1e-2)
     ap.add_argument("--order", type=int, default=1, choices=[1, 2],
                     help="upwind order of the face values (2: deferred least-squares reconstruction)")
     ap.add_argument("--cg-max-iter", type=int, default=5000)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 path's step")
+    ap.add_argument("--fp64-band-group", type=int, default=0)
+    ap.add_argument("--fp64-cta-threads", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-converge", action="store_true", help="skip the time to a converged field")
+    ap.add_argument("--converge-tol", type=float, default=0.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="finfet2d", choices=["finfet2d", "stream", "cube3d", "finfet3d"])
+    ap.add_argument("--converge", action="store_true",
+                    help="time and iterations to a converged field, both schemes and starts (3D workloads)")
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--requests", type=int, default=24)
     ap.add_argument("--min-cells", type=int, default=20000)
@@ -570,10 +743,12 @@ def main():
     ap.add_argument("--planners", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.workload == "stream":
+            args.workload = "finfet3d"
         run_reference(args)
     elif args.workload == "stream":
         run_stream(args)
-    elif args.workload in ("cube3d", "finfet3d"):
+    elif args.converge:
         run_converge(args)
     else:
         run_gpu(args)

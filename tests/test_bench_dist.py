@@ -55,23 +55,29 @@ def test_reference_arm_prints_from_rank_zero_only(monkeypatch):
     assert buf.getvalue() == ""
 
 
-def test_sweep_algorithmic_bytes_by_hand():
-    """The roofline's algorithmic bytes for the 32^3 cube's sweep, item by
-    item: records (cell, slot, export, G and three inflow (reference,
-    coefficient) pairs = 40 B) per (direction, cell), one FP32 partial per
-    (work item, cell), the (T', Qdot) pairs, and the wall rows of all
-    bands."""
-    st = {"K": 3, "items": 1280, "exports": 381056, "imports": 393216}
+def test_sweep_bytes_by_hand():
+    """The roofline's bytes: the scope table's 8 B (FP32) / 16 B (FP64) per
+    band-direction cell update.  Beside it, this design's own minimum for the
+    32^3 cube's sweep, item by item: records (cell, slot, export, G and three
+    inflow (reference, coefficient) pairs = 40 B) per (direction, cell), one
+    FP32 partial per (work item, cell), the (T', Qdot) pairs, and the wall
+    rows of all bands."""
     N, D, Bp = 32768, 128, 40
+    assert bench.sweep_algorithmic_bytes(N * D * Bp, 4) == 8 * N * D * Bp
+    assert bench.sweep_algorithmic_bytes(N * D * Bp, 8) == 16 * N * D * Bp
+    st = {"K": 3, "items": 1280, "exports": 381056, "imports": 393216}
     expect = D * N * 40 + 1280 * N * 4 + N * 8 + (381056 + 393216) * Bp * 4
-    assert bench.sweep_algorithmic_bytes(st, N, D, 4, Bp) == expect == 459689984
+    assert bench.sweep_design_bytes(st, N, D, 4, Bp) == expect == 459689984
     # second order adds the source read and the distribution kept, per band
-    assert bench.sweep_algorithmic_bytes(st, N, D, 4, Bp, order=2) == expect + 2 * D * N * Bp * 4
+    assert bench.sweep_design_bytes(st, N, D, 4, Bp, order=2) == expect + 2 * D * N * Bp * 4
+    # FP operations per update: one FMA per inflow face (half the faces) + 7
+    assert bench.sweep_flops_per_update(4) == 11 and bench.sweep_flops_per_update(6) == 13
 
 
 def test_sweep_traffic_only_for_the_captured_sources(tmp_path, monkeypatch):
     """The committed DRAM traffic is reported only while the digest of the
-    sweep's sources and the launch layout match the capture's."""
+    sweep's sources and the launch layout match the capture's; a capture on
+    a smaller case is scaled by the updates a launch processes."""
     import hashlib
     import shutil
     csrc = tmp_path / "paper_2607_03226_b300" / "csrc"
@@ -83,12 +89,14 @@ def test_sweep_traffic_only_for_the_captured_sources(tmp_path, monkeypatch):
     for f in names:
         h.update((csrc / f).read_bytes())
     (tmp_path / "profiles").mkdir()
-    prof = tmp_path / "profiles" / "sweep_kernel_finfet2d_fp32.md"
-    prof.write_text("# capture\n\ntraffic_bytes_per_launch: 123456\n"
-                    f"sweep_source_digest: {h.hexdigest()[:16]}\nlayout: band_group=2 cta_threads=192\n")
+    prof = tmp_path / "profiles" / "sweep_kernel_finfet3d_fp32.md"
+    prof.write_text("# capture\n\ntraffic_bytes_per_launch: 123456\nupdates_per_launch: 1000\n"
+                    f"sweep_source_digest: {h.hexdigest()[:16]}\nlayout: band_group=8 cta_threads=544\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._sweep_traffic(2, 192) == 123456
-    assert bench._sweep_traffic(4, 256) is None          # another layout
+    assert bench._sweep_traffic("finfet3d", "fp32", 8, 544, 1000) == 123456
+    assert bench._sweep_traffic("finfet3d", "fp32", 8, 544, 8000) == 8 * 123456   # scaled to a full launch
+    assert bench._sweep_traffic("finfet3d", "fp32", 4, 256, 1000) is None          # another layout
+    assert bench._sweep_traffic("finfet2d", "fp32", 8, 544, 1000) is None          # no capture of that workload
     with open(csrc / "sweep.cu", "a") as fh:             # the kernel changed since the capture
         fh.write("\n// edited\n")
-    assert bench._sweep_traffic(2, 192) is None
+    assert bench._sweep_traffic("finfet3d", "fp32", 8, 544, 1000) is None
