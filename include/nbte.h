@@ -374,17 +374,18 @@ int nbte_laplacian_solve_noalloc(int n, const int32_t* row_ptr, const int32_t* c
                                  double* residual, void* cuda_stream);
 
 /* ------------------------------------------------------------ diagnostics --
- * nbte_set_wait_limit: every device-side wait of the library is bounded (the
- * sweep's copy pipeline, the CG grid barriers, the allocation-free solve's
- * barrier); a wait that gives up sets an error word, its kernel returns, and
- * the call reports NBTE_ERR_DEVICE_TIMEOUT.  polls > 0 makes every such wait
- * give up after that many polls, for the launches made after this call in
- * the whole process; polls <= 0 restores each wait's default (about a
- * second).  For testing the timeout paths: with a small limit the solves
- * that follow fail with NBTE_ERR_DEVICE_TIMEOUT.  After a timeout the
- * solver's iterate is incomplete: the next nbte_solve_steady starts again
- * from its initial state even when warm is set.  No paper counterpart.   */
-int nbte_set_wait_limit(int64_t polls);
+ * nbte_test_timeouts: every device-side wait of the library is bounded (the
+ * sweep's copy pipeline: about a second; the CG grid barriers; the
+ * allocation-free solve's barrier); a wait that runs out sets an error word,
+ * its kernel returns, and the call reports NBTE_ERR_DEVICE_TIMEOUT.  With
+ * on != 0, every such wait of the launches made after this call (in the
+ * whole process) runs out: the sweep's producer issues no copy, so its
+ * consumers' waits run out on their bound, and the barrier waits give up
+ * after one poll.  on = 0 restores normal operation.  For testing the
+ * timeout paths.  After a timeout the solver's iterate is incomplete: the
+ * next nbte_solve_steady starts again from its initial state even when warm
+ * is set.  No paper counterpart.                                          */
+int nbte_test_timeouts(int32_t on);
 
 /* Message of the last failing call on this thread (library-owned string). */
 const char* nbte_last_error(void);

@@ -30,13 +30,10 @@ using namespace nbte;
 namespace nbte {
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
-// poll limit of every bounded device wait set with nbte_set_wait_limit (0 =
-// each wait's own default)
-static std::atomic<unsigned long long> g_wait_limit{0};
-unsigned long long wait_limit_or(unsigned long long dflt) {
-  const unsigned long long v = g_wait_limit.load(std::memory_order_relaxed);
-  return v > 0 ? v : dflt;
-}
+// nbte_test_timeouts: every bounded device wait of later launches runs out
+static std::atomic<int> g_test_timeouts{0};
+bool test_timeouts() { return g_test_timeouts.load(std::memory_order_relaxed) != 0; }
+unsigned long long wait_limit_or(unsigned long long dflt) { return test_timeouts() ? 1ull : dflt; }
 }  // namespace nbte
 
 #define NBTE_CK(call)                                                                               \
@@ -1122,7 +1119,7 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.gring_stride = S->gring_stride;
   a.accE = S->accE.as<double>();
   a.accQ = S->accQ.as<double>();
-  a.wait_limit = wait_limit_or(kSweepWaitPolls);
+  a.hold_copies = test_timeouts() ? 1 : 0;
   a.ring_slots = S->max_slots + 1;
   if (kChecks) {
     a.chk_level = S->chk_level.as<int32_t>();
@@ -1627,7 +1624,7 @@ int run_solve(nbte_solver* S, const nbte_solve_opts& o, nbte_solve_info* info) {
   const std::string gkey = S->layout_key + "/" + std::to_string(scheme) + "/" + std::to_string(run.cg_tol) + "/" +
                            std::to_string(run.cg_max) + "/" + std::to_string(S->lap_built) + "/" +
                            std::to_string(S->cg_part_key) + "/" + std::to_string((long long)(intptr_t)st) + "/" +
-                           std::to_string(wait_limit_or(0));
+                           std::to_string(test_timeouts() ? 1 : 0);
   if (use_graph && (S->graph == nullptr || S->graph_key != gkey)) {
     drop_graph(S);
     cudaGraph_t gr = nullptr;
@@ -2107,8 +2104,8 @@ extern "C" {
 
 const char* nbte_last_error(void) { return g_err.c_str(); }
 
-int nbte_set_wait_limit(int64_t polls) {
-  g_wait_limit.store(polls > 0 ? (unsigned long long)polls : 0ull, std::memory_order_relaxed);
+int nbte_test_timeouts(int32_t on) {
+  g_test_timeouts.store(on ? 1 : 0, std::memory_order_relaxed);
   return NBTE_OK;
 }
 const char* nbte_version(void) { return "nanobte-b300 1.0 (sm_103a)"; }

@@ -165,8 +165,8 @@ struct CGArgs {
   CGSlot* slots;                 // [grid]
   unsigned long long* bar;       // barrier counter (only grows)
   int32_t* err;
-  unsigned long long spin_limit; // polls of the barrier word before giving up (kCgSpinPolls unless
-                                 // changed with nbte_set_wait_limit)
+  unsigned long long spin_limit; // polls of the barrier word before giving up (kCgSpinPolls; one
+                                 // poll under nbte_test_timeouts)
   double tol;
   int max_it;
   int32_t* it_out;

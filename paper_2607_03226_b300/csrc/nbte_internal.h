@@ -21,9 +21,10 @@ constexpr bool kChecks = true;
 constexpr bool kChecks = false;
 #endif
 
-// The poll limit every bounded device wait uses: `dflt` unless a positive
-// limit was set with nbte_set_wait_limit (a diagnostic for testing the
-// timeout paths).
+// nbte_test_timeouts (a diagnostic for testing the timeout paths): whether
+// every bounded device wait of the launches made now must run out, and the
+// poll limit a run-time-bounded wait then uses (one poll; else `dflt`).
+bool test_timeouts();
 unsigned long long wait_limit_or(unsigned long long dflt);
 
 struct Status {

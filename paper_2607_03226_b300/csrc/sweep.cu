@@ -21,10 +21,10 @@
 // (GR = false); otherwise (GR = true, large 3D meshes whose sweep front has
 // tens of thousands of live cells) in a per-CTA global-memory region, where
 // the concurrently running CTAs' live windows stay mostly in L2.  Every wait
-// is bounded (SweepArgs::wait_limit polls): on timeout the error word is set,
-// a consumer lane whose wait gave up stops computing but keeps the barrier
-// sequence, the producer waits (with the fixed limit) for the copies it
-// issued, and the CTA leaves.
+// is bounded (kSweepWaitPolls polls, about a second): on timeout the error
+// word is set, a consumer lane whose wait gave up stops computing but keeps
+// the barrier sequence, the producer waits for the copies it issued, and the
+// CTA leaves.
 //
 // Per cell and band the balance is solved for the deviation from the cell's
 // own equilibrium e0 = C T'/W (Eq. (11)):
@@ -69,9 +69,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait (at most `limit` polls); false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit) {
-  for (unsigned long long k = 0; k < limit; ++k)
+// bounded wait (at most kSweepWaitPolls polls, about a second); false on
+// timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (unsigned long long k = 0; k < kSweepWaitPolls; ++k)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -165,6 +166,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
 
   if (threadIdx.x < 32) {
     // ------------------------------------------------------------ producer
+    if (a.hold_copies) return;   // timeout test: no copy, every consumer wait runs out
     // the warp fetches chunk descriptors 32 at a time, one batch ahead; lane
     // 0 waits for free stages and issues the copies
     const int lane = threadIdx.x;
@@ -199,7 +201,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       m.nimp_end = __shfl_sync(0xffffffffu, cur.w, c & 31);
       if (lane == 0) {
         const int s = sp;
-        if (c >= NS && !mbar_wait(empty + s, php ^ 1u, a.wait_limit)) {
+        if (c >= NS && !mbar_wait(empty + s, php ^ 1u)) {
           atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
           ok = false;
         }
@@ -250,11 +252,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         php ^= 1u;
       }
     }
-    // every copy issued must land before the CTA leaves (with the fixed
-    // limit: a configured short limit must not leave copies in flight)
+    // every copy issued must land before the CTA leaves
     if (lane == 0)
-      for (int c = issued - NS > 0 ? issued - NS : 0; c < issued; ++c)
-        mbar_wait(full + (c % NS), (c / NS) & 1, kSweepWaitPolls);
+      for (int c = issued - NS > 0 ? issued - NS : 0; c < issued; ++c) mbar_wait(full + (c % NS), (c / NS) & 1);
     return;
   }
 
@@ -297,7 +297,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     // left waiting at a level barrier.  A warp releases a stage only when
     // all its lanes saw the stage's data, so the producer never refills a
     // stage while a copy into it may still be in flight.
-    if (!dead && !mbar_wait(full + s, phc, a.wait_limit)) {
+    if (!dead && !mbar_wait(full + s, phc)) {
       dead = true;
       atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
     }
@@ -329,7 +329,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     // the ring values the previous one wrote)
     int lb = 0;
     for (int lv = 0; lv < n_lev; ++lv) {
-      const int le = dead ? 0 : lev_end[lv];
+      const int le = dead ? 0 : lev_end[lv];   // a dead lane has no positions
       for (int j = lb + ct; j < le; j += ncons) {
         uint4 w[NQ];
 #pragma unroll

@@ -11,11 +11,12 @@ namespace nbte {
 // device error word values (written by bounded waits, read by the host)
 enum DevError : int32_t { DEV_OK = 0, DEV_BARRIER_TIMEOUT = 1, DEV_QUEUE_TIMEOUT = 2, DEV_CHECK_FAILED = 3 };
 
-// Polls of an mbarrier before a sweep wait gives up (about a second): the
-// default of SweepArgs::wait_limit, and the fixed limit of the final wait for
-// the copies a CTA issued (which must land before it leaves, whatever the
-// configured limit).
-constexpr unsigned long long kSweepWaitPolls = 1ull << 26;
+// Polls of an mbarrier before a sweep wait gives up.  A poll that finds the
+// phase incomplete suspends the thread for a few microseconds (measured about
+// 3.9 us on B300), so this is about a second.  The bound is a compile-time
+// constant: a run-time bound in the producer's wait loop made the 2D fin's
+// sweep 1.8x slower (same-box A/B).
+constexpr unsigned long long kSweepWaitPolls = 1ull << 18;
 
 // shared-memory budget of one sweep CTA (the rest of the SM's 228 KB stays
 // free for a second CTA when the ring is small)
@@ -61,8 +62,8 @@ struct SweepArgs {
   double* accE;                  // [N]   (full)
   double* accQ;                  // [N*dim] (full)
   int32_t* err;                  // device error word
-  unsigned long long wait_limit; // polls before a pipeline wait gives up (kSweepWaitPolls unless
-                                 // changed with nbte_set_wait_limit)
+  int32_t hold_copies;           // nonzero: the producer issues no copy, so every consumer wait runs
+                                 // out (the timeout test of nbte_test_timeouts)
   // consistency checks (NBTE_CHECKS builds only; null otherwise): per work
   // item and ring slot the level that last wrote the slot and the last level
   // that may read it, and per position the last level reading its value

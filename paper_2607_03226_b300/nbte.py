@@ -39,7 +39,7 @@ EXPORTS = [
     "nbte_get_heat_flux", "nbte_get_wall_heat", "nbte_plan_stats", "nbte_last_error", "nbte_version",
     "nbte_laplacian_solve_noalloc", "nbte_get_distribution", "nbte_solve_batch", "nbte_server_create",
     "nbte_server_submit", "nbte_server_poll", "nbte_server_drain", "nbte_server_stats", "nbte_server_destroy",
-    "nbte_set_wait_limit",
+    "nbte_test_timeouts",
 ]
 
 
@@ -119,7 +119,7 @@ def load(path: str | None = None):
         "nbte_version": ([], C.c_char_p),
         "nbte_laplacian_solve_noalloc": ([C.c_int, _P, _P, _P, _P, _P, C.c_double, C.c_int, _I32, _D, _P],
                                          C.c_int),
-        "nbte_set_wait_limit": ([C.c_int64], C.c_int),
+        "nbte_test_timeouts": ([C.c_int32], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -369,9 +369,10 @@ def nbte_laplacian_solve_noalloc(n, row_ptr_dev, col_dev, val_dev, rhs_dev, x_de
     return rc, it.value, res.value
 
 
-def nbte_set_wait_limit(polls):
-    """Poll limit of every bounded device wait (polls <= 0: the defaults)."""
-    _check(load().nbte_set_wait_limit(int(polls)))
+def nbte_test_timeouts(on):
+    """Make every bounded device wait of later launches run out (on), or
+    restore normal operation."""
+    _check(load().nbte_test_timeouts(int(bool(on))))
 
 
 def nbte_last_error():

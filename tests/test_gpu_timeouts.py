@@ -1,11 +1,13 @@
 """Failure detection without a GPU fault: every device-side wait of the
-library is bounded, and nbte_set_wait_limit cuts the bound to a single poll
-so that the waits give up.  Each kernel then sets its error word and returns
-(the sweep's consumers leave together after a vote, its producer still waits
-for the copies it issued); the call reports NBTE_ERR_DEVICE_TIMEOUT, and the
-same solver, with the default limit restored, solves to the oracle's result
-on the next call.  Nothing here hangs or faults: a wait that gives up only
-ends its kernel early."""
+library is bounded, and nbte_test_timeouts makes the waits run out -- the
+sweep's producer issues no copy (a barrier phase nothing completes, so each
+consumer's wait runs out on its bound of about a second) and the CG barriers
+give up after one poll.  Each kernel then sets its error word and returns
+(a sweep consumer whose wait ran out stops computing and keeps the barrier
+sequence); the call reports NBTE_ERR_DEVICE_TIMEOUT, and the same solver,
+back in normal operation, solves to the oracle's result on the next call.
+Nothing here hangs or faults: a wait that runs out only ends its kernel
+early."""
 import numpy as np
 import pytest
 
@@ -18,25 +20,26 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture
 def nbte_mod(gpu_lib):
     from paper_2607_03226_b300 import nbte
-    nbte.nbte_set_wait_limit(0)
+    nbte.nbte_test_timeouts(0)
     yield nbte
-    nbte.nbte_set_wait_limit(0)
+    nbte.nbte_test_timeouts(0)
 
 
 def _timed_out(nbte, call, tries=3):
-    """Run call() with one poll per wait until it reports a timeout (a wait
-    whose data is already there succeeds at its first poll, so a launch may
-    occasionally get through); returns the status code seen."""
+    """Run call() with every wait made to run out until it reports a
+    timeout (a CG barrier whose blocks all arrived at once passes its single
+    poll, so a launch may occasionally get through); returns the status code
+    seen."""
     code = None
     for _ in range(tries):
-        nbte.nbte_set_wait_limit(1)
+        nbte.nbte_test_timeouts(1)
         try:
             call()
             code = nbte.NBTE_OK
         except nbte.NbteError as e:
             code = e.code
         finally:
-            nbte.nbte_set_wait_limit(0)
+            nbte.nbte_test_timeouts(0)
         if code == nbte.NBTE_ERR_DEVICE_TIMEOUT:
             break
     return code
@@ -49,7 +52,7 @@ def test_sweep_wait_gives_up_then_next_solve_is_exact(nbte_mod, precision, tol):
     s = nbte.Solver(p)
     kw = dict(scheme="sequential", precision=precision, band_group=1, cta_threads=64)
     s.solve(n_iter=1, **kw)    # plan and layout with the default limit
-    code = _timed_out(nbte, lambda: s.solve(n_iter=3, **kw))
+    code = _timed_out(nbte, lambda: s.solve(n_iter=1, **kw))
     assert code == nbte.NBTE_ERR_DEVICE_TIMEOUT
     assert "gave up" in nbte.nbte_last_error()
     # warm is asked for, but after a timeout the solver starts over from T_ref
@@ -87,7 +90,7 @@ def test_batched_sweep_wait_gives_up(nbte_mod):
     nbte.solve_batch([a, b], n_iter=1, **kw)
 
     def batch():
-        infos = nbte.solve_batch([a, b], n_iter=2, **kw)
+        infos = nbte.solve_batch([a, b], n_iter=1, **kw)
         codes = {i["status"] for i in infos}
         if nbte.NBTE_ERR_DEVICE_TIMEOUT in codes:
             raise nbte.NbteError(nbte.NBTE_ERR_DEVICE_TIMEOUT, "batch")

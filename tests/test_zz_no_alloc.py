@@ -16,9 +16,9 @@ The checks:
   system;
 * after a first call on the device (n = 0 does only that set-up) a call
   leaves the device's free memory unchanged;
-* a row without a positive diagonal entry is refused, and a barrier wait cut
-  to one poll gives up with NBTE_ERR_DEVICE_TIMEOUT, after which the next
-  call is exact again.
+* a row without a positive diagonal entry is refused, and a barrier wait made
+  to run out (nbte_test_timeouts: one poll) gives up with
+  NBTE_ERR_DEVICE_TIMEOUT, after which the next call is exact again.
 The test's own device buffers come from PyTorch; the calls under test
 allocate nothing.
 """
@@ -127,7 +127,7 @@ def test_noalloc_barrier_timeout_then_exact(gpu_lib):
     code = None
     try:
         for _ in range(3):
-            nbte.nbte_set_wait_limit(1)
+            nbte.nbte_test_timeouts(1)
             try:
                 nbte.nbte_laplacian_solve_noalloc(*args)
                 code = nbte.NBTE_OK
@@ -136,7 +136,7 @@ def test_noalloc_barrier_timeout_then_exact(gpu_lib):
             if code == nbte.NBTE_ERR_DEVICE_TIMEOUT:
                 break
     finally:
-        nbte.nbte_set_wait_limit(0)
+        nbte.nbte_test_timeouts(0)
     assert code == nbte.NBTE_ERR_DEVICE_TIMEOUT
     status, iters, res = nbte.nbte_laplacian_solve_noalloc(*args)
     assert status == nbte.NBTE_OK and res <= 1e-12
