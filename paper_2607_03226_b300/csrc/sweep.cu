@@ -22,9 +22,9 @@
 // tens of thousands of live cells) in a per-CTA global-memory region, where
 // the concurrently running CTAs' live windows stay mostly in L2.  Every wait
 // is bounded (kSweepWaitPolls polls, about a second): on timeout the error
-// word is set, a consumer lane whose wait gave up stops computing but keeps
-// the barrier sequence, the producer waits for the copies it issued, and the
-// CTA leaves.
+// word is set, a consumer warp any of whose lanes gave up stops computing
+// but keeps the barrier sequence, the producer waits for the copies it
+// issued, and the CTA leaves.
 //
 // Per cell and band the balance is solved for the deviation from the cell's
 // own equilibrium e0 = C T'/W (Eq. (11)):
@@ -285,25 +285,18 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
   int next_level = 0;        // level index of the next chunk's first level
 #endif
   consumer_barrier(ncons);
-  bool dead = false;   // this lane's wait for a chunk gave up
 
   int sc = 0;          // stage of chunk c, and the parity of its round
   unsigned phc = 0;
-  for (int c = 0; c < nch; ++c) {
+  int c = 0;
+  for (; c < nch; ++c) {
     const int s = sc;
-    // A lane whose wait gives up is dead from then on: it neither waits nor
-    // computes, but walks the remaining chunks with the barrier sequence of
-    // the chunk descriptors (read from global memory), so no consumer is
-    // left waiting at a level barrier.  A warp releases a stage only when
-    // all its lanes saw the stage's data, so the producer never refills a
-    // stage while a copy into it may still be in flight.
-    if (!dead && !mbar_wait(full + s, phc)) {
-      dead = true;
-      atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
+    // a warp any of whose lanes' waits gave up leaves this loop (below)
+    if (__any_sync(0xffffffffu, !mbar_wait(full + s, phc))) {
+      if ((ct & 31) == 0) atomicExch(a.err, (int32_t)DEV_QUEUE_TIMEOUT);
+      break;
     }
-    Chunk m;
-    if (dead) m = a.chunks[ch0 + c];
-    else m = meta[s];
+    const Chunk m = meta[s];
     const int n_lev = chunk_levels(m.nimp_end);
 #ifdef NBTE_CHECKS
     const int level0 = next_level;
@@ -329,7 +322,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     // the ring values the previous one wrote)
     int lb = 0;
     for (int lv = 0; lv < n_lev; ++lv) {
-      const int le = dead ? 0 : lev_end[lv];   // a dead lane has no positions
+      const int le = lev_end[lv];
       for (int j = lb + ct; j < le; j += ncons) {
         uint4 w[NQ];
 #pragma unroll
@@ -422,13 +415,22 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
       if (lv + 1 < n_lev) consumer_barrier(ncons);
       lb = le;
     }
-    const bool all_saw = __all_sync(0xffffffffu, !dead);
-    if (all_saw && (ct & 31) == 0) mbar_arrive(empty + s);
+    __syncwarp();
+    if ((ct & 31) == 0) mbar_arrive(empty + s);
     if (chunk_level_end(m.nimp_end)) consumer_barrier(ncons);
     if (++sc == NS) {
       sc = 0;
       phc ^= 1u;
     }
+  }
+  // A warp whose wait gave up computes nothing more and releases no stage,
+  // but keeps the barrier sequence of the remaining chunks (read from the
+  // chunk descriptors in global memory), so no other consumer is left
+  // waiting at a level barrier.
+  for (; c < nch; ++c) {
+    const Chunk m = a.chunks[ch0 + c];
+    for (int lv = 0; lv + 1 < chunk_levels(m.nimp_end); ++lv) consumer_barrier(ncons);
+    if (chunk_level_end(m.nimp_end)) consumer_barrier(ncons);
   }
 }
 
