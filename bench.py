@@ -149,7 +149,8 @@ def sweep_design_bytes(st, n_cells, n_dirs, prec_bytes, Bp, order=1):
       diagonal G, and K inflow references and coefficients; the 16-byte
       padding of the packed record is not counted) -- the band groups of a
       direction read the same records, which L2 serves after the first;
-    * one collision-moment partial (sweep precision) per (work item, cell);
+    * the per-cell FP64 collision-moment sum once (the sweep's atomic adds
+      resolve in L2);
     * the (T', Qdot) pair of every cell once;
     * the wall/lag import values read and the export values written
       (boundary cells only), all bands.
@@ -159,7 +160,7 @@ def sweep_design_bytes(st, n_cells, n_dirs, prec_bytes, Bp, order=1):
     for the next iteration's gradients."""
     K = st["K"]
     rec = 3 * 4 + prec_bytes + K * (4 + prec_bytes)
-    b = (n_dirs * n_cells * rec + st["items"] * n_cells * prec_bytes + n_cells * 2 * prec_bytes
+    b = (n_dirs * n_cells * rec + n_cells * 8 + n_cells * 2 * prec_bytes
          + (st["exports"] + st["imports"]) * Bp * prec_bytes)
     if order == 2:
         b += 2 * n_dirs * n_cells * Bp * prec_bytes

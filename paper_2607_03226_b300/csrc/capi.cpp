@@ -174,7 +174,7 @@ struct nbte_solver {
   std::vector<int32_t> h_sub_end;
   int64_t gring_stride = 0;
   DBuf item_dir, item_grp, band_v, band_itau, band_aT, band_aQ, band_CoW, band_v64;
-  DBuf expt, impt, srcTQ, srcTQ_fin, part, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
+  DBuf expt, impt, srcTQ, srcTQ_fin, acc, T, Tprev, Tkin, Delta, rhs, delta, Qd, Vd, dsum, accE, accQ, res, heat;
   DBuf perm_d, io_d;   // caller index of each internal cell; caller-order staging on the device
   DBuf cg_r, cg_u, cg_w, cg_p, cg_s, cg_xw, cg_slots, cg_bar, cg_err, cg_it, cg_res;
   DBuf cg_Ainv64;
@@ -240,7 +240,7 @@ size_t device_bytes(const nbte_solver* S) {
                        &S->exp_cell, &S->imp_kind, &S->imp_dbf, &S->imp_src, &S->imp_par, &S->dif_ptr,
                        &S->dif_src, &S->dif_wt, &S->wf_ptr, &S->wf_val, &S->wf_coef, &S->dir_w, &S->dir_s,
                        &S->item_dir, &S->item_grp, &S->band_v, &S->band_itau, &S->band_aT, &S->band_aQ,
-                       &S->band_CoW, &S->band_v64, &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part,
+                       &S->band_CoW, &S->band_v64, &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->acc,
                        &S->T, &S->Tprev, &S->Tkin, &S->Delta, &S->rhs, &S->delta, &S->Qd, &S->Vd, &S->dsum,
                        &S->perm_d, &S->io_d,
                        &S->accE, &S->accQ, &S->res, &S->heat, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s,
@@ -682,7 +682,7 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
     size_t b = D * N * (2 * RL.size + 12 + 2 * sz);                     // records (by position and in chunk
                                                                          // blocks), cells, (cell, pair) index,
                                                                          // (T', Qdot)
-    b += (size_t)D * ng * N * sz;                                        // collision partials
+    b += N * 8;                                                          // collision moment (FP64)
     b += (size_t)ng * (S->n_exp + S->n_imp) * Gp * sz;                   // export / import rows
     if (gr) b += (size_t)D * ng * (((size_t)(S->max_slots + 1) * G + 3) / 4 * 4) * sz;   // global rings
     b += N * (4 * sz + 12 * 8 + 8 * (size_t)S->mesh->m.dim);            // per-cell fields
@@ -760,7 +760,8 @@ int ensure_layout(nbte_solver* S, const nbte_solve_opts& o, size_t* estimate = n
   NBTE_CK(S->impt.alloc((size_t)ng * S->n_imp * S->Gpad * sz));
   NBTE_CK(S->srcTQ.alloc((size_t)2 * N * sz));
   NBTE_CK(S->srcTQ_fin.alloc((size_t)2 * N * sz));
-  NBTE_CK(S->part.alloc((size_t)S->n_items * N * sz));
+  NBTE_CK(S->acc.alloc((size_t)N * 8));
+  NBTE_CK(cudaMemsetAsync(S->acc.p, 0, (size_t)N * 8, S->stream));
   if (gr) {
     NBTE_CK(S->gring.alloc((size_t)S->n_items * S->gring_stride * sz));
   } else {
@@ -1114,7 +1115,7 @@ SweepArgs<R> sweep_args(nbte_solver* S, int full) {
   a.band_aQ = S->band_aQ.as<R>();
   a.dir_w = S->dir_w.as<double>();
   a.dir_s = S->dir_s.as<double>();
-  a.part = S->part.as<R>();
+  a.acc = S->acc.as<double>();
   a.gring = S->gring.p ? S->gring.as<R>() : nullptr;
   a.gring_stride = S->gring_stride;
   a.accE = S->accE.as<double>();
@@ -1162,7 +1163,7 @@ UpdateArgs<R> update_args(nbte_solver* S, int mode) {
   a.mode = mode;
   a.beta = S->beta;
   a.inv_beta = 1.0 / S->beta;
-  a.part = S->part.as<R>();
+  a.acc = S->acc.as<double>();
   a.Q = S->Qd.as<double>();
   a.V = S->Vd.as<double>();
   a.T = S->T.as<double>();
@@ -1542,6 +1543,9 @@ int run_begin(Run& run, nbte_solver* S, const nbte_solve_opts& o) {
     launch_fill_srcTQ<R>(S->srcTQ.as<R>(), S->T.as<double>(), S->Qd.as<double>(), (int)S->mesh->m.n_cells, st);
   }
   if (S->cg_it.p) NBTE_CK(cudaMemsetAsync(S->cg_it.p, 0, 4, st));
+  // the sweeps add into the collision-moment sums and the update clears them;
+  // a timing sweep or a sweep that gave up leaves them dirty
+  NBTE_CK(cudaMemsetAsync(S->acc.p, 0, (size_t)S->mesh->m.n_cells * 8, st));
   run.t0 = std::chrono::steady_clock::now();
   return NBTE_OK;
 }
@@ -1911,7 +1915,7 @@ void shrink(nbte_solver* S) {
   drop_graph(S);
   DBuf* big[] = {&S->rec_pos, &S->rec, &S->pos_cell, &S->gring, &S->e_scratch, &S->chunks, &S->chunk_off,
                  &S->chunk_doff, &S->chunk_dir, &S->chunk_sub_ptr, &S->chunk_sub_end, &S->tq_dst,
-                 &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->part, &S->Tprev, &S->Delta, &S->rhs,
+                 &S->expt, &S->impt, &S->srcTQ, &S->srcTQ_fin, &S->acc, &S->Tprev, &S->Delta, &S->rhs,
                  &S->delta, &S->dsum, &S->cg_r, &S->cg_u, &S->cg_p, &S->cg_s, &S->cg_w, &S->cg_x, &S->cg_xw,
                  &S->cg_rw, &S->cg_rcx, &S->cg_scx, &S->cg_Ainv, &S->cg_Ainv64, &S->L_ecol, &S->L_eval,
                  &S->L_diag, &S->L_dinv, &S->cg_perm, &S->cg_agg_rel, &S->cg_agg_cell, &S->cg_blk_cell,

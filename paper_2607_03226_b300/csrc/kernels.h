@@ -104,7 +104,7 @@ struct UpdateArgs {
   int N, n_items;
   int mode;                      // 0 sequential, 1 synthetic (DSA), 2 synthetic (literal), 3 rhs only
   double inv_beta, beta;
-  const R* part;
+  double* acc;                   // [N] collision moment of e - e0 (read, then cleared)
   const double* Q;
   const double* V;
   double* T;                     // T' iterate (in/out)

@@ -14,6 +14,15 @@
 //    inflow faces from unprocessed cells are marked "lagged": their upwind
 //    value is taken from the previous iteration.  Structured and 2D meshes
 //    have none.
+//  * tilted fronts: where a direction's level fronts are wide (many cells
+//    live at once), each cell may also be given a release level that grows
+//    along the mesh's longest axis, level(c) = max(release(c), 1 + max over
+//    upstream u of level(u)).  Any such assignment is a topological order of
+//    the same graph, so the sweep computes the same values; the fronts lean
+//    along the long axis and cross the mesh where it is narrow, which cuts
+//    the live cells (ring slots) severalfold for a few more levels.  The
+//    release slope is chosen per direction from a few candidates: fewest
+//    live cells without more levels than the longest untilted direction.
 //  * ring slots: a cell's value lives in shared memory from its own level to
 //    the last level that reads it; slots are reused (interval colouring), so
 //    a sweep needs only max-live-cells slots, not N.
@@ -27,6 +36,7 @@
 #include <array>
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <thread>
 
@@ -55,6 +65,10 @@ struct DirOut {
 };
 
 constexpr double kTangent = 1e-12;   // |s.An| <= kTangent |An| counts as no flux
+// directions with more live cells than this (untilted) try tilted fronts
+constexpr int32_t kTiltLive = 4096;
+// release slopes tried, in levels per cell length along the long axis
+constexpr double kTiltSlopes[] = {1.0, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0, 16.0};
 
 }  // namespace
 
@@ -148,13 +162,41 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
   P.pos_coef.assign((size_t)D * K * N, 0.0);
   std::vector<DirOut> outs(D);
 
-  auto work = [&](int tid, int nt) {
-    std::vector<int32_t> indeg(N), level(N), slot(N), last_use(N), exp_local(N);
+  // tilted fronts: the longest axis of the mesh's bounding box and a cell
+  // length (the release level of cell c is slope * (x_c - x_min) / h along it,
+  // x measured in the direction's own sense along the axis)
+  // NBTE_PLAN_TILT: "0" plans untilted levels only; "force" (for testing)
+  // tilts every direction, with the steepest slope within the level cap
+  // whether or not it saves live cells
+  const char* tilt_env = std::getenv("NBTE_PLAN_TILT");
+  const bool tilt = !(tilt_env && tilt_env[0] == '0');
+  const bool tilt_force = tilt_env && std::string(tilt_env) == "force";
+  const int32_t tilt_live = tilt_force ? -1 : kTiltLive;
+  int tilt_axis = 0;
+  double bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};
+  for (int d = 0; d < dim; ++d) {
+    bb_lo[d] = INFINITY;
+    bb_hi[d] = -INFINITY;
+    for (int64_t c = 0; c < N; ++c) {
+      bb_lo[d] = std::min(bb_lo[d], m.xc[c * dim + d]);
+      bb_hi[d] = std::max(bb_hi[d], m.xc[c * dim + d]);
+    }
+    if (bb_hi[d] - bb_lo[d] > bb_hi[tilt_axis] - bb_lo[tilt_axis]) tilt_axis = d;
+  }
+  const double hcell = std::pow(m.volume / (double)std::max<int64_t>(N, 1), 1.0 / dim);
+  std::vector<int32_t> untilted_levels(D, 0);
+  int32_t level_cap = 0;   // the longest untilted direction's level count
+
+  // pass 0: Kahn level counts only (they set level_cap); pass 1: the plan
+  auto work = [&](int tid, int nt, int pass) {
+    std::vector<int32_t> indeg(N), level(N), slot(N), last_use(N), exp_local(N), cand, best, occ;
     std::vector<char> lagged(H);
+    std::vector<signed char> fcls(H);
     std::vector<int32_t> order, cur, next, free_slots;
     std::vector<std::vector<int32_t>> release;
     for (int i = tid; i < D; i += nt) {
       DirOut& o = outs[i];
+      o = DirOut();
       std::fill(indeg.begin(), indeg.end(), 0);
       std::fill(level.begin(), level.end(), -1);
       std::fill(lagged.begin(), lagged.end(), 0);
@@ -204,7 +246,102 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
         std::sort(next.begin(), next.end());
         cur.swap(next);
       }
-      const int L = (int)o.lp.size() - 1;
+      if (pass == 0) {
+        untilted_levels[i] = (int32_t)o.lp.size() - 1;
+        continue;
+      }
+      int L = (int)o.lp.size() - 1;
+      // ---- tilted fronts (release levels along the long axis), see the
+      // file comment.  `order` is topological for the non-lagged edges.
+      for (int64_t h = 0; h < H; ++h) fcls[h] = (signed char)cls(dotsa(i, h), h);
+      // levels with release slope `slope` (0: none), then as late as
+      // possible; returns the level count
+      auto relevel = [&](double slope, std::vector<int32_t>& lev) -> int {
+        const double sg = s[i * 3 + tilt_axis] >= 0 ? 1.0 : -1.0;
+        const double x0 = sg > 0 ? bb_lo[tilt_axis] : -bb_hi[tilt_axis];
+        lev.resize(N);
+        for (int64_t p = 0; p < N; ++p) {
+          const int32_t c = order[p];
+          int32_t l = slope > 0 ? (int32_t)std::floor(slope * (sg * m.xc[(int64_t)c * dim + tilt_axis] - x0) / hcell)
+                                : 0;
+          for (int k = 0; k < nfc; ++k) {
+            const int64_t h = (int64_t)c * nfc + k;
+            if (fcls[h] < 0 && m.nb[h] >= 0 && !lagged[h]) l = std::max(l, lev[m.nb[h]] + 1);
+          }
+          lev[c] = l;
+        }
+        for (int64_t p = N - 1; p >= 0; --p) {
+          const int32_t u = order[p];
+          int32_t first = INT32_MAX;
+          for (int k = 0; k < nfc; ++k) {
+            const int64_t h = (int64_t)u * nfc + k;
+            const int64_t v = m.nb[h];
+            if (v < 0 || fcls[h] <= 0 || lagged[m.twin[h]]) continue;
+            first = std::min(first, lev[v]);
+          }
+          if (first != INT32_MAX && first - 1 > lev[u]) lev[u] = first - 1;
+        }
+        // drop empty levels (release levels can leave gaps)
+        int32_t top = 0;
+        for (int64_t c = 0; c < N; ++c) top = std::max(top, lev[c]);
+        occ.assign(top + 1, 0);
+        for (int64_t c = 0; c < N; ++c) occ[lev[c]] = 1;
+        int32_t used = 0;
+        for (int32_t l = 0; l <= top; ++l) {
+          const int32_t u = occ[l];
+          occ[l] = used;
+          used += u;
+        }
+        for (int64_t c = 0; c < N; ++c) lev[c] = occ[lev[c]];
+        return used;
+      };
+      // most cells live at once (value written, a reader still to come)
+      auto live_of = [&](const std::vector<int32_t>& lev, int nl) -> int32_t {
+        occ.assign(nl + 1, 0);
+        for (int64_t c = 0; c < N; ++c) {
+          int32_t last = -1;
+          for (int k = 0; k < nfc; ++k) {
+            const int64_t h = c * nfc + k;
+            const int64_t v = m.nb[h];
+            if (v < 0 || fcls[h] <= 0 || lagged[m.twin[h]]) continue;
+            last = std::max(last, lev[v]);
+          }
+          if (last >= 0) {
+            occ[lev[c]]++;
+            occ[last + 1]--;
+          }
+        }
+        int32_t run = 0, mx = 0;
+        for (int l = 0; l < nl; ++l) mx = std::max(mx, run += occ[l]);
+        return mx;
+      };
+      if (tilt) {
+        int nl0 = relevel(0.0, best);
+        int32_t live_best = live_of(best, nl0);
+        int nl_best = nl0;
+        if (live_best > tilt_live) {
+          for (double slope : kTiltSlopes) {
+            const int nl = relevel(slope, cand);
+            if (nl > level_cap) break;
+            const int32_t lv = live_of(cand, nl);
+            if (lv < live_best || tilt_force) {
+              live_best = lv;
+              nl_best = nl;
+              best.swap(cand);
+            }
+          }
+        }
+        std::copy(best.begin(), best.end(), level.begin());
+        L = nl_best;
+        // level lists (stable in topological order within a level)
+        std::vector<int32_t> cnt(L + 1, 0);
+        for (int64_t c = 0; c < N; ++c) cnt[level[c] + 1]++;
+        for (int l = 0; l < L; ++l) cnt[l + 1] += cnt[l];
+        o.lp.assign(cnt.begin(), cnt.end());
+        std::vector<int32_t> reord(N);
+        for (int64_t p = 0; p < N; ++p) reord[cnt[level[order[p]]]++] = order[p];
+        order.swap(reord);
+      }
       // ---- push producers down to just before their first consumer (as
       // late as possible), visiting cells in reverse level order: a value then
       // lives in the ring for fewer levels, and the dependency order is kept
@@ -338,10 +475,13 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
     }
   };
   n_threads = std::max(1, std::min(n_threads, D));
-  std::vector<std::thread> th;
-  for (int t = 1; t < n_threads; ++t) th.emplace_back(work, t, n_threads);
-  work(0, n_threads);
-  for (auto& t : th) t.join();
+  for (int pass = tilt ? 0 : 1; pass < 2; ++pass) {
+    std::vector<std::thread> th;
+    for (int t = 1; t < n_threads; ++t) th.emplace_back(work, t, n_threads, pass);
+    work(0, n_threads, pass);
+    for (auto& t : th) t.join();
+    if (pass == 0) level_cap = *std::max_element(untilted_levels.begin(), untilted_levels.end());
+  }
   for (auto& o : outs)
     if (!o.error.empty()) return Status::err(NBTE_ERR_MESH, o.error);
 

@@ -33,7 +33,8 @@
 // src2 = 0 for first-order upwind; with second-order face values it is the
 // reconstruction increment of every interior face taken from the previous
 // iteration's gradients (deferred correction, see launch_src2).
-// The collision-moment partial is sum_l w_i (e - e0)/tau_l; the equilibrium
+// Each position adds its collision-moment share sum_l w_i (e - e0)/tau_l to
+// the cell's FP64 sum over all work items (one atomic add); the equilibrium
 // part sums to beta T' exactly and is added back in FP64 by the update kernel.
 #include <cuda_runtime.h>
 
@@ -95,6 +96,28 @@ __device__ __forceinline__ float recip(float x) {
 }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// exact FP32 -> FP64 widening by the IEEE-754 field layout (8-bit exponent
+// rebiased by 1023 - 127, 23-bit fraction shifted into the 52-bit one) in
+// integer instructions: the conversion instruction would run on the FP64
+// pipe, which has a small fraction of the FP32 rate on this part.  Zero and
+// FP32 subnormals (below 1.2e-38, far under any collision moment) give a
+// signed zero; infinities and NaNs keep their class.
+__device__ __forceinline__ double widen(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  const uint32_t sg = u & 0x80000000u;
+  uint32_t hi = sg | ((ex + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  uint32_t lo = u << 29;
+  if (ex == 0u) {
+    hi = sg;
+    lo = 0u;
+  } else if (ex == 0xffu) {
+    hi |= 0x7ff00000u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 // word idx (4-byte units) of a record held in registers; idx is a
 // compile-time constant after unrolling, so this folds to a register move
 template <int NQ>
@@ -127,7 +150,7 @@ struct RecField<double> {
 }  // namespace
 
 // One work item (direction i, band group g) of one solver; the whole CTA.
-// MODE selects the outputs beyond the collision partials: 0 none, 1 every
+// MODE selects the outputs beyond the collision moment: 0 none, 1 every
 // outgoing value to e_out, 2 the energy and flux moments.  Second order
 // always writes e_out (the next iteration's gradients read it).  They are
 // compile-time switches: behind runtime flags the compiler evaluated their
@@ -272,7 +295,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     aQ[b] = a.band_aQ[band0 + b];
     wt[b] = (R)(wi * (double)itau[b]);
   }
-  R* part = a.part + (int64_t)item * a.N;
+  double* acc = a.acc;
   R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * GP;
 #ifdef NBTE_CHECKS
   // every slot of this item's ring: not written yet, no reader left
@@ -398,7 +421,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
                                  (size_t)cell * a.e_out_cstride,
                              e);
         }
-        part[cell] = nl;
+        // the collision moment of Eq. (5): one FP64 atomic add per position
+        // into the per-cell sum over every (direction, band group); the
+        // output sweep (MODE 2) does not need it
+        if constexpr (MODE != 2) atomicAdd(acc + cell, widen(nl));
         // energy and flux moments, Eq. (7): the output sweep only
         if constexpr (MODE == 2) {
           R es = R(0), evs = R(0);

@@ -59,15 +59,15 @@ def test_sweep_bytes_by_hand():
     """The roofline's bytes: the scope table's 8 B (FP32) / 16 B (FP64) per
     band-direction cell update.  Beside it, this design's own minimum for the
     32^3 cube's sweep, item by item: records (cell, slot, export, G and three
-    inflow (reference, coefficient) pairs = 40 B) per (direction, cell), one
-    FP32 partial per (work item, cell), the (T', Qdot) pairs, and the wall
-    rows of all bands."""
+    inflow (reference, coefficient) pairs = 40 B) per (direction, cell), the
+    per-cell FP64 collision-moment sum once, the (T', Qdot) pairs, and the
+    wall rows of all bands."""
     N, D, Bp = 32768, 128, 40
     assert bench.sweep_algorithmic_bytes(N * D * Bp, 4) == 8 * N * D * Bp
     assert bench.sweep_algorithmic_bytes(N * D * Bp, 8) == 16 * N * D * Bp
     st = {"K": 3, "items": 1280, "exports": 381056, "imports": 393216}
-    expect = D * N * 40 + 1280 * N * 4 + N * 8 + (381056 + 393216) * Bp * 4
-    assert bench.sweep_design_bytes(st, N, D, 4, Bp) == expect == 459689984
+    expect = D * N * 40 + N * 8 + N * 8 + (381056 + 393216) * Bp * 4
+    assert bench.sweep_design_bytes(st, N, D, 4, Bp) == expect == 292179968
     # second order adds the source read and the distribution kept, per band
     assert bench.sweep_design_bytes(st, N, D, 4, Bp, order=2) == expect + 2 * D * N * Bp * 4
     # FP operations per update: one FMA per inflow face (half the faces) + 7

@@ -9,7 +9,10 @@ The checks library runs in a child process (a process loads one build of the
 library): three sequential iterations on the small parity cases and the
 cyclic mesh, shared and global value rings, several launch layouts, FP64 and
 FP32, first and second order and a batched solve; every solve must pass its
-checks and agree with the oracle as the normal build does."""
+checks and agree with the oracle as the normal build does.  It runs once with
+the default plan and once with tilted fronts forced on every direction
+(NBTE_PLAN_TILT=force: release levels along the mesh's long axis), which
+reorders levels and ring slots but must leave every check and result intact."""
 import json
 import os
 import subprocess
@@ -61,8 +64,12 @@ print("RESULTS " + json.dumps(out))
 """
 
 
-def test_sweep_checks_pass_on_every_layout(gpu_lib):
+@pytest.mark.parametrize("tilt", ["default", "force"])
+def test_sweep_checks_pass_on_every_layout(gpu_lib, tilt):
     env = dict(os.environ)
+    env.pop("NBTE_PLAN_TILT", None)
+    if tilt == "force":
+        env["NBTE_PLAN_TILT"] = "force"
     r = subprocess.run([sys.executable, "-c", "ROOT = %r\n" % ROOT + SCRIPT], capture_output=True, text=True,
                        env=env, timeout=1800)
     assert r.returncode == 0, r.stderr[-3000:]

@@ -134,8 +134,10 @@ def test_order2_warm_start_continues(nbte_mod):
 def test_hex_gradients_in_direction_batches(nbte_mod, monkeypatch, precision):
     """Hexahedra compute the reconstruction gradients in direction batches
     sized by a memory budget.  A budget of one byte (one direction per
-    batch) gives bitwise the same second-order iterations as one batch of
-    all directions."""
+    batch) gives the same second-order iterations as one batch of all
+    directions: to FP64 rounding (1e-12) in FP64; in FP32 the order of the
+    FP64 atomic adds of the collision moment can move an FP32-rounded
+    temperature by one unit in the last place (1e-6)."""
     p = CASES["cube_hex"]()
     s = nbte_mod.Solver(p)
     s.solve(scheme="sequential", precision=precision, n_iter=3, order=2)
@@ -145,13 +147,14 @@ def test_hex_gradients_in_direction_batches(nbte_mod, monkeypatch, precision):
     s = nbte_mod.Solver(p)
     info = s.solve(scheme="sequential", precision=precision, n_iter=3, order=2)
     assert info["status"] == 0
-    assert np.array_equal(s.temperature(0), T_one)
+    assert rel_T(s.temperature(0), T_one, p.T_ref) <= (1e-12 if precision == "fp64" else 1e-6)
     s.close()
 
 
 def test_order2_in_a_batch(nbte_mod):
     """A second-order solve batched with first-order ones (fused sweep
-    launches) equals the same solve alone; the first-order solves too."""
+    launches) equals the same solve alone, to FP64 rounding (the order of
+    the collision moment's atomic adds varies); the first-order solves too."""
     probs = [CASES[n]() for n in ("square_mixed", "fin2d_mixed", "cube_hex")]
     orders = [2, 1, 2]
     alone = []
@@ -167,8 +170,8 @@ def test_order2_in_a_batch(nbte_mod):
         infos = nbte_mod.solve_batch(sel, scheme="sequential", precision="fp64", n_iter=3, band_group=2,
                                      cta_threads=160, order=o)
         assert all(i["status"] == 0 for i in infos)
-    for s, T in zip(ss, alone):
-        assert np.array_equal(s.temperature(0), T)
+    for p, s, T in zip(probs, ss, alone):
+        assert rel_T(s.temperature(0), T, p.T_ref) <= 1e-12
         s.close()
 
 
