@@ -175,6 +175,15 @@ int nbte_set_heat_source(nbte_solver* solver, const double* Qdot);
  *            gradient, which keeps the lagged correction contracting on
  *            unstructured meshes.  Holds one more distribution and one
  *            source per (work item, position) on the device.
+ * deterministic: how the sweep sums the collision moment of Eq. (5) over
+ *            work items.  0 (default) = by the layout's size: when one
+ *            partial per (work item, cell) takes at most 256 MB, the sweep
+ *            writes them and the update kernel sums each cell's in a fixed
+ *            order (results reproducible bit for bit); above that, FP64
+ *            atomic adds into one sum per cell, whose order, and so whose
+ *            last bits, vary from run to run (about 1e-16 relative in FP64;
+ *            an FP32 sweep may then round a temperature to the neighbouring
+ *            FP32 value).  1 = always the fixed-order partials.
  * cg_tol, cg_max_iter: relative residual and cap of the conjugate-gradient
  *            solve of the synthetic correction (0 = defaults 1e-2, 5000); the
  *            correction only changes the rate of convergence, not the limit.
@@ -209,6 +218,7 @@ typedef struct {
   int32_t ring;
   int32_t init;
   int32_t order;
+  int32_t deterministic;
 } nbte_solve_opts;
 
 /* Filled on return from nbte_solve_steady (also on NOT_CONVERGED):

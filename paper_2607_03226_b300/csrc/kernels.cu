@@ -115,26 +115,144 @@ void launch_walls(const WallArgs<R>& a, cudaStream_t st) {
 }
 
 // ============================================================================ update
-// One thread per cell, blocks of kUpdThreads.  In the reducing modes (0 and
-// 3) the thread takes the cell's collision moment, which the sweep summed in
-// FP64 over every work item, and clears it for the next sweep.
-constexpr int kUpdThreads = 256;
+// One block per 32 cell slots (V cells each: V = 2 for FP32 partials with an
+// even cell count, read as float2, else 1).  The collision moment comes in one
+// of two forms:
+//  * per-cell FP64 sums of the sweep's atomic adds (part null): read, then
+//    cleared for the next sweep;
+//  * per-(work item, cell) partials (deterministic): summed by 8 item slices
+//    per cell and combined in shared memory in a fixed order; one warp then
+//    applies the update.  FP32 partials are summed with compensation (Kahan)
+//    in FP32, which keeps the sum to FP32 rounding of the total while
+//    spending no FP64 instruction per partial; FP64 partials are summed in
+//    FP64.  Every cell's summation order is the same for V = 1 and V = 2.
+constexpr int kUpdCells = 32, kUpdSlices = 8;
 
-template <typename R>
-__global__ void __launch_bounds__(kUpdThreads) update_kernel(const UpdateArgs<R> a) {
-  const int c = blockIdx.x * kUpdThreads + threadIdx.x;
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <int V>
+__device__ __forceinline__ void load_part(const float* p, int64_t k, float (&x)[V]) {
+  if constexpr (V == 2) {
+    const float2 v = __ldcs(reinterpret_cast<const float2*>(p) + k);
+    x[0] = v.x;
+    x[1] = v.y;
+  } else {
+    x[0] = __ldcs(p + k);
+  }
+}
+
+template <typename R, int V>
+__global__ void __launch_bounds__(kUpdCells * kUpdSlices) update_kernel(const UpdateArgs<R> a) {
+  static_assert(V == 1 || (V == 2 && sizeof(R) == 4), "two cells per thread with FP32 partials only");
+  const int c0 = (blockIdx.x * kUpdCells + threadIdx.x) * V;
   const bool reduce = a.mode == 0 || a.mode == 3;
+  double s[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) s[v] = 0.0;
+  if (reduce && a.part == nullptr) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int c = c0 + v;
+      if (c < a.N) {
+        s[v] = a.acc[c];
+        a.acc[c] = 0.0;
+      }
+    }
+  } else if (reduce) {
+    if constexpr (sizeof(R) == 4) {
+      __shared__ float red_s[kUpdSlices][V][kUpdCells], red_c[kUpdSlices][V][kUpdCells];
+      float ks[V], kc[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) ks[v] = kc[v] = 0.0f;
+      if (c0 < a.N) {
+        // in units of V floats: the row of item it starts at it * (N / V)
+        const float* p = a.part + c0;
+        const int64_t NV = a.N / V;
+        int it = threadIdx.y;
+        for (; it + 3 * kUpdSlices < a.n_items; it += 4 * kUpdSlices) {
+          float x0[V], x1[V], x2[V], x3[V];
+          load_part<V>(p, it * NV, x0);
+          load_part<V>(p, (it + kUpdSlices) * NV, x1);
+          load_part<V>(p, (it + 2 * kUpdSlices) * NV, x2);
+          load_part<V>(p, (it + 3 * kUpdSlices) * NV, x3);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            kahan_add(ks[v], kc[v], x0[v]);
+            kahan_add(ks[v], kc[v], x1[v]);
+            kahan_add(ks[v], kc[v], x2[v]);
+            kahan_add(ks[v], kc[v], x3[v]);
+          }
+        }
+        for (; it < a.n_items; it += kUpdSlices) {
+          float x[V];
+          load_part<V>(p, it * NV, x);
+#pragma unroll
+          for (int v = 0; v < V; ++v) kahan_add(ks[v], kc[v], x[v]);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        red_s[threadIdx.y][v][threadIdx.x] = ks[v];
+        red_c[threadIdx.y][v][threadIdx.x] = kc[v];
+      }
+      __syncthreads();
+      if (threadIdx.y != 0) return;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        float ts = 0.0f, tc = 0.0f;
+#pragma unroll
+        for (int y = 0; y < kUpdSlices; ++y) {
+          kahan_add(ts, tc, red_s[y][v][threadIdx.x]);
+          kahan_add(ts, tc, -red_c[y][v][threadIdx.x]);
+        }
+        s[v] = (double)ts - (double)tc;
+      }
+    } else {
+      __shared__ double red[kUpdSlices][kUpdCells];
+      double t = 0.0;
+      if (c0 < a.N) {
+        const R* p = a.part + c0;
+        const int64_t N = a.N;
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+        int it = threadIdx.y;
+        for (; it + 3 * kUpdSlices < a.n_items; it += 4 * kUpdSlices) {
+          acc0 += __ldcs(p + it * N);
+          acc1 += __ldcs(p + (it + kUpdSlices) * N);
+          acc2 += __ldcs(p + (it + 2 * kUpdSlices) * N);
+          acc3 += __ldcs(p + (it + 3 * kUpdSlices) * N);
+        }
+        for (; it < a.n_items; it += kUpdSlices) acc0 += __ldcs(p + it * N);
+        t = (acc0 + acc1) + (acc2 + acc3);
+      }
+      red[threadIdx.y][threadIdx.x] = t;
+      __syncthreads();
+      if (threadIdx.y != 0) return;
+      t = 0.0;
+#pragma unroll
+      for (int y = 0; y < kUpdSlices; ++y) t += red[y][threadIdx.x];
+      s[0] = t;
+    }
+  } else if (threadIdx.y != 0) {
+    return;
+  }
+  // one warp per block from here on
   double dmax = 0.0, tmax = 0.0;
-  if (c < a.N) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int c = c0 + v;
+    if (c >= a.N) break;
     const double Told = a.T[c];
     double TL = 0.0;
     if (reduce) {
-      const double s = a.acc[c];
-      a.acc[c] = 0.0;
       // Eq. (5) as a deviation from T_ref: the equilibrium part of every
       // distribution sums to beta T'_used, T'_used being the (possibly
       // reduced-precision) temperature the sweep emitted from
-      TL = (double)a.srcTQ_next[2 * c] + s * a.inv_beta;
+      TL = (double)a.srcTQ_next[2 * c] + s[v] * a.inv_beta;
       a.Tkin[c] = TL;
       // the first update of an iteration keeps the iterate the sweep started
       // from (the final moments replay that sweep)
@@ -151,8 +269,8 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const UpdateArgs<R>
       a.Delta[c] = Tn - TL;
       double d = fabs(Tn - Told), t = fabs(Tn);
       if (!isfinite(d) || !isfinite(t)) d = t = CUDART_INF;
-      dmax = d;
-      tmax = t;
+      dmax = fmax(dmax, d);
+      tmax = fmax(tmax, t);
       a.T[c] = Tn;
       a.srcTQ_next[2 * c] = (R)Tn;
       a.srcTQ_next[2 * c + 1] = (R)a.Q[c];
@@ -163,7 +281,7 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const UpdateArgs<R>
       dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
       tmax = fmax(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (threadIdx.x == 0) {
       // non-negative doubles order like their bit patterns; NaN sorts above +inf
       atomicMax(a.res, (unsigned long long)__double_as_longlong(dmax));
       atomicMax(a.res + 1, (unsigned long long)__double_as_longlong(tmax));
@@ -173,8 +291,16 @@ __global__ void __launch_bounds__(kUpdThreads) update_kernel(const UpdateArgs<R>
 
 template <typename R>
 void launch_update(const UpdateArgs<R>& a, cudaStream_t st) {
-  update_kernel<R><<<(a.N + kUpdThreads - 1) / kUpdThreads, kUpdThreads, 0, st>>>(a);
+  const bool reduce = a.mode == 0 || a.mode == 3;
+  const dim3 block(kUpdCells, reduce && a.part ? kUpdSlices : 1);
+  if (sizeof(R) == 4 && a.N % 2 == 0) {
+    const int slots = a.N / 2;
+    update_kernel<R, (sizeof(R) == 4 ? 2 : 1)><<<(slots + kUpdCells - 1) / kUpdCells, block, 0, st>>>(a);
+  } else {
+    update_kernel<R, 1><<<(a.N + kUpdCells - 1) / kUpdCells, block, 0, st>>>(a);
+  }
 }
+
 
 template <typename R>
 __global__ void fill_srcTQ_kernel(R* srcTQ, const double* T, const double* Q, int N) {

@@ -104,7 +104,8 @@ struct UpdateArgs {
   int N, n_items;
   int mode;                      // 0 sequential, 1 synthetic (DSA), 2 synthetic (literal), 3 rhs only
   double inv_beta, beta;
-  double* acc;                   // [N] collision moment of e - e0 (read, then cleared)
+  const R* part;                 // [n_items*N] collision-moment partials of e - e0, or null:
+  double* acc;                   // [N] their FP64 sums from the sweep's atomic adds (read, then cleared)
   const double* Q;
   const double* V;
   double* T;                     // T' iterate (in/out)

@@ -34,7 +34,8 @@
 // reconstruction increment of every interior face taken from the previous
 // iteration's gradients (deferred correction, see launch_src2).
 // Each position adds its collision-moment share sum_l w_i (e - e0)/tau_l to
-// the cell's FP64 sum over all work items (one atomic add); the equilibrium
+// the cell's FP64 sum over all work items (one atomic add), or writes it as
+// the (work item, cell) partial of the deterministic form; the equilibrium
 // part sums to beta T' exactly and is added back in FP64 by the update kernel.
 #include <cuda_runtime.h>
 
@@ -295,6 +296,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     aQ[b] = a.band_aQ[band0 + b];
     wt[b] = (R)(wi * (double)itau[b]);
   }
+  R* part = a.part ? a.part + (int64_t)item * a.N : nullptr;
   double* acc = a.acc;
   R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * GP;
 #ifdef NBTE_CHECKS
@@ -421,10 +423,15 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
                                  (size_t)cell * a.e_out_cstride,
                              e);
         }
-        // the collision moment of Eq. (5): one FP64 atomic add per position
-        // into the per-cell sum over every (direction, band group); the
-        // output sweep (MODE 2) does not need it
-        if constexpr (MODE != 2) atomicAdd(acc + cell, widen(nl));
+        // the collision moment of Eq. (5) (the output sweep, MODE 2, does not
+        // need it): one FP64 atomic add per position into the cell's sum over
+        // every (direction, band group), or, in the deterministic form, one
+        // partial per (work item, cell) that the update kernel sums in a
+        // fixed order
+        if constexpr (MODE != 2) {
+          if (part) part[cell] = nl;
+          else atomicAdd(acc + cell, widen(nl));
+        }
         // energy and flux moments, Eq. (7): the output sweep only
         if constexpr (MODE == 2) {
           R es = R(0), evs = R(0);

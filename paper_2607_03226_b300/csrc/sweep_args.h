@@ -58,8 +58,10 @@ struct SweepArgs {
   int64_t e_out_dstride, e_out_gstride, e_out_cstride;   // (direction i, band group g)
   R* gring;                      // global-memory value rings, or null for the shared-memory ring
   int64_t gring_stride;          // elements per CTA's global ring
-  double* acc;                   // [N] collision moment of e - e0, accumulated over every work item
-                                 // (FP64 atomic adds; the update kernel reads and clears it)
+  R* part;                       // [n_items*N] collision-moment partials of e - e0 (deterministic
+                                 // form), or null: then
+  double* acc;                   // [N] the collision moment summed over every work item by FP64
+                                 // atomic adds (the update kernel reads and clears it)
   double* accE;                  // [N]   (full)
   double* accQ;                  // [N*dim] (full)
   int32_t* err;                  // device error word

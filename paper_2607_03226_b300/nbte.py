@@ -53,7 +53,7 @@ class nbte_solve_opts(C.Structure):
                 ("warm", C.c_int32), ("band_group", C.c_int32), ("threads_per_cell", C.c_int32),
                 ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("use_graph", C.c_int32),
                 ("skip_outputs", C.c_int32), ("profile", C.c_int32), ("cta_threads", C.c_int32),
-                ("ring", C.c_int32), ("init", C.c_int32), ("order", C.c_int32)]
+                ("ring", C.c_int32), ("init", C.c_int32), ("order", C.c_int32), ("deterministic", C.c_int32)]
 
 
 class nbte_solve_info(C.Structure):
@@ -224,7 +224,8 @@ def nbte_default_opts():
 
 def make_opts(scheme="sequential", precision="fp64", tol=1e-10, max_iter=10000, n_iter=0, T_init=None,
               warm=False, band_group=0, threads_per_cell=0, cg_tol=0.0, cg_max_iter=0, use_graph=False,
-              skip_outputs=False, profile=False, cta_threads=0, ring=0, init="tref", order=1):
+              skip_outputs=False, profile=False, cta_threads=0, ring=0, init="tref", order=1,
+              deterministic=False):
     o = nbte_default_opts()
     o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     o.precision = {"fp64": 0, "fp32": 1}[precision] if isinstance(precision, str) else int(precision)
@@ -235,6 +236,7 @@ def make_opts(scheme="sequential", precision="fp64", tol=1e-10, max_iter=10000, 
     o.ring = {"auto": 0, "shared": 1, "global": 2}[ring] if isinstance(ring, str) else int(ring)
     o.init = {"tref": 0, "fourier": 1}[init] if isinstance(init, str) else int(init)
     o.order = int(order)
+    o.deterministic = int(bool(deterministic))
     keep = None
     if T_init is not None:
         keep, o.T_init = _d(T_init)

@@ -134,33 +134,31 @@ def test_order2_warm_start_continues(nbte_mod):
 def test_hex_gradients_in_direction_batches(nbte_mod, monkeypatch, precision):
     """Hexahedra compute the reconstruction gradients in direction batches
     sized by a memory budget.  A budget of one byte (one direction per
-    batch) gives the same second-order iterations as one batch of all
-    directions: to FP64 rounding (1e-12) in FP64; in FP32 the order of the
-    FP64 atomic adds of the collision moment can move an FP32-rounded
-    temperature by one unit in the last place (1e-6)."""
+    batch) gives bitwise the same second-order iterations as one batch of
+    all directions (fixed-order collision moment)."""
     p = CASES["cube_hex"]()
     s = nbte_mod.Solver(p)
-    s.solve(scheme="sequential", precision=precision, n_iter=3, order=2)
+    s.solve(scheme="sequential", precision=precision, n_iter=3, order=2, deterministic=True)
     T_one = s.temperature(0)
     s.close()
     monkeypatch.setenv("NBTE_O2_GRAD_BYTES", "1")
     s = nbte_mod.Solver(p)
-    info = s.solve(scheme="sequential", precision=precision, n_iter=3, order=2)
+    info = s.solve(scheme="sequential", precision=precision, n_iter=3, order=2, deterministic=True)
     assert info["status"] == 0
-    assert rel_T(s.temperature(0), T_one, p.T_ref) <= (1e-12 if precision == "fp64" else 1e-6)
+    assert np.array_equal(s.temperature(0), T_one)
     s.close()
 
 
 def test_order2_in_a_batch(nbte_mod):
     """A second-order solve batched with first-order ones (fused sweep
-    launches) equals the same solve alone, to FP64 rounding (the order of
-    the collision moment's atomic adds varies); the first-order solves too."""
+    launches) equals the same solve alone; the first-order solves too."""
     probs = [CASES[n]() for n in ("square_mixed", "fin2d_mixed", "cube_hex")]
     orders = [2, 1, 2]
     alone = []
     for p, o in zip(probs, orders):
         s = nbte_mod.Solver(p)
-        s.solve(scheme="sequential", precision="fp64", n_iter=3, band_group=2, cta_threads=160, order=o)
+        s.solve(scheme="sequential", precision="fp64", n_iter=3, band_group=2, cta_threads=160, order=o,
+                deterministic=True)
         alone.append(s.temperature(0))
         s.close()
     ss = [nbte_mod.Solver(p) for p in probs]
@@ -168,10 +166,10 @@ def test_order2_in_a_batch(nbte_mod):
     for o in (1, 2):
         sel = [s for s, oo in zip(ss, orders) if oo == o]
         infos = nbte_mod.solve_batch(sel, scheme="sequential", precision="fp64", n_iter=3, band_group=2,
-                                     cta_threads=160, order=o)
+                                     cta_threads=160, order=o, deterministic=True)
         assert all(i["status"] == 0 for i in infos)
-    for p, s, T in zip(probs, ss, alone):
-        assert rel_T(s.temperature(0), T, p.T_ref) <= 1e-12
+    for s, T in zip(ss, alone):
+        assert np.array_equal(s.temperature(0), T)
         s.close()
 
 
