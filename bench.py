@@ -390,6 +390,8 @@ def run_gpu(args):
         "clocks": clocks,
     }
     solver.close()
+    if rank == 0 and ws == 1 and not args.no_serve:
+        out["serving"] = serving_summary()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, max_seconds=args.cpu_seconds)
     if dist:
@@ -501,6 +503,74 @@ def cpu_baseline(workload, max_seconds=20.0, steps=1, warmup=1, pool=None):
                       f"from T_ref ({pool.n_cells} cells each; moments included), {k} per worker process; "
                       f"sparse LU of Eq. (13) in a fill-free upwind order (SciPy), one process per core",
             "seconds_per_step": dt}
+
+
+def serving_summary(n_requests=8, n_range=(20000, 80000), tol=1e-8):
+    """Batched and served forms against one solve at a time, on a small
+    seeded request stream (2D tri / 3D hex / 3D tet geometries, mixed band
+    counts, direction sets, heat loads and walls), every request submitted
+    at once: one at a time (nbte_solve_steady per request, planning
+    included), one nbte_solve_batch call, and the continuous-batching server.
+    Same options and tolerance in every arm (synthetic scheme, FP32 sweep,
+    fixed layout); the largest relative temperature difference between each
+    arm's results and the one-at-a-time ones is reported beside the rates."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2607_03226_b300 import nbte
+
+    reqs = W.stream.requests(n_requests, rate=1.0, n_range=n_range)
+    probs = [W.stream.build(r) for r in reqs]
+    opts = dict(scheme="synthetic", precision="fp32", tol=tol, max_iter=20000, band_group=2, cta_threads=160,
+                use_graph=True, skip_outputs=True)
+    upd = [p.updates_per_iteration for p in probs]
+
+    def rel(T, Tref, p):
+        return float(np.abs(T - Tref).max() / max(np.abs(Tref - p.T_ref).max(), 1e-300))
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    alone, work1 = [], 0
+    for p, u in zip(probs, upd):
+        s = nbte.Solver(p)
+        info = s.solve(**opts)
+        alone.append(s.temperature(0))
+        work1 += u * info["iterations"]
+        s.close()
+    t_one = time.perf_counter() - t0
+
+    solvers = [nbte.Solver(p) for p in probs]
+    t0 = time.perf_counter()
+    infos = nbte.solve_batch(solvers, **opts)
+    t_batch = time.perf_counter() - t0
+    work2 = sum(u * i["iterations"] for u, i in zip(upd, infos))
+    d_batch = max(rel(s.temperature(0), T, p) for s, T, p in zip(solvers, alone, probs))
+    for s in solvers:
+        s.close()
+
+    solvers = [nbte.Solver(p) for p in probs]
+    srv = nbte.Server(max_active=32, n_planners=4, **opts)
+    t0 = time.perf_counter()
+    ids = [srv.submit(s) for s in solvers]
+    srv.drain(timeout_s=600)
+    t_srv = time.perf_counter() - t0
+    polls = [srv.poll(i) for i in ids]
+    work3 = sum(u * pl[0]["iterations"] for u, pl in zip(upd, polls))
+    failed = sum(pl[0]["status"] != 0 for pl in polls)
+    lat = np.array([pl[1] for pl in polls])
+    d_srv = max(rel(s.temperature(0), T, p) for s, T, p in zip(solvers, alone, probs))
+    srv.close()
+    for s in solvers:
+        s.close()
+    return {"requests": len(probs), "cells": list(n_range), "tol": tol,
+            "one_at_a_time": {"updates_per_s": work1 / t_one, "makespan_s": t_one},
+            "batched": {"updates_per_s": work2 / t_batch, "makespan_s": t_batch, "max_rel_T_vs_alone": d_batch},
+            "served": {"updates_per_s": work3 / t_srv, "makespan_s": t_srv, "max_rel_T_vs_alone": d_srv,
+                       "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                       "failed": int(failed)},
+            "speedup_batched": (work2 / t_batch) / (work1 / t_one),
+            "speedup_served": (work3 / t_srv) / (work1 / t_one),
+            "layout": "band_group=2 cta_threads=160, synthetic scheme, FP32 sweep, every request at once"}
 
 
 def run_stream(args):
@@ -732,6 +802,8 @@ def main():
     ap.add_argument("--converge-tol", type=float, default=0.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the batched / served / one-at-a-time comparison on a small request stream")
     ap.add_argument("--converge", action="store_true",
                     help="time and iterations to a converged field, both schemes and starts (3D workloads)")
     ap.add_argument("--max-iter", type=int, default=20000)

@@ -175,6 +175,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
 
   const int i = a.item_dir[item];
   const int g = a.item_grp[item];
+  const int64_t di = (int64_t)i * a.n_groups + g;   // direction-major index of the per-item tables
   const int ncons = blockDim.x - 32;
   const int64_t ch0 = a.chunk_off[i];
   const int nch = (int)(a.chunk_off[i + 1] - ch0);
@@ -247,7 +248,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         int64_t da = 0;
         if constexpr (sizeof(R) == 8) {
           constexpr int dper16 = G == 1 ? 2 : 1;   // positions per 16 bytes
-          const int64_t d0 = (int64_t)item * a.N + m.pos;
+          const int64_t d0 = di * a.N + m.pos;
           da = d0 / dper16 * dper16;
           const int64_t de = (d0 + m.len + dper16 - 1) / dper16 * dper16;
           den_bytes = (unsigned)((de - da) * G * 8);
@@ -257,7 +258,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
         int64_t sa = 0;
         if constexpr (O2) {
           constexpr int sper16 = (int)(16 / (G * sizeof(R))) > 1 ? (int)(16 / (G * sizeof(R))) : 1;
-          const int64_t s0 = (int64_t)item * a.N + m.pos;
+          const int64_t s0 = di * a.N + m.pos;
           sa = s0 / sper16 * sper16;
           const int64_t se = (s0 + m.len + sper16 - 1) / sper16 * sper16;
           s2_bytes = (unsigned)((se - sa) * G * sizeof(R));
@@ -296,7 +297,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     aQ[b] = a.band_aQ[band0 + b];
     wt[b] = (R)(wi * (double)itau[b]);
   }
-  R* part = a.part ? a.part + (int64_t)item * a.N : nullptr;
+  R* part = a.part ? a.part + di * a.N : nullptr;
   double* acc = a.acc;
   R* exp_g = a.exp + ((size_t)g * a.n_exp + a.exp_off[i]) * GP;
 #ifdef NBTE_CHECKS
@@ -338,11 +339,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<R>& a, const int item
     const int imp0 = m.imp;
     // FP64: this chunk's precomputed denominators (superset starts d_shift early)
     const R* dens = reinterpret_cast<const R*>(st + a.off_den);
-    const int d_shift = sizeof(R) == 8 && G == 1 ? (int)(((int64_t)item * a.N + m.pos) % 2) : 0;
+    const int d_shift = sizeof(R) == 8 && G == 1 ? (int)((di * a.N + m.pos) % 2) : 0;
     // second order: this chunk's reconstruction sources (superset starts s_shift early)
     constexpr int sper16 = (int)(16 / (G * sizeof(R))) > 1 ? (int)(16 / (G * sizeof(R))) : 1;
     const R* s2 = reinterpret_cast<const R*>(st + a.off_src2);
-    const int s_shift = O2 ? (int)(((int64_t)item * a.N + m.pos) % sper16) : 0;
+    const int s_shift = O2 ? (int)((di * a.N + m.pos) % sper16) : 0;
     // the chunk's levels in order, a named barrier between them (each sees
     // the ring values the previous one wrote)
     int lb = 0;

@@ -34,8 +34,10 @@ struct SweepArgs {
   const R* src2;                 // second-order upwind: [n_items*N*G] per position, the
                                  // reconstruction's extra source (sum over faces), else null
   int64_t n_exp, n_imp;
-  const int32_t* item_dir;       // [n_items]
-  const int32_t* item_grp;       // [n_items]
+  const int32_t* item_dir;       // [n_items] direction of the CTA's work item
+  const int32_t* item_grp;       // [n_items] band group of the CTA's work item
+  int n_groups;                  // band groups per direction: per-item tables (dinv, src2, part) are
+                                 // indexed direction-major, i * n_groups + g
   const int64_t* chunk_off;      // [D+1]
   const Chunk* chunks;
   const unsigned char* rec;      // per chunk: its packed position records, then its (T', Qdot) pairs
