@@ -2436,6 +2436,24 @@ int nbte_solve_batch(nbte_solver* const* solvers, int32_t n, const nbte_solve_op
       if (Ss[j] == Ss[k]) return fail(NBTE_ERR_ARG, "a solver appears twice in the batch");
   }
   try {
+    // the host-heavy set-up of every solver at once, one thread each (as the
+    // server's planner threads do): direction plans and, for the synthetic
+    // schemes, the correction's operator.  A failure here is left for the
+    // serial preparation below to report on the calling thread.
+    if (n > 1) {
+      int dev = 0;
+      NBTE_CK(cudaGetDevice(&dev));
+      std::vector<std::thread> th;
+      for (int k = 0; k < n; ++k)
+        th.emplace_back([&, k] {
+          nbte_solver* S = Ss[k];
+          cudaSetDevice(S->device >= 0 ? S->device : dev);
+          int r = ensure_device(S);
+          if (!r) r = ensure_plan(S);
+          if (!r && (o.scheme != 0 || o.init == 1)) ensure_laplacian(S);
+        });
+      for (auto& t : th) t.join();
+    }
     for (int k = 0; k < n; ++k) {
       rc = prepare(Ss[k], o);
       if (rc) return rc;
