@@ -6,7 +6,7 @@ iteration count; values are absolute temperatures (K) and heat fluxes (W/m^2).
 
 Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_converged|
                                             finfet2d_order2_steps|cube3d_tasks|finfet3d_tasks|
-                                            cube3d_converged|finfet3d_steps ...]
+                                            cube3d_converged|stream_converged|finfet3d_steps ...]
 
 * ``square``              - the 40x40 in-plane square, sequential to 1e-12
                             (all 1600 cells).
@@ -28,11 +28,14 @@ Usage:  python tests/golden/make_golden.py [square|finfet2d_steps|finfet2d_conve
 * ``cube3d_converged``    - the 64^3 cube converged with the synthetic scheme
                             (1e-12, from the diffusion guess): T_L and q on
                             the sample cells.
+* ``stream_converged``    - the smallest 2D-triangle, 3D-hex and 3D-tet
+                            requests of the serving stream, each converged
+                            (synthetic, 1e-12): T_L and q on sample cells.
 * ``finfet3d_steps``      - the 1.14M-tet FinFET: T_L after sequential
                             iterations 1, 2 and 3 from T_ref and q of the
                             third sweep, on the sample cells.
 
-The last three split every pass over worker processes by direction (one per
+The 3D ones and the stream requests split every pass over worker processes by direction (one per
 available core, or GOLDEN_WORKERS; ``PoolSweep``).
 """
 from __future__ import annotations
@@ -74,9 +77,20 @@ _O = None
 _KEEP = True
 
 
+def _problem(name, kwargs):
+    """A workload by name: a family of workloads.problems, or
+    "stream:<kind>" for the smallest request of that mesh kind in the
+    benchmark's seeded 24-request stream."""
+    if name.startswith("stream:"):
+        kind = name.split(":", 1)[1]
+        reqs = W.stream.requests(24, 1.0)
+        return W.stream.build(min((r for r in reqs if r.kind == kind), key=lambda r: r.n_cells_target))
+    return getattr(W.problems, name)(**kwargs)
+
+
 def _pool_init(name, kwargs, keep):
     global _O, _KEEP
-    _O = OracleSolver(getattr(W.problems, name)(**kwargs))
+    _O = OracleSolver(_problem(name, kwargs))
     _KEEP = keep
 
 
@@ -250,6 +264,32 @@ def cube3d_converged():
         cells=idx.tolist(), T=r["T"][idx].tolist(), q=r["q"][idx].tolist(),
         T_max=float(r["T"].max()), T_min=float(r["T"].min()), q_max=float(np.abs(r["q"]).max()),
         energy_imbalance=r["energy_imbalance"], residuals=r["residuals"]))
+
+
+def stream_converged():
+    """The smallest request of each mesh kind in the benchmark's seeded
+    24-request stream (a 2D triangle fin, a 3D hex box, a 3D tet fin, with
+    their random wall mixes and heat boxes), each converged with the
+    synthetic scheme to 1e-12 from the diffusion guess: T_L and q on up to
+    4096 sample cells of each."""
+    out = dict(command="python tests/golden/make_golden.py stream_converged", scheme="synthetic",
+               init="fourier", tol=1e-12, sample_seed=SAMPLE_SEED, requests={})
+    for kind in ("tri2d", "hex3d", "tet3d"):
+        name = "stream:" + kind
+        p = _problem(name, {})
+        o = OracleSolver(p)
+        pool = PoolSweep(o, name)
+        idx = _sample(p.n_cells)
+        t = time.time()
+        r = o.solve(scheme="synthetic", tol=1e-12, max_iter=5000, init="fourier", sweep=pool, verbose=True)
+        pool.close()
+        out["requests"][kind] = dict(
+            n_cells=p.n_cells, bands=p.n_bands, directions=p.n_dirs, iterations=r["iterations"],
+            converged=r["converged"], seconds=time.time() - t, cells=idx.tolist(), T=r["T"][idx].tolist(),
+            q=r["q"][idx].tolist(), T_max=float(r["T"].max()), T_min=float(r["T"].min()),
+            q_max=float(np.abs(r["q"]).max()), energy_imbalance=r["energy_imbalance"])
+        print(kind, r["iterations"], time.time() - t, flush=True)
+    _write("stream_converged.json", out)
 
 
 def finfet3d_steps():

@@ -144,3 +144,32 @@ def test_cube3d_full_size_converged(nbte_mod):
     eT = np.abs(s.temperature(0)[idx] - Tg).max() / dev
     print(f"cube3d fp32 synthetic: {info['iterations']} iterations (floor {info['residual']:.1e}), T {eT:.2e}")
     assert eT < 1e-6
+
+
+@pytest.mark.parametrize("k,kind", [(0, "tri2d"), (1, "hex3d"), (2, "tet3d")])
+def test_stream_requests_converged(nbte_mod, k, kind):
+    """The smallest 2D-triangle, 3D-hex and 3D-tet requests of the serving
+    stream (random wall mixes with partially specular and specular walls,
+    heat boxes) converged with the synthetic scheme, against the oracle's
+    field converged to 1e-12: FP64 T 1e-9, q 1e-8; the FP32 sweep T 1e-6."""
+    g = _golden("stream_converged.json")
+    assert g["tol"] <= 1e-12
+    r = g["requests"][kind]
+    p = _stream_problems()[k]
+    assert p.n_cells == r["n_cells"] and r["converged"]
+    idx = np.array(r["cells"])
+    Tg, qg = np.array(r["T"]), np.array(r["q"])
+    dev = max(r["T_max"] - p.T_ref, p.T_ref - r["T_min"])
+    s = nbte_mod.Solver(p)
+    info = s.solve(scheme="synthetic", precision="fp64", tol=1e-13, max_iter=20000, init="fourier")
+    assert info["status"] == 0
+    eT = np.abs(s.temperature(0)[idx] - Tg).max() / dev
+    eq = np.abs(s.heat_flux()[idx] - qg).max() / r["q_max"]
+    print(f"{kind} ({p.n_cells} cells) fp64: {info['iterations']} iterations, T {eT:.2e}, q {eq:.2e}")
+    assert eT < 1e-9 and eq < 1e-8
+    info = s.solve(scheme="synthetic", precision="fp32", tol=1e-9, max_iter=20000, init="fourier")
+    assert info["status"] == 0
+    eT = np.abs(s.temperature(0)[idx] - Tg).max() / dev
+    print(f"{kind} fp32: {info['iterations']} iterations (floor {info['residual']:.1e}), T {eT:.2e}")
+    assert eT < 1e-6
+    s.close()
