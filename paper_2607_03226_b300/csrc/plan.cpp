@@ -195,6 +195,8 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
   // pass 0: Kahn level counts only (they set level_cap); pass 1: the plan
   auto work = [&](int tid, int nt, int pass) {
     std::vector<int32_t> indeg(N), level(N), slot(N), last_use(N), exp_local(N), cand, best, occ;
+    std::vector<int32_t> up_off, up_list, dn_off, dn_list;
+    std::vector<double> xr;
     std::vector<char> lagged(H);
     std::vector<signed char> fcls(H);
     std::vector<int32_t> order, cur, next, free_slots;
@@ -202,13 +204,15 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
     for (int i = tid; i < D; i += nt) {
       DirOut& o = outs[i];
       o = DirOut();
+      // each half-face's class for this direction: inflow (-1), none, outflow
+      for (int64_t h = 0; h < H; ++h) fcls[h] = (signed char)cls(dotsa(i, h), h);
       std::fill(indeg.begin(), indeg.end(), 0);
       std::fill(level.begin(), level.end(), -1);
       std::fill(lagged.begin(), lagged.end(), 0);
       for (int64_t c = 0; c < N; ++c)
         for (int k = 0; k < nfc; ++k) {
           const int64_t h = c * nfc + k;
-          if (m.nb[h] >= 0 && cls(dotsa(i, h), h) < 0) indeg[c]++;
+          if (m.nb[h] >= 0 && fcls[h] < 0) indeg[c]++;
         }
       // ---- Kahn levels with deterministic cycle breaking
       order.clear();
@@ -223,7 +227,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
           const int64_t c = scan;
           for (int k = 0; k < nfc; ++k) {
             const int64_t h = c * nfc + k;
-            if (m.nb[h] >= 0 && level[m.nb[h]] < 0 && cls(dotsa(i, h), h) < 0) {
+            if (m.nb[h] >= 0 && level[m.nb[h]] < 0 && fcls[h] < 0) {
               lagged[h] = 1;
               o.lagged++;
             }
@@ -244,7 +248,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
           for (int k = 0; k < nfc; ++k) {
             const int64_t h = (int64_t)u * nfc + k;
             const int64_t v = m.nb[h];
-            if (v < 0 || cls(dotsa(i, h), h) <= 0) continue;
+            if (v < 0 || fcls[h] <= 0) continue;
             if (level[v] >= 0) continue;   // edge into an already released cell: lagged
             if (--indeg[v] == 0) next.push_back((int32_t)v);
           }
@@ -258,32 +262,47 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
       int L = (int)o.lp.size() - 1;
       // ---- tilted fronts (release levels along the long axis), see the
       // file comment.  `order` is topological for the non-lagged edges.
-      for (int64_t h = 0; h < H; ++h) fcls[h] = (signed char)cls(dotsa(i, h), h);
+      // the direction's upwind graph without its lagged edges, compact:
+      // upstream cells of each position (in topological order) and
+      // downstream cells of each cell, and each position's coordinate along
+      // the tilt axis (in the direction's sense, from the mesh's near end)
+      const double sg = s[i * 3 + tilt_axis] >= 0 ? 1.0 : -1.0;
+      const double x0 = sg > 0 ? bb_lo[tilt_axis] : -bb_hi[tilt_axis];
+      up_off.assign(N + 1, 0);
+      dn_off.assign(N + 1, 0);
+      up_list.clear();
+      dn_list.clear();
+      xr.resize(N);
+      for (int64_t p = 0; p < N; ++p) {
+        const int32_t c = order[p];
+        for (int k = 0; k < nfc; ++k) {
+          const int64_t h = (int64_t)c * nfc + k;
+          if (fcls[h] < 0 && m.nb[h] >= 0 && !lagged[h]) up_list.push_back((int32_t)m.nb[h]);
+        }
+        up_off[p + 1] = (int32_t)up_list.size();
+        xr[p] = sg * m.xc[(int64_t)c * dim + tilt_axis] - x0;
+      }
+      for (int64_t c = 0; c < N; ++c) {
+        for (int k = 0; k < nfc; ++k) {
+          const int64_t h = c * nfc + k;
+          const int64_t v = m.nb[h];
+          if (v >= 0 && fcls[h] > 0 && !lagged[m.twin[h]]) dn_list.push_back((int32_t)v);
+        }
+        dn_off[c + 1] = (int32_t)dn_list.size();
+      }
       // levels with release slope `slope` (0: none), then as late as
       // possible; returns the level count
       auto relevel = [&](double slope, std::vector<int32_t>& lev) -> int {
-        const double sg = s[i * 3 + tilt_axis] >= 0 ? 1.0 : -1.0;
-        const double x0 = sg > 0 ? bb_lo[tilt_axis] : -bb_hi[tilt_axis];
         lev.resize(N);
         for (int64_t p = 0; p < N; ++p) {
-          const int32_t c = order[p];
-          int32_t l = slope > 0 ? (int32_t)std::floor(slope * (sg * m.xc[(int64_t)c * dim + tilt_axis] - x0) / hcell)
-                                : 0;
-          for (int k = 0; k < nfc; ++k) {
-            const int64_t h = (int64_t)c * nfc + k;
-            if (fcls[h] < 0 && m.nb[h] >= 0 && !lagged[h]) l = std::max(l, lev[m.nb[h]] + 1);
-          }
-          lev[c] = l;
+          int32_t l = slope > 0 ? (int32_t)std::floor(slope * xr[p] / hcell) : 0;
+          for (int32_t e = up_off[p]; e < up_off[p + 1]; ++e) l = std::max(l, lev[up_list[e]] + 1);
+          lev[order[p]] = l;
         }
         for (int64_t p = N - 1; p >= 0; --p) {
           const int32_t u = order[p];
           int32_t first = INT32_MAX;
-          for (int k = 0; k < nfc; ++k) {
-            const int64_t h = (int64_t)u * nfc + k;
-            const int64_t v = m.nb[h];
-            if (v < 0 || fcls[h] <= 0 || lagged[m.twin[h]]) continue;
-            first = std::min(first, lev[v]);
-          }
+          for (int32_t e = dn_off[u]; e < dn_off[u + 1]; ++e) first = std::min(first, lev[dn_list[e]]);
           if (first != INT32_MAX && first - 1 > lev[u]) lev[u] = first - 1;
         }
         // drop empty levels (release levels can leave gaps)
@@ -305,12 +324,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
         occ.assign(nl + 1, 0);
         for (int64_t c = 0; c < N; ++c) {
           int32_t last = -1;
-          for (int k = 0; k < nfc; ++k) {
-            const int64_t h = c * nfc + k;
-            const int64_t v = m.nb[h];
-            if (v < 0 || fcls[h] <= 0 || lagged[m.twin[h]]) continue;
-            last = std::max(last, lev[v]);
-          }
+          for (int32_t e = dn_off[c]; e < dn_off[c + 1]; ++e) last = std::max(last, lev[dn_list[e]]);
           if (last >= 0) {
             occ[lev[c]]++;
             occ[last + 1]--;
@@ -358,7 +372,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
           for (int k = 0; k < nfc; ++k) {
             const int64_t h = (int64_t)u * nfc + k;
             const int64_t v = m.nb[h];
-            if (v < 0 || cls(dotsa(i, h), h) <= 0 || lagged[m.twin[h]]) continue;
+            if (v < 0 || fcls[h] <= 0 || lagged[m.twin[h]]) continue;
             first = std::min(first, level[v]);
           }
           if (first != INT32_MAX && first - 1 > level[u]) level[u] = first - 1;
@@ -378,7 +392,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
         for (int k = 0; k < nfc; ++k) {
           const int64_t h = c * nfc + k;
           const int64_t v = m.nb[h];
-          if (v < 0 || cls(dotsa(i, h), h) <= 0) continue;
+          if (v < 0 || fcls[h] <= 0) continue;
           if (lagged[m.twin[h]]) continue;
           last_use[c] = std::max(last_use[c], level[v]);
         }
@@ -413,7 +427,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
       o.exp_cells.clear();
       std::vector<char> is_exp(N, 0);
       for (int64_t h : bhf)
-        if (cls(dotsa(i, h), h) > 0) is_exp[h / nfc] = 1;
+        if (fcls[h] > 0) is_exp[h / nfc] = 1;
       for (int64_t h = 0; h < H; ++h)
         if (lagged[h]) is_exp[m.nb[h]] = 1;
       for (int64_t c = 0; c < N; ++c)
