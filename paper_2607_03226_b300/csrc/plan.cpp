@@ -205,7 +205,16 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
       DirOut& o = outs[i];
       o = DirOut();
       // each half-face's class for this direction: inflow (-1), none, outflow
-      for (int64_t h = 0; h < H; ++h) fcls[h] = (signed char)cls(dotsa(i, h), h);
+      if (dim == 3) {
+        const double s0 = s[i * 3], s1 = s[i * 3 + 1], s2 = s[i * 3 + 2];
+        for (int64_t h = 0; h < H; ++h) {
+          const double a = s0 * m.An[h * 3] + s1 * m.An[h * 3 + 1] + s2 * m.An[h * 3 + 2];
+          const double t = kTangent * area[h];
+          fcls[h] = (signed char)(a > t ? 1 : (a < -t ? -1 : 0));
+        }
+      } else {
+        for (int64_t h = 0; h < H; ++h) fcls[h] = (signed char)cls(dotsa(i, h), h);
+      }
       std::fill(indeg.begin(), indeg.end(), 0);
       std::fill(level.begin(), level.end(), -1);
       std::fill(lagged.begin(), lagged.end(), 0);
