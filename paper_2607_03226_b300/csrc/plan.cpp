@@ -200,7 +200,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
     std::vector<char> lagged(H);
     std::vector<signed char> fcls(H);
     std::vector<int32_t> order, cur, next, free_slots;
-    std::vector<std::vector<int32_t>> release;
+    std::vector<int32_t> rel_off, rel_cells, rel_fill;
     for (int i = tid; i < D; i += nt) {
       DirOut& o = outs[i];
       o = DirOut();
@@ -405,13 +405,21 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
           if (lagged[m.twin[h]]) continue;
           last_use[c] = std::max(last_use[c], level[v]);
         }
-      release.assign(L + 1, {});
+      // cells whose slot frees at each level (counting sort by that level,
+      // cell order kept within one)
+      rel_off.assign(L + 2, 0);
       for (int64_t c = 0; c < N; ++c)
-        if (last_use[c] >= 0) release[last_use[c] + 1 <= L ? last_use[c] + 1 : L].push_back((int32_t)c);
+        if (last_use[c] >= 0) rel_off[(last_use[c] + 1 <= L ? last_use[c] + 1 : L) + 1]++;
+      for (int l = 0; l <= L; ++l) rel_off[l + 1] += rel_off[l];
+      rel_cells.resize(rel_off[L + 1]);
+      rel_fill.assign(rel_off.begin(), rel_off.end() - 1);
+      for (int64_t c = 0; c < N; ++c)
+        if (last_use[c] >= 0) rel_cells[rel_fill[last_use[c] + 1 <= L ? last_use[c] + 1 : L]++] = (int32_t)c;
       free_slots.clear();
       int32_t next_new = 1;   // slot 0 is the permanent zero slot
       for (int l = 0; l < L; ++l) {
-        for (int32_t c : release[l]) {
+        for (int32_t e = rel_off[l]; e < rel_off[l + 1]; ++e) {
+          const int32_t c = rel_cells[e];
           free_slots.push_back(slot[c]);
           std::push_heap(free_slots.begin(), free_slots.end(), std::greater<int32_t>());
         }
