@@ -152,10 +152,12 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
     }
     return mirror_cache.emplace(key, std::move(R)).first->second;
   };
-  // fill the cache serially (it is read by the worker threads)
+  // fill the cache serially (it is read by the worker threads), and keep
+  // each reflecting half-face's map
+  std::vector<const std::vector<int32_t>*> mirror_of_h(H, nullptr);
   for (int64_t h : bhf) {
     const BC& b = bcmap.at(m.tag[h]);
-    if (b.type == NBTE_SPECULAR || b.type == NBTE_PARTIAL) mirror_map(h);
+    if (b.type == NBTE_SPECULAR || b.type == NBTE_PARTIAL) mirror_of_h[h] = &mirror_map(h);
   }
 
   P.pos_cell.assign((size_t)D * N, 0);
@@ -490,12 +492,7 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
               } else {
                 im.kind = b.type == NBTE_SPECULAR ? IMP_SPECULAR : IMP_PARTIAL;
                 im.par = b.p;
-                im.src_dir = mirror_cache.at([&] {
-                  double n[3];
-                  unit_normal(h, n);
-                  return std::array<long long, 3>{std::llround(n[0] * 1e12), std::llround(n[1] * 1e12),
-                                                  std::llround(n[2] * 1e12)};
-                }())[i];
+                im.src_dir = (*mirror_of_h[h])[i];
                 im.src_cell = c;
                 if (im.src_dir < 0) { o.error = "no direction leaves through a specular wall"; return; }
               }
