@@ -263,7 +263,9 @@ Status build_plan(const Mesh& m, int D, const double* s, const double* w, const 
             if (level[v] >= 0) continue;   // edge into an already released cell: lagged
             if (--indeg[v] == 0) next.push_back((int32_t)v);
           }
-        std::sort(next.begin(), next.end());
+        // (the order within a level does not matter: the forced cell of a
+        // cycle is found by index, and the level lists are rebuilt by cell
+        // index below)
         cur.swap(next);
       }
       if (pass == 0) {
